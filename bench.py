@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark of the MHAR walker step on one GB300 (or N replicas, one per GPU).
+
+One bench step = one full run of the workload: z = 4096 walkers advanced
+2000 iterations of Algorithm 2 on a random polytope with n = 100, m = 2000
+(unit-norm Gaussian rows, b = 1, x0 = 0), in the mixed tensor-core mode, with
+the final points written to a device buffer.  Metric: walker-steps/s
+(= z x iterations / time, the paper's "samples per second" of Section 6.2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2104_07097_gb300 import workloads as wl  # noqa: E402
+
+WORKLOAD = dict(name="rand100x2000", n=100, m=2000, seed=2, z=4096, iterations=2000)
+METRIC = "walker-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE = dict(walkers=256, iterations=200)
+REF_SAMPLE = dict(walkers=64, iterations=20)
+
+
+def polytope():
+    return wl.random_polytope(WORKLOAD["n"], WORKLOAD["m"], seed=WORKLOAD["seed"])
+
+
+def config(precision: str) -> dict:
+    return {"workload": f"{WORKLOAD['name']} z={WORKLOAD['z']} x {WORKLOAD['iterations']} iterations",
+            "n": WORKLOAD["n"], "m": WORKLOAD["m"], "z": WORKLOAD["z"],
+            "iterations_per_step": WORKLOAD["iterations"], "precision": precision,
+            "l2": "flushed between steps (256 MiB write); the chain's own state stays resident within a step"}
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "_source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def cpu_baseline(p) -> dict:
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    zs, ts = CPU_SAMPLE["walkers"], CPU_SAMPLE["iterations"]
+    X0 = np.tile(p.x0, (zs, 1))
+    t0 = time.perf_counter()
+    oracle.mhar_run(p.A, p.b, X0, steps=ts, thin=0, seed=0)
+    dt = time.perf_counter() - t0
+    return {"value": zs * ts / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{zs} walkers x {ts} iterations of {WORKLOAD['name']} (FP64 oracle, 1 thread, {dt:.1f} s)"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    p = polytope()
+    zs, ts = REF_SAMPLE["walkers"], REF_SAMPLE["iterations"]
+    X = np.tile(p.x0, (zs, 1))
+    step0 = 0
+    for _ in range(args.warmup):
+        X = oracle.mhar_run(p.A, p.b, X, steps=ts, thin=0, seed=0, step0=step0)["X"]
+        step0 += ts
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        X = oracle.mhar_run(p.A, p.b, X, steps=ts, thin=0, seed=0, step0=step0)["X"]
+        times.append(time.perf_counter() - t0)
+        step0 += ts
+    ms = 1e3 * statistics.mean(times)
+    value = zs * ts / (ms / 1e3)
+    sample = f"{zs} walkers x {ts} iterations of {WORKLOAD['name']} per step (FP64 oracle, 1 thread)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random polytope)", "config": config("fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2104_07097_gb300 import build as libbuild
+    from paper_2104_07097_gb300 import mhar
+    libbuild.build()
+    mhar.load()
+
+    p = polytope()
+    z, iters = WORKLOAD["z"], WORKLOAD["iterations"]
+    stream = torch.cuda.current_stream()
+    s = mhar.Sampler(p.A, p.b, p.x0, z, precision=args.precision, seed=0, walker0=rank * z,
+                     stream=stream, out_on_device=True)
+    out = torch.empty((1, z, p.n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        s.run(iters, thin=iters, out=out)
+    torch.cuda.synchronize()
+    launches0 = s.stats().kernel_launches
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            s.run(iters, thin=iters, out=out)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    launches = s.stats().kernel_launches - launches0
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * z * iters / (ms / 1e3)
+
+    # Per-kernel device times (CUDA events around each launch, same stream).
+    kms = s.time_kernels(128)
+    st = s.check()
+    peaks = load_peaks()
+    m, n = p.m, p.n
+    if args.precision == "mixed":
+        flops = 6.0 * m * n * z          # 3 FP16 products of 2 m n per walker-step
+        peak = peaks["bf16_tflops_sustained"]
+        roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
+                    "traffic": None, "kernel": "chord_tc_kernel",
+                    "algorithmic": "6 m n flops per walker-step (FP16 hi.hi + hi.lo + lo.hi)",
+                    "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}
+    else:
+        bytes_ = 2.0 * m * n * z * (8 if args.precision == "fp64" else 4)
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel": "chord_simt_kernel"}
+
+    # End to end through the public API from pinned host buffers: create
+    # (H2D of A, b, x0), run, D2H of the emitted points, destroy.
+    pinA = torch.from_numpy(p.A).pin_memory()
+    pinb = torch.from_numpy(p.b).pin_memory()
+    pinx = torch.from_numpy(p.x0).pin_memory()
+    pinout = torch.empty((1, z, n), dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(min(3, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with mhar.Sampler(pinA.numpy(), pinb.numpy(), pinx.numpy(), z, precision=args.precision,
+                          seed=1, walker0=rank * z, stream=stream) as se:
+            se.run(iters, thin=iters, out=pinout.numpy())
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * z * iters / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": int(8 * (m * n + m + n)), "d2h_bytes_per_step": int(8 * z * n + 16)}
+
+    # Plain FP32 MHAR (CUDA cores, the paper's recompute formulation) on the
+    # same workload, for the mixed-vs-plain comparison.
+    plain = None
+    if args.precision == "mixed":
+        with mhar.Sampler(p.A, p.b, p.x0, z, precision="fp32", seed=0, walker0=rank * z,
+                          stream=stream, out_on_device=True) as sp:
+            sp.run(iters, thin=iters, out=out)
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            sp.run(iters, thin=iters, out=out)
+            b2.record(stream)
+            torch.cuda.synchronize()
+            plain = {"value": z * iters / (a.elapsed_time(b2) / 1e3), "unit": METRIC,
+                     "precision": "fp32 (CUDA cores)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"mixed": "f16x3-f32acc", "fp32": "f32", "fp64": "f64"}[args.precision],
+                "data": "synthetic (seeded random polytope, unit-norm Gaussian rows)",
+                "config": config(args.precision), "roofline": roofline,
+                "kernel_ms": {"directions": kms[0], "chord": kms[1], "refresh": kms[2]},
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+                "feasibility": {"max_violation": st.max_violation, "refresh_drift": st.refresh_drift,
+                                "stalls": st.stalls},
+                "plain_fp32": plain}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

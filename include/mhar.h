@@ -1,0 +1,178 @@
+/*
+ * mhar.h -- C ABI of the GB300 Matrix Hit-and-Run library (libmhar.so).
+ *
+ * Matrix Hit-and-Run (MHAR; Vazquez Corte & Montiel, arXiv 2104.07097,
+ * Algorithm 2) moves z walkers together inside the polytope
+ *     Delta = { x in R^n : A x <= b,  A_E x = b_E }       (Section 2.1, Eqs. TS1-TS3)
+ * Each iteration draws Gaussian directions H (n x z; Section 4.3), projects
+ * them onto the null space of A_E (D = P H with P = I - A_E^T (A_E A_E^T)^{-1} A_E,
+ * Section 3.2), finds every walker's chord (lambda_min, lambda_max) from the
+ * ratios (b - A X) / (A D) (Section 4.4), draws theta uniformly on it and
+ * moves x^k += theta^k d^k (Section 4.5).  Every `thin` iterations the z
+ * points are emitted (the thinning factor phi of Algorithm 2).
+ *
+ * Everything below runs as hand-written CUDA kernels for sm_103a on the
+ * current CUDA device.  There is no CPU fallback: without a usable device
+ * every entry point returns MHAR_E_CUDA.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major FP64 host arrays unless stated otherwise; the
+ *     library copies what it needs, the caller keeps ownership.
+ *   - Return value 0 (MHAR_OK) or a negative MHAR_E_* code.  After an error
+ *     the context stays usable; mhar_last_error() describes the failure.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef MHAR_H
+#define MHAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define MHAR_OK                 0
+#define MHAR_E_ARG             -1  /* bad pointer, size or option            */
+#define MHAR_E_X0_INFEASIBLE   -2  /* start not strictly inside A x <= b, or
+                                      |A_E x0 - b_E| too large               */
+#define MHAR_E_UNBOUNDED       -3  /* some walker met a chord open on one side
+                                      (the body is unbounded, Section 2.1
+                                      assumes bounded bodies)                */
+#define MHAR_E_NONFINITE       -4  /* a non-finite slack, ratio or point     */
+#define MHAR_E_CUDA            -5  /* CUDA runtime / driver failure, or no
+                                      sm_103 device                          */
+#define MHAR_E_RANK            -6  /* A_E A_E^T not positive definite        */
+#define MHAR_E_UNSUPPORTED     -7  /* size or mode this build does not cover */
+
+/* ---- arithmetic modes -------------------------------------------------- */
+/* MHAR_FP64: every step in FP64 on CUDA cores; the slack b - A x and A d are
+ *   recomputed each iteration exactly as Lemma 4.2 lists them.
+ * MHAR_FP32: the same recompute formulation in FP32 on CUDA cores (points are
+ *   kept as FP32 pairs, "double-float", so they do not drift).
+ * MHAR_MIXED_F16X3: A D on tcgen05 tensor cores.  Each row of A is scaled by
+ *   a power of two and split into FP16 high + low parts, each direction into
+ *   FP16 high + low parts; three products (hi.hi + hi.lo + lo.hi) accumulate
+ *   in FP32 in tensor memory, which carries A d to about 2^-22 relative.  The
+ *   slack S = b - A X is stored (FP32), updated as S -= (A D) diag(theta) in
+ *   the same kernel, and recomputed from X every refresh_k iterations. */
+#define MHAR_FP64          0
+#define MHAR_FP32          1
+#define MHAR_MIXED_F16X3  2
+
+typedef struct {
+  uint64_t seed;          /* Philox4x32-10 key (default 0)                      */
+  int32_t  precision;     /* MHAR_FP64 (default) | MHAR_FP32 | MHAR_MIXED_F16X3 */
+  int32_t  refresh_k;     /* mixed mode: recompute S = b - A X every refresh_k
+                             iterations (default 64; 0 = never)               */
+  int32_t  out_on_device; /* 1: `out` of mhar_run is a device pointer          */
+  uint32_t walker0;       /* global index of walker 0 (shards of one ensemble
+                             use disjoint ranges; results are then identical
+                             to the unsharded run)                            */
+  void*    stream;        /* cudaStream_t for all work (NULL: legacy stream)   */
+  int32_t  graph_chunk;   /* iterations per captured CUDA graph (default 16;
+                             0 = launch kernels one by one)                   */
+  int32_t  refresh_fp64;  /* mixed mode: 0 (default) recomputes S on the tensor
+                             cores from the same FP16-pair operands the walk
+                             uses (FP32 accumulation); 1 recomputes it in FP64
+                             on CUDA cores (exact, far slower on GB300)       */
+  int32_t  reserved[6];   /* must be zero                                     */
+} mhar_opts;
+
+typedef struct {
+  uint64_t step;            /* iterations completed since creation            */
+  int64_t  walker_steps;    /* step * z                                        */
+  int64_t  stalls;          /* walker-iterations that kept theta = 0 because
+                               the clamped chord was empty                     */
+  int64_t  unbounded;       /* walker-iterations with a one-sided chord        */
+  int32_t  status_bits;     /* OR of MHAR_ST_* seen so far                     */
+  int32_t  precision;
+  double   refresh_drift;   /* max |S_tracked - S_recomputed| at the last
+                               refresh (mixed mode; 0 otherwise)               */
+  double   max_violation;   /* max over walkers, rows of a_i x - b_i (FP64),
+                               filled by mhar_check                            */
+  double   eq_residual;     /* max over walkers of |A_E x - b_E|_inf (FP64),
+                               filled by mhar_check                            */
+  int64_t  kernel_launches; /* library kernels launched so far (graph replays
+                               count every kernel node)                        */
+} mhar_stats;
+
+#define MHAR_ST_UNBOUNDED 1
+#define MHAR_ST_STALL     2
+#define MHAR_ST_NONFINITE 4
+
+typedef struct mhar_ctx mhar_ctx;
+
+/* Fills *opts with the defaults listed above. */
+void mhar_default_opts(mhar_opts* opts);
+
+/* Creates a context holding z walkers, all at x0 (Algorithm 2 initialises
+ * every column of X to the same strictly interior point).
+ *   A    m x n  (m >= 1, n >= 1)        b   m
+ *   AE   mE x n or NULL when mE == 0    bE  mE or NULL
+ *   x0   n, strictly inside: b - A x0 > 0 and |A_E x0 - b_E|_inf <= 1e-9 (1 + |b_E|_inf)
+ *   z    number of walkers; z <= 0 selects the paper's default max(m, n) + 1
+ *   opts NULL for defaults
+ * Copies all inputs to the device, factors A_E A_E^T (FP64 Cholesky) when
+ * mE > 0, and prepares the per-mode operands.  On success *out is a new
+ * context (free with mhar_destroy). */
+int mhar_create(const double* A, const double* b, int m, int n,
+                const double* AE, const double* bE, int mE,
+                const double* x0, int z, const mhar_opts* opts, mhar_ctx** out);
+
+/* Advances every walker `steps` iterations (Algorithm 2's loop) and writes
+ * floor(steps / thin) samples to `out`, laid out out[s][k][i] (s-th sample,
+ * walker k, coordinate i; FP64): the points after iterations thin, 2 thin, ...
+ * of this call.  `out` may be NULL when steps < thin.  It is host memory
+ * unless opts.out_on_device.  Iteration counters (and thus the random
+ * streams) continue across calls.  Returns MHAR_E_UNBOUNDED /
+ * MHAR_E_NONFINITE if any walker met that condition during the call (the
+ * walkers concerned kept theta = 0; the state is still that of the last
+ * iteration). */
+int mhar_run(mhar_ctx* ctx, int64_t steps, int64_t thin, double* out);
+
+/* Copies the current points (z x n, FP64, host) and the iteration counter. */
+int mhar_get_state(const mhar_ctx* ctx, double* X, uint64_t* step);
+
+/* Replaces the points (z x n host FP64, each strictly feasible) and the
+ * iteration counter (checkpoint / resume; per-walker starts).  The stored
+ * slack is recomputed. */
+int mhar_set_state(mhar_ctx* ctx, const double* X, uint64_t step);
+
+/* Chord and step length of every walker at the last iteration run:
+ * lambda_min, lambda_max, theta (each z doubles on the host; any may be NULL). */
+int mhar_get_chord(const mhar_ctx* ctx, double* lmin, double* lmax, double* theta);
+
+/* Recomputes feasibility in FP64 from the current points (max_violation,
+ * eq_residual) and returns all statistics. */
+int mhar_check(mhar_ctx* ctx, mhar_stats* stats);
+
+/* Statistics without the FP64 feasibility pass. */
+int mhar_get_stats(const mhar_ctx* ctx, mhar_stats* stats);
+
+/* Device-time profile of the walker step on the context's stream.  Captures
+ * `iters` (1..4096) real iterations into a CUDA graph and times one replay
+ * with CUDA events; times the direction kernels alone the same way (they are
+ * idempotent for a fixed iteration counter); then times one slack refresh
+ * (mixed mode).  Writes average device milliseconds:
+ *   ms[0] direction draw (+ projection when mE > 0)   (Section 4.3)
+ *   ms[1] the rest of one iteration: the fused tensor-core kernel in mixed
+ *         mode, the chord and update kernels otherwise   (Sections 4.4-4.5)
+ *   ms[2] one slack refresh (mixed mode; 0 otherwise)
+ * The timed iterations are real: the chain and its counters advance. */
+int mhar_time_kernels(mhar_ctx* ctx, int iters, double* ms);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* mhar_last_error(const mhar_ctx* ctx);
+
+/* Name of a return code. */
+const char* mhar_strerror(int code);
+
+/* Frees the context and its device memory; NULL is ignored. */
+void mhar_destroy(mhar_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,619 @@
+// kernels_simt.cu -- CUDA-core kernels of the MHAR walker step.
+//
+// Section 4.3 (Generating D): Philox4x32-10 words -> Box-Muller N(0,1) entries
+//   of H, one thread per (walker, quad of coordinates); D = P H through the
+//   factored projector (Section 3.2): d = h - A_E^T (L L^T)^{-1} (A_E h),
+//   with L the Cholesky factor of A_E A_E^T.
+// Section 4.4 (Finding the line sets) in the recompute formulation of
+//   Lemma 4.2: A X and A D are tiled over (64 rows x 64 walkers) blocks, the
+//   slack b - A X and the ratios are formed in registers, and every block
+//   folds its rows into per-walker (lambda_min, lambda_max) with ordered-key
+//   atomics, so the m x z ratio matrix never reaches memory.
+// Section 4.5 (Choosing samples): one warp per walker draws theta uniformly
+//   on the chord and moves x += theta d.
+// These kernels serve MHAR_FP64 (T = double) and MHAR_FP32 (T = float; points
+// kept as FP32 pairs).  The tensor-core mode is in kernels_tc.cu.
+#include <cfloat>
+#include <cmath>
+#include <cuda_fp16.h>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+
+namespace mhar {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double neg_inf() { return -__longlong_as_double(0x7ff0000000000000ll); }
+__device__ __forceinline__ double pos_inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+// ---- Section 4.3: direction entries ----------------------------------------
+// mode 0: FP64 -> D64; mode 1: FP32 -> D32; mode 2: FP32 -> FP16 hi/lo split
+// (when there is no projection) or FP32 scratch D32 (projection follows).
+__global__ void directions_kernel(int mode, int split, uint64_t seed, const uint64_t* step_ptr,
+                                  int j, uint32_t walker0, int z, int n, int n_ld, int k_pad,
+                                  double* D64, float* D32, __half* Dh, __half* Dl) {
+  const int quads = (n + 3) >> 2;
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(z) * quads) return;
+  const int k = static_cast<int>(idx / quads);
+  const int q = static_cast<int>(idx - static_cast<long long>(k) * quads);
+  const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+  const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k),
+                            static_cast<uint32_t>(q), kStreamDirection);
+  const int i0 = 4 * q;
+  if (mode == 0) {
+    double v[4];
+    box_muller_f64(open_unit_f64(w.x), open_unit_f64(w.y), v[0], v[1]);
+    box_muller_f64(open_unit_f64(w.z), open_unit_f64(w.w), v[2], v[3]);
+    double* dst = D64 + static_cast<size_t>(k) * n_ld + i0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (i0 + e < n) dst[e] = v[e];
+  } else {
+    float v[4];
+    box_muller_f32(w.x, w.y, v[0], v[1]);
+    box_muller_f32(w.z, w.w, v[2], v[3]);
+    if (mode == 2 && split) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (i0 + e < n) {
+          const __half h = __float2half_rn(v[e]);
+          const __half l = __float2half_rn(v[e] - __half2float(h));
+          Dh[static_cast<size_t>(k) * k_pad + i0 + e] = h;
+          Dl[static_cast<size_t>(k) * k_pad + i0 + e] = l;
+        }
+      }
+    } else {
+      float* dst = D32 + static_cast<size_t>(k) * n_ld + i0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (i0 + e < n) dst[e] = v[e];
+    }
+  }
+}
+
+// ---- Section 3.2: d = P h with P in factored form --------------------------
+// One warp per walker; mE <= 32.  y = A_E h (warp reductions), c solves
+// L L^T c = y (lane 0, FP64), d = h - A_E^T c.
+// FP32 modes: the direction actually used (FP32, or the FP16 hi + lo pair of
+// the tensor-core mode) leaves a rounding residual A_E d of order 1e-7 |d|.
+// Its exact FP64 correction c' = (A_E A_E^T)^{-1} A_E d is stored per walker
+// (corr), and the point update moves along d - A_E^T c', so A_E x = b_E holds
+// to FP64 rounding instead of drifting by theta * 1e-7 per iteration.
+__device__ __forceinline__ void cholesky_solve(const double* L, int mE, double* c) {
+  for (int r = 0; r < mE; ++r) {
+    double s = c[r];
+    for (int q = 0; q < r; ++q) s -= L[r * mE + q] * c[q];
+    c[r] = s / L[r * mE + r];
+  }
+  for (int r = mE - 1; r >= 0; --r) {
+    double s = c[r];
+    for (int q = r + 1; q < mE; ++q) s -= L[q * mE + r] * c[q];
+    c[r] = s / L[r * mE + r];
+  }
+}
+
+template <typename T>
+__global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
+                                  const double* __restrict__ AE64, const double* __restrict__ L,
+                                  T* D, int split, int k_pad, __half* Dh, __half* Dl,
+                                  float* corr) {
+  __shared__ double cbuf[kThreads / 32][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (kThreads / 32) + warp;
+  if (k >= z) return;
+  T* h = D + static_cast<size_t>(k) * n_ld;
+  double* c = cbuf[warp];
+  for (int e = 0; e < mE; ++e) {
+    T acc = T(0);
+    for (int i = lane; i < n; i += 32) acc += AE[static_cast<size_t>(e) * n_ld + i] * h[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) c[e] = static_cast<double>(acc);
+  }
+  __syncwarp();
+  if (lane == 0) cholesky_solve(L, mE, c);
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    T s = h[i];
+    for (int e = 0; e < mE; ++e) s -= AE[static_cast<size_t>(e) * n_ld + i] * static_cast<T>(c[e]);
+    if (split) {
+      const float v = static_cast<float>(s);
+      const __half hh = __float2half_rn(v);
+      Dh[static_cast<size_t>(k) * k_pad + i] = hh;
+      Dl[static_cast<size_t>(k) * k_pad + i] = __float2half_rn(v - __half2float(hh));
+    } else {
+      h[i] = s;
+    }
+  }
+  if (corr == nullptr) return;
+  __syncwarp();
+  // Residual of the rounded direction, in FP64.
+  for (int e = 0; e < mE; ++e) {
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      double v;
+      if (split)
+        v = static_cast<double>(__half2float(Dh[static_cast<size_t>(k) * k_pad + i])) +
+            static_cast<double>(__half2float(Dl[static_cast<size_t>(k) * k_pad + i]));
+      else
+        v = static_cast<double>(h[i]);
+      acc += AE64[static_cast<size_t>(e) * n_ld + i] * v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) c[e] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    cholesky_solve(L, mE, c);
+    for (int e = 0; e < mE; ++e) corr[static_cast<size_t>(k) * mE + e] = static_cast<float>(c[e]);
+  }
+}
+
+// ---- Section 4.4: line sets, recompute formulation ---------------------------
+template <typename T>
+struct ChordTile;
+template <>
+struct ChordTile<double> { static constexpr int BK = 8; };
+template <>
+struct ChordTile<float> { static constexpr int BK = 16; };
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+chord_simt_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ X,
+                  const T* __restrict__ D, int m, int n_ld, int z,
+                  unsigned long long* key_lo, unsigned long long* key_hi, int* status) {
+  constexpr int BK = ChordTile<T>::BK;
+  __shared__ T As[BK][64];
+  __shared__ T Xs[BK][64];
+  __shared__ T Ds[BK][64];
+  __shared__ T red_lo[16][64];
+  __shared__ T red_hi[16][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * 64, w0 = blockIdx.y * 64;
+  T accS[4][4], accG[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { accS[r][c] = T(0); accG[r][c] = T(0); }
+
+  for (int k0 = 0; k0 < n_ld; k0 += BK) {
+    for (int e = tid; e < 64 * BK; e += kThreads) {
+      const int r = e / BK, c = e - r * BK;
+      const int gi = i0 + r, gw = w0 + r;
+      As[c][r] = gi < m ? A[static_cast<size_t>(gi) * n_ld + k0 + c] : T(0);
+      Xs[c][r] = gw < z ? X[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
+      Ds[c][r] = gw < z ? D[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], xv[4], dv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { xv[c] = Xs[kk][tx + 16 * c]; dv[c] = Ds[kk][tx + 16 * c]; }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          accS[r][c] += a[r] * xv[c];
+          accG[r][c] += a[r] * dv[c];
+        }
+    }
+    __syncthreads();
+  }
+
+  bool bad = false;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T lo = static_cast<T>(neg_inf()), hi = static_cast<T>(pos_inf());
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int gi = i0 + ty * 4 + r;
+      if (gi >= m) continue;
+      T s = b[gi] - accS[r][c];
+      const T g = accG[r][c];
+      if (!isfinite(s) || !isfinite(g)) { bad = true; continue; }
+      if (s < T(0)) s = T(0);
+      if (g > T(0)) {
+        const T lam = s / g;
+        hi = lam < hi ? lam : hi;
+      } else if (g < T(0)) {
+        const T lam = s / g;
+        lo = lam > lo ? lam : lo;
+      }
+    }
+    red_lo[ty][tx + 16 * c] = lo;
+    red_hi[ty][tx + 16 * c] = hi;
+  }
+  __syncthreads();
+  if (tid < 64) {
+    T lo = red_lo[0][tid], hi = red_hi[0][tid];
+#pragma unroll
+    for (int t = 1; t < 16; ++t) {
+      lo = red_lo[t][tid] > lo ? red_lo[t][tid] : lo;
+      hi = red_hi[t][tid] < hi ? red_hi[t][tid] : hi;
+    }
+    const int gw = w0 + tid;
+    if (gw < z) {
+      if (!isinf(lo)) atomicMax(&key_lo[gw], f64_key(static_cast<double>(lo)));
+      if (!isinf(hi)) atomicMin(&key_hi[gw], f64_key(static_cast<double>(hi)));
+    }
+  }
+  if (bad) atomicOr(status, MHAR_ST_NONFINITE);
+}
+
+// ---- Section 4.5: theta on the chord, x += theta d ---------------------------
+// mode 0: FP64 points; mode 1: FP32-pair points with FP32 directions.
+__global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr, int j,
+                              uint32_t walker0, int z, int n, int n_ld,
+                              unsigned long long* key_lo, unsigned long long* key_hi,
+                              double* lmin, double* lmax, double* theta, int* status,
+                              unsigned long long* counters, double* X64, const double* D64,
+                              float* Xhi, float* Xlo, const float* D32, int mE,
+                              const float* AE32, const float* corr) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (kThreads / 32) + warp;
+  if (k >= z) return;
+  double t = 0.0;
+  if (lane == 0) {
+    const double L = f64_unkey(key_lo[k]);
+    const double H = f64_unkey(key_hi[k]);
+    key_lo[k] = f64_key(neg_inf());
+    key_hi[k] = f64_key(pos_inf());
+    if (isinf(L) || isinf(H)) {
+      atomicOr(status, MHAR_ST_UNBOUNDED);
+      atomicAdd(&counters[1], 1ull);
+    } else if (L > H) {
+      atomicOr(status, MHAR_ST_STALL);
+      atomicAdd(&counters[0], 1ull);
+    } else {
+      const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+      const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k), 0u, kStreamChord);
+      const double u = open_unit_f64(w.x);
+      t = L + u * (H - L);
+      if (mode != 0) t = static_cast<double>(static_cast<float>(t));
+    }
+    lmin[k] = L;
+    lmax[k] = H;
+    theta[k] = t;
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  const size_t row = static_cast<size_t>(k) * n_ld;
+  if (mode == 0) {
+    for (int i = lane; i < n; i += 32) X64[row + i] += t * D64[row + i];
+  } else {
+    const float tf = static_cast<float>(t);
+    for (int i = lane; i < n; i += 32) df_axpy(Xhi[row + i], Xlo[row + i], tf, D32[row + i]);
+    if (corr != nullptr && tf != 0.0f) {
+      for (int i = lane; i < n; i += 32) {
+        float dlt = 0.0f;
+        for (int e = 0; e < mE; ++e)
+          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
+        Xlo[row + i] = fmaf(-tf, dlt, Xlo[row + i]);
+      }
+    }
+  }
+}
+
+__global__ void advance_kernel(uint64_t* step_ptr, int steps) { *step_ptr += steps; }
+
+__global__ void emit_kernel(int mode, int z, int n, int n_ld, const double* X64, const float* Xhi,
+                            const float* Xlo, double* out) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(z) * n) return;
+  const int k = static_cast<int>(idx / n), i = static_cast<int>(idx - static_cast<long long>(k) * n);
+  const size_t src = static_cast<size_t>(k) * n_ld + i;
+  out[idx] = mode == 0 ? X64[src] : static_cast<double>(Xhi[src]) + static_cast<double>(Xlo[src]);
+}
+
+__global__ void set_points_kernel(int mode, int z, int n, int n_ld, const double* Xin, double* X64,
+                                  float* Xhi, float* Xlo) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(z) * n) return;
+  const int k = static_cast<int>(idx / n), i = static_cast<int>(idx - static_cast<long long>(k) * n);
+  const size_t dst = static_cast<size_t>(k) * n_ld + i;
+  const double v = Xin[idx];
+  if (mode == 0) {
+    X64[dst] = v;
+  } else {
+    const float h = static_cast<float>(v);
+    Xhi[dst] = h;
+    Xlo[dst] = static_cast<float>(v - static_cast<double>(h));
+  }
+}
+
+__device__ __forceinline__ double load_point(int mode, const double* X64, const float* Xhi,
+                                             const float* Xlo, size_t idx) {
+  return mode == 0 ? X64[idx] : static_cast<double>(Xhi[idx]) + static_cast<double>(Xlo[idx]);
+}
+
+// FP64 feasibility check: max over (walker, row) of a_i x - b_i, and
+// max over walkers of |A_E x - b_E|_inf.  One block per (row block, walker).
+__global__ void check_kernel(int mode, int m, int n, int n_ld, int mE, const double* A,
+                             const double* b, const double* AE, const double* bE,
+                             const double* X64, const float* Xhi, const float* Xlo,
+                             unsigned long long* out_keys) {
+  extern __shared__ double xs[];
+  const int k = blockIdx.y;
+  const size_t row = static_cast<size_t>(k) * n_ld;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = load_point(mode, X64, Xhi, Xlo, row + i);
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += A[static_cast<size_t>(r) * n_ld + i] * xs[i];
+    atomicMax(&out_keys[0], f64_key(s - b[r]));
+  }
+  if (blockIdx.x == 0 && r < mE) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += AE[static_cast<size_t>(r) * n_ld + i] * xs[i];
+    atomicMax(&out_keys[1], f64_key(fabs(s - bE[r])));
+  }
+}
+
+// Mixed mode: S[i][k] = b_i - a_i x_k recomputed in FP64 from the FP32-pair
+// points (tiles of 64 rows x 64 walkers, K staged through shared memory), and
+// the largest change |S_old - S_new| recorded (drift).
+__global__ void __launch_bounds__(kThreads)
+refresh_simt_kernel(int m, int n_ld, int z, int z_ld, const double* __restrict__ A,
+                    const double* __restrict__ b, const float* __restrict__ Xhi,
+                    const float* __restrict__ Xlo, float* S, unsigned long long* drift_key) {
+  constexpr int BK = 8;
+  __shared__ double As[BK][64];
+  __shared__ double Xs[BK][64];
+  __shared__ double red[kThreads];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * 64, w0 = blockIdx.y * 64;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int k0 = 0; k0 < n_ld; k0 += BK) {
+    for (int e = tid; e < 64 * BK; e += kThreads) {
+      const int r = e / BK, c = e - r * BK;
+      const int gi = i0 + r, gw = w0 + r;
+      As[c][r] = gi < m ? A[static_cast<size_t>(gi) * n_ld + k0 + c] : 0.0;
+      const size_t xi = static_cast<size_t>(gw) * n_ld + k0 + c;
+      Xs[c][r] = gw < z ? static_cast<double>(Xhi[xi]) + static_cast<double>(Xlo[xi]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], xv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xv[c] = Xs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * xv[c];
+    }
+    __syncthreads();
+  }
+  double drift = 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gi = i0 + ty * 4 + r;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gw = w0 + tx + 16 * c;
+      if (gw >= z) continue;
+      const double s = b[gi] - acc[r][c];
+      float* sp = S + static_cast<size_t>(gi) * z_ld + gw;
+      drift = fmax(drift, fabs(static_cast<double>(*sp) - s));
+      *sp = static_cast<float>(s);
+    }
+  }
+  red[tid] = drift;
+  __syncthreads();
+  for (int st = kThreads / 2; st > 0; st >>= 1) {
+    if (tid < st) red[tid] = fmax(red[tid], red[tid + st]);
+    __syncthreads();
+  }
+  if (tid == 0) atomicMax(drift_key, f64_key(red[0]));
+}
+
+// Mixed mode with equalities: x <- x - A_E^T (A_E A_E^T)^{-1} (A_E x - b_E),
+// in FP64 on the FP32-pair points (removes drift of the equality residual).
+__global__ void reproject_kernel(int z, int n, int n_ld, int mE, const double* AE,
+                                 const double* bE, const double* L, float* Xhi, float* Xlo) {
+  __shared__ double cbuf[kThreads / 32][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (kThreads / 32) + warp;
+  if (k >= z) return;
+  const size_t row = static_cast<size_t>(k) * n_ld;
+  double* c = cbuf[warp];
+  for (int e = 0; e < mE; ++e) {
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32)
+      acc += AE[static_cast<size_t>(e) * n_ld + i] *
+             (static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) c[e] = acc - bE[e];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int r = 0; r < mE; ++r) {
+      double s = c[r];
+      for (int q = 0; q < r; ++q) s -= L[r * mE + q] * c[q];
+      c[r] = s / L[r * mE + r];
+    }
+    for (int r = mE - 1; r >= 0; --r) {
+      double s = c[r];
+      for (int q = r + 1; q < mE; ++q) s -= L[q * mE + r] * c[q];
+      c[r] = s / L[r * mE + r];
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    double v = static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]);
+    for (int e = 0; e < mE; ++e) v -= AE[static_cast<size_t>(e) * n_ld + i] * c[e];
+    const float h = static_cast<float>(v);
+    Xhi[row + i] = h;
+    Xlo[row + i] = static_cast<float>(v - static_cast<double>(h));
+  }
+}
+
+// Tensor-core operands: per-row power-of-two scale s_i with max_k |a_ik| / s_i
+// in [0.5, 1), then A/s split into FP16 hi + lo.  FP32 copy of b padded.
+__global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, const double* A,
+                                  const double* b, __half* Ah, __half* Al, float* row_scale,
+                                  float* bS) {
+  const int r = blockIdx.x;
+  if (r >= m_pad) return;
+  __shared__ double red[kThreads];
+  double mx = 0.0;
+  if (r < m)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      mx = fmax(mx, fabs(A[static_cast<size_t>(r) * n_ld + i]));
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  mx = red[0];
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  const double scale = ldexp(1.0, e);
+  if (threadIdx.x == 0) {
+    row_scale[r] = r < m ? static_cast<float>(scale) : 1.0f;
+    bS[r] = r < m ? static_cast<float>(b[r]) : 0.0f;
+  }
+  for (int i = threadIdx.x; i < k_pad; i += blockDim.x) {
+    float v = 0.0f;
+    if (r < m && i < n) v = static_cast<float>(A[static_cast<size_t>(r) * n_ld + i] / scale);
+    const __half h = __float2half_rn(v);
+    Ah[static_cast<size_t>(r) * k_pad + i] = h;
+    Al[static_cast<size_t>(r) * k_pad + i] = __float2half_rn(v - __half2float(h));
+  }
+}
+
+__global__ void init_keys_kernel(int z, unsigned long long* key_lo, unsigned long long* key_hi) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < z) {
+    key_lo[k] = f64_key(neg_inf());
+    key_hi[k] = f64_key(pos_inf());
+  }
+}
+
+inline int blocks_for(long long count, int per_block) {
+  return static_cast<int>((count + per_block - 1) / per_block);
+}
+
+}  // namespace
+
+cudaError_t launch_directions(mhar_ctx* c, int j) {
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : (c->opts.precision == MHAR_FP32 ? 1 : 2);
+  const long long threads = static_cast<long long>(c->z) * ((c->n + 3) / 4);
+  directions_kernel<<<blocks_for(threads, kThreads), kThreads, 0, c->stream>>>(
+      mode, c->mE == 0 ? 1 : 0, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld,
+      c->k_pad, c->d.D64, c->d.D32, c->d.Dh, c->d.Dl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_projection(mhar_ctx* c) {
+  const int grid = blocks_for(c->z, kThreads / 32);
+  if (c->opts.precision == MHAR_FP64) {
+    projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
+        c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
+        nullptr, nullptr);
+  } else {
+    const int split = c->opts.precision == MHAR_MIXED_F16X3 ? 1 : 0;
+    projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
+        c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
+        c->d.Dh, c->d.Dl, c->d.corr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chord_simt(mhar_ctx* c) {
+  dim3 grid(blocks_for(c->m, 64), blocks_for(c->z, 64));
+  if (c->opts.precision == MHAR_FP64) {
+    chord_simt_kernel<double><<<grid, kThreads, 0, c->stream>>>(
+        c->d.A64, c->d.b64, c->d.X64, c->d.D64, c->m, c->n_ld, c->z, c->d.key_lo, c->d.key_hi,
+        c->d.status);
+  } else {
+    chord_simt_kernel<float><<<grid, kThreads, 0, c->stream>>>(
+        c->d.A32, c->d.b32, c->d.Xhi, c->d.D32, c->m, c->n_ld, c->z, c->d.key_lo, c->d.key_hi,
+        c->d.status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_simt(mhar_ctx* c, int j) {
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
+  update_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
+      mode, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->d.key_lo,
+      c->d.key_hi, c->d.lmin, c->d.lmax, c->d.theta, c->d.status, c->d.counters, c->d.X64,
+      c->d.D64, c->d.Xhi, c->d.Xlo, c->d.D32, c->mE, c->d.AE32, c->d.corr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(mhar_ctx* c, int steps) {
+  advance_kernel<<<1, 1, 0, c->stream>>>(c->d.step, steps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(mhar_ctx* c, double* out_device) {
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
+  const long long count = static_cast<long long>(c->z) * c->n;
+  emit_kernel<<<blocks_for(count, kThreads), kThreads, 0, c->stream>>>(
+      mode, c->z, c->n, c->n_ld, c->d.X64, c->d.Xhi, c->d.Xlo, out_device);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_points(mhar_ctx* c, const double* X_dev) {
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
+  const long long count = static_cast<long long>(c->z) * c->n;
+  if (X_dev)
+    set_points_kernel<<<blocks_for(count, kThreads), kThreads, 0, c->stream>>>(
+        mode, c->z, c->n, c->n_ld, X_dev, c->d.X64, c->d.Xhi, c->d.Xlo);
+  init_keys_kernel<<<blocks_for(c->z, kThreads), kThreads, 0, c->stream>>>(c->z, c->d.key_lo,
+                                                                         c->d.key_hi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check(mhar_ctx* c) {
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
+  const int block = 128;
+  const int rows = c->m > c->mE ? c->m : c->mE;
+  dim3 grid(blocks_for(rows, block), c->z);
+  check_kernel<<<grid, block, sizeof(double) * c->n, c->stream>>>(
+      mode, c->m, c->n, c->n_ld, c->mE, c->d.A64, c->d.b64, c->d.AE64, c->d.bE64, c->d.X64,
+      c->d.Xhi, c->d.Xlo, reinterpret_cast<unsigned long long*>(c->d.check));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_simt(mhar_ctx* c) {
+  const int z_ld = (c->z + 127) / 128 * 128;
+  dim3 grid(blocks_for(c->m, 64), blocks_for(c->z, 64));
+  refresh_simt_kernel<<<grid, kThreads, 0, c->stream>>>(
+      c->m, c->n_ld, c->z, z_ld, c->d.A64, c->d.b64, c->d.Xhi, c->d.Xlo, c->d.S,
+      reinterpret_cast<unsigned long long*>(c->d.check) + 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reproject(mhar_ctx* c) {
+  reproject_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
+      c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.bE64, c->d.Lchol, c->d.Xhi, c->d.Xlo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_tc_operands(mhar_ctx* c) {
+  prepare_tc_kernel<<<c->m_pad, kThreads, 0, c->stream>>>(c->m, c->n, c->n_ld, c->m_pad, c->k_pad,
+                                                         c->d.A64, c->d.b64, c->d.Ah, c->d.Al,
+                                                         c->d.row_scale, c->d.bS);
+  return cudaGetLastError();
+}
+
+}  // namespace mhar

@@ -1,0 +1,714 @@
+// kernels_tc.cu -- the fused tensor-core walker step (MHAR_MIXED_F16X3 mode).
+//
+// One launch performs, for every walker, Sections 4.4 and 4.5 of the paper on
+// the stored slack S = b - A X:
+//   G = D A^T           tcgen05.mma kind::f16 (FP16 hi/lo split operands,
+//                       3 products hi.hi + hi.lo + lo.hi, FP32 accumulation
+//                       in tensor memory; TMA-staged 128B-swizzled tiles)
+//   lambda_max = min{ s_i / g_i : g_i > 0 },  lambda_min = max{ s_i / g_i : g_i < 0 }
+//                       folded in registers straight out of tensor memory --
+//                       the m x z ratio matrix never reaches memory
+//   theta = lambda_min + u (lambda_max - lambda_min),  u from Philox stream 1
+//   S -= G diag(theta),  X += D diag(theta)   (X as FP32 pairs)
+//
+// Work decomposition.  The MMA's M dimension is the walkers (128 per CTA, one
+// walker per tensor-memory lane, so every thread owns one walker and reduces
+// its chord sequentially), N is the constraint rows (128 per tile), K is the
+// dimension n.  The rows of A are split over the CTAs of a thread-block
+// cluster (up to 4 tiles = 512 tensor-memory columns per CTA); the partial
+// chords are combined through distributed shared memory, so each CTA can
+// update its own slack rows while G is still in tensor memory.
+//
+// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// tensor-memory owner, warps 2..9 = epilogue (two warps per 32-lane quarter,
+// each taking half of every tile's columns).
+//
+// Every mbarrier wait is bounded (about 2 s of clock); on expiry the kernel
+// records a timeout in the error word, stops waiting and still runs
+// through every cluster barrier, so no peer is left waiting.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+
+namespace mhar {
+namespace {
+
+constexpr int kStages = 3;
+constexpr int kWalkers = 128;                         // MMA M
+constexpr int kRowsTile = 128;                        // MMA N per tile
+constexpr int kMaxTilesPerCta = 4;                    // 512 TMEM columns
+constexpr int kOperandBytes = 128 * kTcKChunk * 2;    // one 128 x 64 FP16 tile = 16 KB
+constexpr int kStageBytes = 4 * kOperandBytes;        // A hi, A lo, W hi, W lo
+constexpr int kEpiWarps = 16;                         // 4 per TMEM lane quarter
+constexpr int kThreadsTc = (2 + kEpiWarps) * 32;
+constexpr long long kTimeoutCycles = 4000000000ll;    // ~2 s at 2 GHz
+constexpr int kErrTimeout = 1;
+
+enum : int { kModeChord = 0, kModeRefresh = 1 };
+
+struct TcParams {
+  int mode;                 // kModeChord | kModeRefresh
+  const float* row_scale;   // m_pad: A[i,:] = row_scale[i] (Ah + Al)[i,:]
+  const float* bS;          // m_pad: b in FP32 (refresh)
+  const float* wscale;      // z_ld: X[k,:] = wscale[k] (Xh + Xl)[k,:] (refresh)
+  float* S;                 // m_pad x z_ld
+  float* Xhi;               // z x n_ld
+  float* Xlo;
+  const __half* Dh;         // z_ld x k_pad
+  const __half* Dl;
+  const float* AE32;        // mE x n_ld (equality rows) or null
+  const float* corr;        // z x mE residual corrections or null
+  double* lmin;
+  double* lmax;
+  double* theta;
+  int* status;
+  unsigned long long* counters;
+  int* err;
+  unsigned long long* drift_key;
+  const uint64_t* step_ptr;
+  uint64_t seed;
+  int j;
+  uint32_t walker0;
+  int m, n, n_ld, z, z_ld, kdim, k_chunks, tiles_per_cta, m_tiles, mE;
+};
+
+struct SmemTail {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t tfull[kMaxTilesPerCta];
+  uint32_t tmem_base;
+  int timed_out;
+  float part_lo[4][kWalkers];
+  float part_hi[4][kWalkers];
+  float cta_lo[kWalkers];
+  float cta_hi[kWalkers];
+  float theta[kWalkers];
+  float scale[kMaxTilesPerCta * kRowsTile];
+  float brow[kMaxTilesPerCta * kRowsTile];
+};
+
+constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + sizeof(SmemTail);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and flags the CTA) once the budget is spent or
+// an earlier wait of this CTA already expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* timed_out,
+                                          int* err) {
+  const uint32_t a = smem_u32(bar);
+  if (mbar_try_wait(a, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(a, parity)) {
+    if (*timed_out) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
+      *timed_out = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand stored as 128-byte
+// rows with the 128B swizzle (8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= static_cast<uint64_t>(1) << 16;                    // leading byte offset (unused)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;            // stride byte offset: 8 rows
+  d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                    // 128B swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = FP16, D = FP32, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__device__ __forceinline__ float ld_dsmem_f32(const float* local, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+}
+
+// Slack of 32 consecutive rows for one walker (rows are z_ld floats apart,
+// so each load is one coalesced 128-byte line across the warp's walkers).
+__device__ __forceinline__ void load_s32(const float* src, size_t stride, float (&v)[32]) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __ldcg(src + static_cast<size_t>(c) * stride);
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1)
+walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+                 const __grid_constant__ CUtensorMap tm_wh, const __grid_constant__ CUtensorMap tm_wl,
+                 const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  SmemTail* tail = reinterpret_cast<SmemTail*>(base + kStages * kStageBytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = blockIdx.x;       // cluster rank: the cluster spans grid.x
+  const uint32_t csize = gridDim.x;
+  const int strip = blockIdx.y;
+  const int tile0 = static_cast<int>(rank) * p.tiles_per_cta;
+  int ntiles = p.m_tiles - tile0;
+  ntiles = ntiles < 0 ? 0 : (ntiles > p.tiles_per_cta ? p.tiles_per_cta : ntiles);
+  const int row_base = tile0 * kRowsTile;
+  const bool refresh = p.mode == kModeRefresh;
+
+  // ---- set-up -------------------------------------------------------------
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&tail->full[s], 1);
+      mbar_init(&tail->empty[s], 1);
+    }
+    for (int t = 0; t < kMaxTilesPerCta; ++t) mbar_init(&tail->tfull[t], 1);
+    tail->timed_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    const uint32_t cols = p.tiles_per_cta <= 1 ? 128u : (p.tiles_per_cta == 2 ? 256u : 512u);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int r = threadIdx.x; r < p.tiles_per_cta * kRowsTile; r += blockDim.x) {
+    const bool in = r < ntiles * kRowsTile;
+    tail->scale[r] = in ? p.row_scale[row_base + r] : 1.0f;
+    tail->brow[r] = in ? p.bS[row_base + r] : 0.0f;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tail->tmem_base;
+  volatile int* timed_out = &tail->timed_out;
+
+  if (warp == 0) {
+    // ---- TMA producer -------------------------------------------------------
+    if (lane == 0) {
+      int it = 0;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        for (int kc = 0; kc < p.k_chunks; ++kc, ++it) {
+          const int s = it % kStages;
+          if (it >= kStages) mbar_wait(&tail->empty[s], ((it / kStages) - 1) & 1, timed_out, p.err);
+          uint8_t* st = base + s * kStageBytes;
+          mbar_expect_tx(&tail->full[s], kStageBytes);
+          const int x = kc * kTcKChunk;
+          const int yr = row_base + nt * kRowsTile;
+          const int yw = strip * kWalkers;
+          tma_load_2d(st, &tm_ah, &tail->full[s], x, yr);
+          tma_load_2d(st + kOperandBytes, &tm_al, &tail->full[s], x, yr);
+          tma_load_2d(st + 2 * kOperandBytes, &tm_wh, &tail->full[s], x, yw);
+          tma_load_2d(st + 3 * kOperandBytes, &tm_wl, &tail->full[s], x, yw);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer: G = (Wh + Wl)(Ah + Al)^T, four FP16 products ------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      int it = 0;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        const uint32_t d_tmem = tmem + static_cast<uint32_t>(nt * kRowsTile);
+        for (int kc = 0; kc < p.k_chunks; ++kc, ++it) {
+          const int s = it % kStages;
+          mbar_wait(&tail->full[s], (it / kStages) & 1, timed_out, p.err);
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + s * kStageBytes);
+          const uint32_t a_hi = st, a_lo = st + kOperandBytes;
+          const uint32_t w_hi = st + 2 * kOperandBytes, w_lo = st + 3 * kOperandBytes;
+          int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
+          ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
+          for (int ks = 0; ks < ks_n; ++ks) {
+            const uint32_t off = static_cast<uint32_t>(ks * kTcK * 2);  // 32 bytes per K step
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_f16(d_tmem, sw128_desc(w_hi + off), sw128_desc(a_hi + off), idesc, acc);
+            mma_f16(d_tmem, sw128_desc(w_hi + off), sw128_desc(a_lo + off), idesc, 1u);
+            mma_f16(d_tmem, sw128_desc(w_lo + off), sw128_desc(a_hi + off), idesc, 1u);
+            mma_f16(d_tmem, sw128_desc(w_lo + off), sw128_desc(a_lo + off), idesc, 1u);
+          }
+          mma_commit(&tail->empty[s]);
+        }
+        mma_commit(&tail->tfull[nt]);
+      }
+    }
+    __syncwarp();
+  } else if (refresh) {
+    // ---- refresh epilogue: S = b - A X from tensor memory ----------------------
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    const float ws = p.wscale[k];
+    float drift = 0.0f;
+    for (int nt = 0; nt < ntiles; ++nt) {
+      const int col = nt * kRowsTile + cg * 32;
+      float* Srow = p.S + static_cast<size_t>(row_base + col) * p.z_ld + k;
+      float old[32];
+      load_s32(Srow, p.z_ld, old);
+      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
+      tc_fence_after();
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float g[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(col + 16 * half), g);
+        if (k < p.z) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int cc = 16 * half + c;
+            const float sn = fmaf(-g[c] * tail->scale[col + cc], ws, tail->brow[col + cc]);
+            drift = fmaxf(drift, fabsf(sn - old[cc]));
+            __stcg(Srow + static_cast<size_t>(cc) * p.z_ld, sn);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
+    if (lane == 0 && drift > 0.0f) atomicMax(p.drift_key, f64_key(static_cast<double>(drift)));
+  } else {
+    // ---- chord epilogue, pass 1: partial (lambda_min, lambda_max) ---------------
+    const int e = warp - 2;
+    const int q = warp & 3;       // TMEM lane quarter this warp may access
+    const int cg = e >> 2;        // which 32-column group of each tile
+    const int wl = q * 32 + lane; // walker within the strip
+    const int k = strip * kWalkers + wl;
+    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    float s_cur[32], s_nxt[32];
+    if (ntiles > 0)
+      load_s32(p.S + static_cast<size_t>(row_base + cg * 32) * p.z_ld + k, p.z_ld, s_cur);
+    for (int nt = 0; nt < ntiles; ++nt) {
+      const int col = nt * kRowsTile + cg * 32;
+      if (nt + 1 < ntiles)
+        load_s32(p.S + static_cast<size_t>(row_base + col + kRowsTile) * p.z_ld + k, p.z_ld, s_nxt);
+      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
+      tc_fence_after();
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float g[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                      static_cast<uint32_t>(col + 16 * half), g);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float gg = g[c] * tail->scale[col + 16 * half + c];
+          const float sv = s_cur[16 * half + c];
+          const float ss = fmaxf(sv, 0.0f);
+          chk = fmaf(gg, 0.0f, chk);
+          chk = fmaf(sv, 0.0f, chk);
+          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
+          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
+          const float bnd = gg > 0.0f ? hi : lo;
+          if (ss < bnd * gg) {
+            const float r = __fdividef(ss, gg);
+            if (gg > 0.0f) hi = r; else lo = r;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) s_cur[c] = s_nxt[c];
+    }
+    tail->part_lo[cg][wl] = lo;
+    tail->part_hi[cg][wl] = hi;
+    const int bad = !(chk == 0.0f);
+    epi_bar();
+    if (cg == 0) {
+      tail->cta_lo[wl] = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
+      tail->cta_hi[wl] = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
+    }
+    if (bad) atomicOr(p.status, MHAR_ST_NONFINITE);
+  }
+
+  // Partials of every CTA of the cluster are now in shared memory.
+  cluster_sync_all();
+
+  if (warp >= 2 && !refresh) {
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    if (cg == 0) {
+      float L = -INFINITY, H = INFINITY;
+      for (uint32_t r = 0; r < csize; ++r) {
+        L = fmaxf(L, ld_dsmem_f32(&tail->cta_lo[wl], r));
+        H = fminf(H, ld_dsmem_f32(&tail->cta_hi[wl], r));
+      }
+      float t = 0.0f;
+      int flag = 0;
+      if (k < p.z) {
+        if (isinf(L) || isinf(H)) {
+          flag = MHAR_ST_UNBOUNDED;
+        } else if (L > H) {
+          flag = MHAR_ST_STALL;
+        } else {
+          const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+          const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
+                                    kStreamChord);
+          const double u = open_unit_f64(w.x);
+          t = static_cast<float>(static_cast<double>(L) +
+                                 u * (static_cast<double>(H) - static_cast<double>(L)));
+        }
+        if (rank == 0) {
+          p.lmin[k] = L;
+          p.lmax[k] = H;
+          p.theta[k] = t;
+          if (flag) {
+            atomicOr(p.status, flag);
+            atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+          }
+        }
+      }
+      tail->theta[wl] = t;
+    }
+    epi_bar();
+    // ---- chord epilogue, pass 2: S -= G diag(theta) -----------------------------
+    const float t = tail->theta[wl];
+    if (__any_sync(0xffffffffu, t != 0.0f)) {
+      float s_cur[32], s_nxt[32];
+      if (ntiles > 0)
+        load_s32(p.S + static_cast<size_t>(row_base + cg * 32) * p.z_ld + k, p.z_ld, s_cur);
+      for (int nt = 0; nt < ntiles; ++nt) {
+        const int col = nt * kRowsTile + cg * 32;
+        if (nt + 1 < ntiles)
+          load_s32(p.S + static_cast<size_t>(row_base + col + kRowsTile) * p.z_ld + k, p.z_ld, s_nxt);
+        float* Srow = p.S + static_cast<size_t>(row_base + col) * p.z_ld + k;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float g[16];
+          // tcgen05.ld is warp-collective: every lane joins, lanes with theta == 0 skip the update.
+          tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                        static_cast<uint32_t>(col + 16 * half), g);
+          if (t != 0.0f) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              __stcg(Srow + static_cast<size_t>(16 * half + c) * p.z_ld,
+                     fmaf(-t, g[c] * tail->scale[col + 16 * half + c], s_cur[16 * half + c]));
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) s_cur[c] = s_nxt[c];
+      }
+    }
+    // ---- X += D diag(theta) on this CTA's slice of coordinates ---------------
+    const int slice = (p.n + static_cast<int>(csize) - 1) / static_cast<int>(csize);
+    const int i_begin = static_cast<int>(rank) * slice;
+    const int i_end = min(p.n, i_begin + slice);
+    for (int w = e; w < kWalkers; w += kEpiWarps) {
+      const int kk = strip * kWalkers + w;
+      const float tw = tail->theta[w];
+      if (kk >= p.z || tw == 0.0f) continue;
+      const size_t xr = static_cast<size_t>(kk) * p.n_ld;
+      const size_t dr = static_cast<size_t>(kk) * (p.k_chunks * kTcKChunk);
+      for (int i = i_begin + lane; i < i_end; i += 32) {
+        const float d = __half2float(p.Dh[dr + i]) + __half2float(p.Dl[dr + i]);
+        df_axpy(p.Xhi[xr + i], p.Xlo[xr + i], tw, d);
+        if (p.corr != nullptr) {
+          // Exact null-space correction of the rounded direction (see projection).
+          float dlt = 0.0f;
+          for (int q2 = 0; q2 < p.mE; ++q2)
+            dlt = fmaf(p.AE32[static_cast<size_t>(q2) * p.n_ld + i],
+                       p.corr[static_cast<size_t>(kk) * p.mE + q2], dlt);
+          p.Xlo[xr + i] = fmaf(-tw, dlt, p.Xlo[xr + i]);
+        }
+      }
+    }
+  }
+
+  // Peers may still be reading this CTA's partials; all tensor-memory reads
+  // are complete once every thread is here.
+  tc_fence_before();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    const uint32_t cols = p.tiles_per_cta <= 1 ? 128u : (p.tiles_per_cta == 2 ? 256u : 512u);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols)
+                 : "memory");
+  }
+}
+
+// Refresh operands: each walker's point x = hi + lo scaled by a power of two
+// 2^e (max |x_i| 2^-e in [0.5, 1)) and split into FP16 hi + lo.
+__global__ void split_points_kernel(int z, int z_ld, int n, int n_ld, int k_pad, const float* Xhi,
+                                    const float* Xlo, __half* Xh, __half* Xl, float* wscale) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (k >= z_ld) return;
+  float mx = 0.0f;
+  if (k < z)
+    for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(Xhi[static_cast<size_t>(k) * n_ld + i]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  int ex = 0;
+  if (mx > 0.0f) frexpf(mx, &ex);
+  const float inv = ldexpf(1.0f, -ex);
+  if (lane == 0) wscale[k] = ldexpf(1.0f, ex);
+  for (int i = lane; i < k_pad; i += 32) {
+    float v = 0.0f;
+    if (k < z && i < n)
+      v = (Xhi[static_cast<size_t>(k) * n_ld + i] + Xlo[static_cast<size_t>(k) * n_ld + i]) * inv;
+    const __half h = __float2half_rn(v);
+    Xh[static_cast<size_t>(k) * k_pad + i] = h;
+    Xl[static_cast<size_t>(k) * k_pad + i] = __float2half_rn(v - __half2float(h));
+  }
+}
+
+struct TcPlan {
+  CUtensorMap ah, al, dh, dl, xh, xl;
+  int C = 1;
+  int tiles_per_cta = 1;
+  int m_tiles = 1;
+  int strips = 1;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 2D FP16 map over a (rows x cols) row-major array with 128 x 64 boxes and
+// the 128-byte swizzle the MMA descriptors expect.
+bool make_map(CUtensorMap* map, const void* ptr, int cols, int rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kTcKChunk), 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j) {
+  TcParams p;
+  p.mode = mode;
+  p.row_scale = c->d.row_scale;
+  p.bS = c->d.bS;
+  p.wscale = c->d.wscale;
+  p.S = c->d.S;
+  p.Xhi = c->d.Xhi;
+  p.Xlo = c->d.Xlo;
+  p.Dh = c->d.Dh;
+  p.Dl = c->d.Dl;
+  p.AE32 = c->d.AE32;
+  p.corr = c->d.corr;
+  p.lmin = c->d.lmin;
+  p.lmax = c->d.lmax;
+  p.theta = c->d.theta;
+  p.status = c->d.status;
+  p.counters = c->d.counters;
+  p.err = c->d.status + 1;
+  p.drift_key = reinterpret_cast<unsigned long long*>(c->d.check) + 2;
+  p.step_ptr = c->d.step;
+  p.seed = c->opts.seed;
+  p.j = j;
+  p.walker0 = c->opts.walker0;
+  p.m = c->m;
+  p.n = c->n;
+  p.n_ld = c->n_ld;
+  p.z = c->z;
+  p.z_ld = plan->strips * kWalkers;
+  p.kdim = c->kdim;
+  p.k_chunks = c->k_pad / kTcKChunk;
+  p.tiles_per_cta = plan->tiles_per_cta;
+  p.m_tiles = plan->m_tiles;
+  p.mE = c->mE;
+  return p;
+}
+
+cudaError_t launch_walker_tc(mhar_ctx* c, int mode, int j) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  const TcParams p = make_params(c, plan, mode, j);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan->C, plan->strips, 1);
+  cfg.blockDim = dim3(kThreadsTc, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = plan->C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (mode == kModeRefresh)
+    return cudaLaunchKernelEx(&cfg, walker_tc_kernel, plan->ah, plan->al, plan->xh, plan->xl, p);
+  return cudaLaunchKernelEx(&cfg, walker_tc_kernel, plan->ah, plan->al, plan->dh, plan->dl, p);
+}
+
+}  // namespace
+
+int tc_plan_create(mhar_ctx* c) {
+  auto* plan = new TcPlan();
+  plan->m_tiles = c->m_pad / kRowsTile;
+  plan->tiles_per_cta = plan->m_tiles < kMaxTilesPerCta ? plan->m_tiles : kMaxTilesPerCta;
+  plan->C = (plan->m_tiles + plan->tiles_per_cta - 1) / plan->tiles_per_cta;
+  const int z_ld = (c->z + kWalkers - 1) / kWalkers * kWalkers;
+  plan->strips = z_ld / kWalkers;
+  if (plan->C > 16) {
+    delete plan;
+    snprintf(c->err, sizeof(c->err),
+             "tensor-core mode covers m <= 8192 inequality rows (got m=%d)", c->m);
+    return MHAR_E_UNSUPPORTED;
+  }
+  if (!make_map(&plan->ah, c->d.Ah, c->k_pad, c->m_pad) ||
+      !make_map(&plan->al, c->d.Al, c->k_pad, c->m_pad) ||
+      !make_map(&plan->dh, c->d.Dh, c->k_pad, z_ld) || !make_map(&plan->dl, c->d.Dl, c->k_pad, z_ld) ||
+      !make_map(&plan->xh, c->d.Xh, c->k_pad, z_ld) || !make_map(&plan->xl, c->d.Xl, c->k_pad, z_ld)) {
+    delete plan;
+    snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed");
+    return MHAR_E_CUDA;
+  }
+  cudaError_t e = cudaFuncSetAttribute(walker_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess && plan->C > 8)
+    e = cudaFuncSetAttribute(walker_tc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) {
+    delete plan;
+    snprintf(c->err, sizeof(c->err), "tensor-core kernel attributes: %s", cudaGetErrorString(e));
+    return MHAR_E_CUDA;
+  }
+  c->tc = plan;
+  return MHAR_OK;
+}
+
+void tc_plan_destroy(mhar_ctx* c) {
+  delete static_cast<TcPlan*>(c->tc);
+  c->tc = nullptr;
+}
+
+cudaError_t launch_chord_tc(mhar_ctx* c, int j) { return launch_walker_tc(c, kModeChord, j); }
+
+cudaError_t launch_refresh_tc(mhar_ctx* c) {
+  const int z_ld = (c->z + kWalkers - 1) / kWalkers * kWalkers;
+  split_points_kernel<<<(z_ld + 7) / 8, 256, 0, c->stream>>>(c->z, z_ld, c->n, c->n_ld, c->k_pad,
+                                                          c->d.Xhi, c->d.Xlo, c->d.Xh, c->d.Xl,
+                                                          c->d.wscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_walker_tc(c, kModeRefresh, 0);
+}
+
+}  // namespace mhar

@@ -1,0 +1,715 @@
+// mhar_api.cu -- host side of libmhar: the C ABI declared in include/mhar.h.
+//
+// The context owns every device buffer (cudaMalloc), a stream, and two CUDA
+// graphs of the per-iteration kernels (a chunk of graph_chunk iterations and a
+// single iteration) that are replayed by mhar_run.  Kernels read the
+// iteration index from a device counter, so one captured graph serves every
+// replay; the last node of each graph advances the counter.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+
+namespace {
+
+constexpr int kMaxEqualities = 32;
+
+void set_err(mhar_ctx* c, const char* fmt, ...) {
+  if (!c) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof(c->err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(mhar_ctx* c, cudaError_t e, const char* what) {
+  set_err(c, "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();  // a failed launch must not be reported again by a later check
+  return MHAR_E_CUDA;
+}
+
+#define MHAR_CUDA(call, what)                    \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+unsigned long long host_key(double f) {
+  unsigned long long u;
+  std::memcpy(&u, &f, sizeof(u));
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+double host_unkey(unsigned long long k) {
+  const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  double f;
+  std::memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+template <typename T>
+int dmalloc(mhar_ctx* c, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+  e = cudaMemsetAsync(*p, 0, count * sizeof(T), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+  return MHAR_OK;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+bool mixed(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_F16X3; }
+
+void free_all(mhar_ctx* c) {
+  mhar::DeviceBuffers& d = c->d;
+  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.AE64, d.AE32, d.bE64, d.Lchol, d.Ah, d.Al,
+                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale,
+                  d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
+                  d.emit, d.check};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d = mhar::DeviceBuffers();
+}
+
+// Projector set-up on the device (Section 3.2): G = A_E A_E^T in FP64, then
+// its Cholesky factor L (lower, row-major).  ok[0] = 0 if G is not positive
+// definite.
+__global__ void proj_setup_kernel(int mE, int n, int n_ld, const double* AE, double* L, int* ok) {
+  __shared__ double G[kMaxEqualities * kMaxEqualities];
+  for (int e = threadIdx.x; e < mE * mE; e += blockDim.x) {
+    const int r = e / mE, q = e % mE;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += AE[static_cast<size_t>(r) * n_ld + i] * AE[static_cast<size_t>(q) * n_ld + i];
+    G[e] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    for (int jc = 0; jc < mE && good; ++jc) {
+      double dsum = G[jc * mE + jc];
+      for (int k = 0; k < jc; ++k) dsum -= G[jc * mE + k] * G[jc * mE + k];
+      if (!(dsum > 0.0)) { good = 0; break; }
+      const double ljj = sqrt(dsum);
+      G[jc * mE + jc] = ljj;
+      for (int i = jc + 1; i < mE; ++i) {
+        double s = G[i * mE + jc];
+        for (int k = 0; k < jc; ++k) s -= G[i * mE + k] * G[jc * mE + k];
+        G[i * mE + jc] = s / ljj;
+      }
+    }
+    for (int i = 0; i < mE; ++i)
+      for (int q = 0; q < mE; ++q) L[i * mE + q] = q <= i ? G[i * mE + q] : 0.0;
+    ok[0] = good;
+  }
+}
+
+__global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const double* x0,
+                                        double* X64, float* Xhi, float* Xlo) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(z) * n) return;
+  const int k = static_cast<int>(idx / n), i = static_cast<int>(idx - static_cast<long long>(k) * n);
+  const size_t dst = static_cast<size_t>(k) * n_ld + i;
+  const double v = x0[i];
+  if (mode == 0) {
+    X64[dst] = v;
+  } else {
+    const float h = static_cast<float>(v);
+    Xhi[dst] = h;
+    Xlo[dst] = static_cast<float>(v - static_cast<double>(h));
+  }
+}
+
+int kernels_per_iteration(const mhar_ctx* c) {
+  return 1 + (c->mE > 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
+}
+
+int enqueue_iterations(mhar_ctx* c, int count) {
+  for (int j = 0; j < count; ++j) {
+    MHAR_CUDA(mhar::launch_directions(c, j), "directions kernel");
+    if (c->mE > 0) MHAR_CUDA(mhar::launch_projection(c), "projection kernel");
+    if (mixed(c)) {
+      MHAR_CUDA(mhar::launch_chord_tc(c, j), "tensor-core chord kernel");
+    } else {
+      MHAR_CUDA(mhar::launch_chord_simt(c), "chord kernel");
+      MHAR_CUDA(mhar::launch_update_simt(c, j), "update kernel");
+    }
+  }
+  MHAR_CUDA(mhar::launch_advance(c, count), "advance kernel");
+  return MHAR_OK;
+}
+
+int capture(mhar_ctx* c, int count, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  MHAR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+  int rc = enqueue_iterations(c, count);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc != MHAR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  return MHAR_OK;
+}
+
+int advance(mhar_ctx* c, int64_t count) {
+  if (c->opts.graph_chunk <= 0) {
+    while (count > 0) {
+      const int now = count > (1 << 20) ? (1 << 20) : static_cast<int>(count);
+      int rc = enqueue_iterations(c, now);
+      if (rc != MHAR_OK) return rc;
+      c->launches += static_cast<int64_t>(now) * kernels_per_iteration(c) + 1;
+      count -= now;
+    }
+    return MHAR_OK;
+  }
+  if (!c->g_one) {
+    int rc = capture(c, 1, &c->g_one);
+    if (rc != MHAR_OK) return rc;
+    rc = capture(c, c->opts.graph_chunk, &c->g_chunk);
+    if (rc != MHAR_OK) return rc;
+    c->graph_len = c->opts.graph_chunk;
+    c->launches_one = kernels_per_iteration(c) + 1;
+    c->launches_chunk = static_cast<int64_t>(c->graph_len) * kernels_per_iteration(c) + 1;
+  }
+  while (count >= c->graph_len) {
+    MHAR_CUDA(cudaGraphLaunch(c->g_chunk, c->stream), "graph launch");
+    c->launches += c->launches_chunk;
+    count -= c->graph_len;
+  }
+  while (count-- > 0) {
+    MHAR_CUDA(cudaGraphLaunch(c->g_one, c->stream), "graph launch");
+    c->launches += c->launches_one;
+  }
+  return MHAR_OK;
+}
+
+int refresh(mhar_ctx* c) {
+  if (c->mE > 0) {
+    MHAR_CUDA(mhar::launch_reproject(c), "re-projection kernel");
+    ++c->launches;
+  }
+  if (c->opts.refresh_fp64) {
+    MHAR_CUDA(mhar::launch_refresh_simt(c), "slack refresh kernel");
+    ++c->launches;
+  } else {
+    MHAR_CUDA(mhar::launch_refresh_tc(c), "tensor-core slack refresh");
+    c->launches += 2;
+  }
+  c->since_refresh = 0;
+  return MHAR_OK;
+}
+
+int emit_to(mhar_ctx* c, double* out, bool out_device) {
+  ++c->launches;
+  if (out_device) {
+    MHAR_CUDA(mhar::launch_emit(c, out), "emit kernel");
+  } else {
+    MHAR_CUDA(mhar::launch_emit(c, c->d.emit), "emit kernel");
+    MHAR_CUDA(cudaMemcpyAsync(out, c->d.emit, sizeof(double) * c->z * c->n, cudaMemcpyDeviceToHost,
+                              c->stream),
+              "sample copy");
+  }
+  return MHAR_OK;
+}
+
+int reset_drift(mhar_ctx* c) {
+  const unsigned long long k0 = host_key(0.0);
+  MHAR_CUDA(cudaMemcpyAsync(reinterpret_cast<unsigned long long*>(c->d.check) + 2, &k0, sizeof(k0),
+                            cudaMemcpyHostToDevice, c->stream),
+            "drift reset");
+  return MHAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mhar_default_opts(mhar_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->seed = 0;
+  o->precision = MHAR_FP64;
+  o->refresh_k = 64;
+  o->out_on_device = 0;
+  o->walker0 = 0;
+  o->stream = nullptr;
+  o->graph_chunk = 16;
+}
+
+const char* mhar_strerror(int code) {
+  switch (code) {
+    case MHAR_OK: return "MHAR_OK";
+    case MHAR_E_ARG: return "MHAR_E_ARG";
+    case MHAR_E_X0_INFEASIBLE: return "MHAR_E_X0_INFEASIBLE";
+    case MHAR_E_UNBOUNDED: return "MHAR_E_UNBOUNDED";
+    case MHAR_E_NONFINITE: return "MHAR_E_NONFINITE";
+    case MHAR_E_CUDA: return "MHAR_E_CUDA";
+    case MHAR_E_RANK: return "MHAR_E_RANK";
+    case MHAR_E_UNSUPPORTED: return "MHAR_E_UNSUPPORTED";
+    default: return "MHAR_E_UNKNOWN";
+  }
+}
+
+const char* mhar_last_error(const mhar_ctx* c) {
+  if (!c) return "null context";
+  return c->err[0] ? c->err : "no error";
+}
+
+void mhar_destroy(mhar_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
+  if (c->g_one) cudaGraphExecDestroy(c->g_one);
+  if (c->tc) mhar::tc_plan_destroy(c);
+  free_all(c);
+  if (c->stream && c->stream != static_cast<cudaStream_t>(c->opts.stream))
+    cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static int create_impl(mhar_ctx* c, const double* A, const double* b, const double* AE,
+                       const double* bE, const double* x0) {
+  const int m = c->m, n = c->n, mE = c->mE, z = c->z;
+  // Device must be sm_103 (the only architecture this library is built for).
+  MHAR_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
+  cudaDeviceProp prop;
+  MHAR_CUDA(cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    set_err(c, "device %d is sm_%d%d; libmhar is built for sm_103a only", c->device, prop.major,
+            prop.minor);
+    return MHAR_E_CUDA;
+  }
+  if (c->opts.stream) {
+    c->stream = static_cast<cudaStream_t>(c->opts.stream);
+  } else {
+    MHAR_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream create");
+  }
+
+  // Strict interiority of x0 and the equality residual, in FP64 on the host
+  // (a one-off input check, not part of the sampling path).
+  double worst = INFINITY;
+  for (int i = 0; i < m; ++i) {
+    double s = b[i];
+    for (int k = 0; k < n; ++k) s -= A[static_cast<size_t>(i) * n + k] * x0[k];
+    worst = s < worst ? s : worst;
+  }
+  if (!(worst > 0.0)) {
+    set_err(c, "x0 is not strictly inside A x <= b (min slack %.3e)", worst);
+    return MHAR_E_X0_INFEASIBLE;
+  }
+  if (mE > 0) {
+    double bmax = 0.0, res = 0.0;
+    for (int e = 0; e < mE; ++e) {
+      double s = -bE[e];
+      for (int k = 0; k < n; ++k) s += AE[static_cast<size_t>(e) * n + k] * x0[k];
+      res = std::fmax(res, std::fabs(s));
+      bmax = std::fmax(bmax, std::fabs(bE[e]));
+    }
+    if (res > 1e-9 * (1.0 + bmax)) {
+      set_err(c, "x0 violates A_E x = b_E (residual %.3e)", res);
+      return MHAR_E_X0_INFEASIBLE;
+    }
+  }
+
+  c->n_ld = round_up(n, 32);
+  c->k_pad = round_up(n, mhar::kTcKChunk);
+  c->kdim = round_up(n, mhar::kTcK);
+  c->m_pad = round_up(m, mhar::kTcM);
+  const int z_ld = round_up(z, 128);
+  const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
+  mhar::DeviceBuffers& d = c->d;
+  int rc;
+
+  // Problem data, padded to the leading dimensions.
+  std::vector<double> Ap(static_cast<size_t>(m) * c->n_ld, 0.0);
+  for (int i = 0; i < m; ++i)
+    std::memcpy(&Ap[static_cast<size_t>(i) * c->n_ld], A + static_cast<size_t>(i) * n,
+                sizeof(double) * n);
+  if ((rc = dmalloc(c, &d.A64, Ap.size())) || (rc = dmalloc(c, &d.b64, m))) return rc;
+  MHAR_CUDA(cudaMemcpyAsync(d.A64, Ap.data(), sizeof(double) * Ap.size(), cudaMemcpyHostToDevice,
+                            c->stream), "copy A");
+  MHAR_CUDA(cudaMemcpyAsync(d.b64, b, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream),
+            "copy b");
+  if (c->opts.precision == MHAR_FP32) {
+    std::vector<float> Af(Ap.begin(), Ap.end());
+    std::vector<float> bf(b, b + m);
+    if ((rc = dmalloc(c, &d.A32, Af.size())) || (rc = dmalloc(c, &d.b32, m))) return rc;
+    MHAR_CUDA(cudaMemcpyAsync(d.A32, Af.data(), sizeof(float) * Af.size(), cudaMemcpyHostToDevice,
+                              c->stream), "copy A32");
+    MHAR_CUDA(cudaMemcpyAsync(d.b32, bf.data(), sizeof(float) * m, cudaMemcpyHostToDevice,
+                              c->stream), "copy b32");
+    MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
+  }
+  if (mE > 0) {
+    std::vector<double> AEp(static_cast<size_t>(mE) * c->n_ld, 0.0);
+    for (int e = 0; e < mE; ++e)
+      std::memcpy(&AEp[static_cast<size_t>(e) * c->n_ld], AE + static_cast<size_t>(e) * n,
+                  sizeof(double) * n);
+    std::vector<float> AEf(AEp.begin(), AEp.end());
+    if ((rc = dmalloc(c, &d.AE64, AEp.size())) || (rc = dmalloc(c, &d.AE32, AEf.size())) ||
+        (rc = dmalloc(c, &d.bE64, mE)) || (rc = dmalloc(c, &d.Lchol, static_cast<size_t>(mE) * mE)))
+      return rc;
+    MHAR_CUDA(cudaMemcpyAsync(d.AE64, AEp.data(), sizeof(double) * AEp.size(),
+                              cudaMemcpyHostToDevice, c->stream), "copy AE");
+    MHAR_CUDA(cudaMemcpyAsync(d.AE32, AEf.data(), sizeof(float) * AEf.size(),
+                              cudaMemcpyHostToDevice, c->stream), "copy AE32");
+    MHAR_CUDA(cudaMemcpyAsync(d.bE64, bE, sizeof(double) * mE, cudaMemcpyHostToDevice, c->stream),
+              "copy bE");
+    MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
+  }
+
+  // Walker state and bookkeeping.
+  if ((rc = dmalloc(c, &d.key_lo, z)) || (rc = dmalloc(c, &d.key_hi, z)) ||
+      (rc = dmalloc(c, &d.lmin, z)) || (rc = dmalloc(c, &d.lmax, z)) ||
+      (rc = dmalloc(c, &d.theta, z)) || (rc = dmalloc(c, &d.status, 2)) ||
+      (rc = dmalloc(c, &d.counters, 2)) || (rc = dmalloc(c, &d.step, 1)) ||
+      (rc = dmalloc(c, &d.emit, static_cast<size_t>(z) * n)) || (rc = dmalloc(c, &d.check, 4)))
+    return rc;
+  const size_t zn = static_cast<size_t>(z) * c->n_ld;
+  if (mode == 0) {
+    if ((rc = dmalloc(c, &d.X64, zn)) || (rc = dmalloc(c, &d.D64, zn))) return rc;
+  } else {
+    if ((rc = dmalloc(c, &d.Xhi, zn)) || (rc = dmalloc(c, &d.Xlo, zn))) return rc;
+    if (c->opts.precision == MHAR_FP32 || mE > 0)
+      if ((rc = dmalloc(c, &d.D32, zn))) return rc;
+    if (mE > 0 && (rc = dmalloc(c, &d.corr, static_cast<size_t>(z) * mE))) return rc;
+  }
+  if (mixed(c)) {
+    const size_t opnd = static_cast<size_t>(c->m_pad) * c->k_pad;
+    const size_t dsz = static_cast<size_t>(z_ld) * c->k_pad;
+    if ((rc = dmalloc(c, &d.Ah, opnd)) || (rc = dmalloc(c, &d.Al, opnd)) ||
+        (rc = dmalloc(c, &d.row_scale, c->m_pad)) || (rc = dmalloc(c, &d.bS, c->m_pad)) ||
+        (rc = dmalloc(c, &d.Dh, dsz)) || (rc = dmalloc(c, &d.Dl, dsz)) ||
+        (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld)) ||
+        (rc = dmalloc(c, &d.Xh, dsz)) || (rc = dmalloc(c, &d.Xl, dsz)) ||
+        (rc = dmalloc(c, &d.wscale, z_ld)))
+      return rc;
+  }
+
+  // Projector factor on the device.
+  if (mE > 0) {
+    int* ok = d.status + 1;
+    proj_setup_kernel<<<1, 256, 0, c->stream>>>(mE, n, c->n_ld, d.AE64, d.Lchol, ok);
+    MHAR_CUDA(cudaGetLastError(), "projector set-up kernel");
+    int okh = 0;
+    MHAR_CUDA(cudaMemcpyAsync(&okh, ok, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy");
+    MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
+    MHAR_CUDA(cudaMemsetAsync(ok, 0, sizeof(int), c->stream), "memset");
+    if (!okh) {
+      set_err(c, "A_E A_E^T is not positive definite (rank-deficient equalities)");
+      return MHAR_E_RANK;
+    }
+  }
+
+  // Algorithm 2: every column of X starts at x0.
+  double* x0d = nullptr;
+  if ((rc = dmalloc(c, &x0d, n))) return rc;
+  MHAR_CUDA(cudaMemcpyAsync(x0d, x0, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream),
+            "copy x0");
+  broadcast_points_kernel<<<(static_cast<long long>(z) * n + 255) / 256, 256, 0, c->stream>>>(
+      mode, z, n, c->n_ld, x0d, d.X64, d.Xhi, d.Xlo);
+  cudaError_t e = cudaGetLastError();
+  cudaStreamSynchronize(c->stream);
+  cudaFree(x0d);
+  if (e != cudaSuccess) return cuda_fail(c, e, "broadcast kernel");
+  MHAR_CUDA(mhar::launch_set_points(c, nullptr), "init keys");
+
+  if (mixed(c)) {
+    MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
+    if ((rc = mhar::tc_plan_create(c))) return rc;
+    if ((rc = reset_drift(c)) || (rc = refresh(c))) return rc;
+  }
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "create sync");
+  return MHAR_OK;
+}
+
+int mhar_create(const double* A, const double* b, int m, int n, const double* AE, const double* bE,
+                int mE, const double* x0, int z, const mhar_opts* opts, mhar_ctx** out) {
+  if (!out) return MHAR_E_ARG;
+  *out = nullptr;
+  mhar_ctx* c = new (std::nothrow) mhar_ctx();
+  if (!c) return MHAR_E_ARG;
+  if (opts) c->opts = *opts; else mhar_default_opts(&c->opts);
+  if (z <= 0) z = (m > n ? m : n) + 1;  // Algorithm 2's default padding
+  c->m = m; c->n = n; c->mE = mE; c->z = z;
+  int rc = MHAR_OK;
+  if (!A || !b || !x0 || m < 1 || n < 1 || mE < 0 || (mE > 0 && (!AE || !bE))) {
+    set_err(c, "bad pointer or size (m=%d n=%d mE=%d)", m, n, mE);
+    rc = MHAR_E_ARG;
+  } else if (mE > kMaxEqualities || mE >= n) {
+    set_err(c, "this build handles 0 <= mE <= %d and mE < n (got mE=%d, n=%d)", kMaxEqualities,
+            mE, n);
+    rc = MHAR_E_UNSUPPORTED;
+  } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_F16X3 ||
+             c->opts.refresh_k < 0 || c->opts.graph_chunk < 0) {
+    set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d)", c->opts.precision,
+            c->opts.refresh_k, c->opts.graph_chunk);
+    rc = MHAR_E_ARG;
+  } else if (!all_finite(A, static_cast<size_t>(m) * n) || !all_finite(b, m) ||
+             !all_finite(x0, n) || (mE > 0 && (!all_finite(AE, static_cast<size_t>(mE) * n) ||
+                                               !all_finite(bE, mE)))) {
+    set_err(c, "non-finite input");
+    rc = MHAR_E_NONFINITE;
+  } else {
+    rc = create_impl(c, A, b, AE, bE, x0);
+  }
+  if (rc != MHAR_OK) {
+    // Keep the message: hand back a context that only reports the error.
+    char msg[512];
+    std::memcpy(msg, c->err, sizeof(msg));
+    mhar_destroy(c);
+    fprintf(stderr, "mhar_create: %s (%s)\n", msg, mhar_strerror(rc));
+    return rc;
+  }
+  *out = c;
+  return MHAR_OK;
+}
+
+int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
+  if (!c) return MHAR_E_ARG;
+  if (steps < 0 || thin < 0) {
+    set_err(c, "steps and thin must be >= 0");
+    return MHAR_E_ARG;
+  }
+  const int64_t nsamp = thin > 0 ? steps / thin : 0;
+  if (nsamp > 0 && !out) {
+    set_err(c, "out is NULL but %lld samples are due", static_cast<long long>(nsamp));
+    return MHAR_E_ARG;
+  }
+  if (steps == 0) return MHAR_OK;
+  MHAR_CUDA(cudaMemsetAsync(c->d.status, 0, 2 * sizeof(int), c->stream), "status reset");
+  int rc;
+  if (mixed(c) && (rc = reset_drift(c))) return rc;
+  int64_t done = 0, emitted = 0;
+  const int64_t k = mixed(c) ? c->opts.refresh_k : 0;
+  while (done < steps) {
+    int64_t adv = steps - done;
+    if (thin > 0) adv = std::min<int64_t>(adv, thin - (done % thin));
+    if (k > 0) adv = std::min<int64_t>(adv, k - c->since_refresh);
+    if ((rc = advance(c, adv))) return rc;
+    done += adv;
+    c->step += static_cast<uint64_t>(adv);
+    if (k > 0) {
+      c->since_refresh += adv;
+      if (c->since_refresh >= k && (rc = refresh(c))) return rc;
+    }
+    if (thin > 0 && done % thin == 0 && emitted < nsamp) {
+      if ((rc = emit_to(c, out + static_cast<size_t>(emitted) * c->z * c->n,
+                        c->opts.out_on_device != 0)))
+        return rc;
+      ++emitted;
+    }
+  }
+  int st[2] = {0, 0};
+  MHAR_CUDA(cudaMemcpyAsync(st, c->d.status, sizeof(st), cudaMemcpyDeviceToHost, c->stream),
+            "status copy");
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "run sync");
+  if (mixed(c)) {
+    unsigned long long kd = 0;
+    MHAR_CUDA(cudaMemcpy(&kd, reinterpret_cast<unsigned long long*>(c->d.check) + 2, sizeof(kd),
+                         cudaMemcpyDeviceToHost), "drift copy");
+    c->last_drift = host_unkey(kd);
+  }
+  c->status_bits |= st[0];
+  if (st[1]) {
+    set_err(c, "tensor-core pipeline wait timed out");
+    return MHAR_E_CUDA;
+  }
+  if (st[0] & MHAR_ST_NONFINITE) {
+    set_err(c, "non-finite slack or direction met");
+    return MHAR_E_NONFINITE;
+  }
+  if (st[0] & MHAR_ST_UNBOUNDED) {
+    set_err(c, "a walker met a chord open on one side: the body is unbounded");
+    return MHAR_E_UNBOUNDED;
+  }
+  return MHAR_OK;
+}
+
+int mhar_get_state(const mhar_ctx* cc, double* X, uint64_t* step) {
+  mhar_ctx* c = const_cast<mhar_ctx*>(cc);
+  if (!c) return MHAR_E_ARG;
+  if (X) {
+    int rc = emit_to(c, X, false);
+    if (rc) return rc;
+  }
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "state sync");
+  if (step) *step = c->step;
+  return MHAR_OK;
+}
+
+int mhar_set_state(mhar_ctx* c, const double* X, uint64_t step) {
+  if (!c || !X) return MHAR_E_ARG;
+  const size_t zn = static_cast<size_t>(c->z) * c->n;
+  if (!all_finite(X, zn)) {
+    set_err(c, "non-finite point");
+    return MHAR_E_NONFINITE;
+  }
+  MHAR_CUDA(cudaMemcpyAsync(c->d.emit, X, sizeof(double) * zn, cudaMemcpyHostToDevice, c->stream),
+            "copy X");
+  MHAR_CUDA(mhar::launch_set_points(c, c->d.emit), "set points kernel");
+  MHAR_CUDA(cudaMemcpyAsync(c->d.step, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream),
+            "copy step");
+  c->step = step;
+  if (mixed(c)) {
+    int rc;
+    if ((rc = refresh(c))) return rc;
+  }
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "set_state sync");
+  return MHAR_OK;
+}
+
+int mhar_get_chord(const mhar_ctx* cc, double* lmin, double* lmax, double* theta) {
+  mhar_ctx* c = const_cast<mhar_ctx*>(cc);
+  if (!c) return MHAR_E_ARG;
+  const size_t bytes = sizeof(double) * c->z;
+  if (lmin) MHAR_CUDA(cudaMemcpyAsync(lmin, c->d.lmin, bytes, cudaMemcpyDeviceToHost, c->stream), "copy");
+  if (lmax) MHAR_CUDA(cudaMemcpyAsync(lmax, c->d.lmax, bytes, cudaMemcpyDeviceToHost, c->stream), "copy");
+  if (theta) MHAR_CUDA(cudaMemcpyAsync(theta, c->d.theta, bytes, cudaMemcpyDeviceToHost, c->stream), "copy");
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "chord sync");
+  return MHAR_OK;
+}
+
+int mhar_get_stats(const mhar_ctx* c, mhar_stats* s) {
+  if (!c || !s) return MHAR_E_ARG;
+  std::memset(s, 0, sizeof(*s));
+  unsigned long long cnt[2] = {0, 0};
+  cudaError_t e = cudaMemcpy(cnt, c->d.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return MHAR_E_CUDA;
+  s->step = c->step;
+  s->walker_steps = static_cast<int64_t>(c->step) * c->z;
+  s->stalls = static_cast<int64_t>(cnt[0]);
+  s->unbounded = static_cast<int64_t>(cnt[1]);
+  s->status_bits = c->status_bits;
+  s->precision = c->opts.precision;
+  s->refresh_drift = c->last_drift;
+  s->max_violation = c->max_violation;
+  s->eq_residual = c->eq_residual;
+  s->kernel_launches = c->launches;
+  return MHAR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Captures `body` into a graph, replays it once between two events on the
+// context's stream and returns the elapsed device milliseconds.
+template <typename F>
+cudaError_t time_graph(mhar_ctx* c, F body, float* ms) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t eb = body();
+    e = cudaStreamEndCapture(c->stream, &g);
+    if (eb != cudaSuccess) e = eb;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(ge, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
+  if (!c || !ms || iters < 1 || iters > 4096) return MHAR_E_ARG;
+  // (1) `iters` real iterations, replayed back to back from one graph.
+  auto full = [&]() -> cudaError_t {
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = mhar::launch_directions(c, it);
+      if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
+      if (e == cudaSuccess) {
+        if (mixed(c)) {
+          e = mhar::launch_chord_tc(c, it);
+        } else {
+          e = mhar::launch_chord_simt(c);
+          if (e == cudaSuccess) e = mhar::launch_update_simt(c, it);
+        }
+      }
+      if (e != cudaSuccess) return e;
+    }
+    return mhar::launch_advance(c, iters);
+  };
+  // (2) the direction kernels alone, `iters` times for the current iteration
+  // (idempotent: they rewrite the same directions).
+  auto dirs = [&]() -> cudaError_t {
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = mhar::launch_directions(c, 0);
+      if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  float t_full = 0.f, t_dir = 0.f, t_ref = 0.f;
+  cudaError_t e = time_graph(c, full, &t_full);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
+  c->launches += static_cast<int64_t>(iters) * kernels_per_iteration(c) + 1;
+  c->step += static_cast<uint64_t>(iters);
+  e = time_graph(c, dirs, &t_dir);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
+  c->launches += static_cast<int64_t>(iters) * (1 + (c->mE > 0 ? 1 : 0));
+  if (mixed(c)) {
+    auto ref = [&]() -> cudaError_t {
+      cudaError_t e2 = cudaSuccess;
+      if (c->mE > 0) e2 = mhar::launch_reproject(c);
+      if (e2 == cudaSuccess)
+        e2 = c->opts.refresh_fp64 ? mhar::launch_refresh_simt(c) : mhar::launch_refresh_tc(c);
+      return e2;
+    };
+    e = time_graph(c, ref, &t_ref);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
+    c->launches += (c->mE > 0 ? 1 : 0) + (c->opts.refresh_fp64 ? 1 : 2);
+    c->since_refresh = 0;
+  }
+  ms[0] = t_dir / iters;
+  ms[1] = (t_full - t_dir) / iters;
+  ms[2] = t_ref;
+  return MHAR_OK;
+}
+
+int mhar_check(mhar_ctx* c, mhar_stats* s) {
+  if (!c) return MHAR_E_ARG;
+  const unsigned long long init[2] = {host_key(-INFINITY), host_key(0.0)};
+  MHAR_CUDA(cudaMemcpyAsync(c->d.check, init, sizeof(init), cudaMemcpyHostToDevice, c->stream),
+            "check init");
+  MHAR_CUDA(mhar::launch_check(c), "check kernel");
+  unsigned long long res[2];
+  MHAR_CUDA(cudaMemcpyAsync(res, c->d.check, sizeof(res), cudaMemcpyDeviceToHost, c->stream),
+            "check copy");
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "check sync");
+  c->max_violation = host_unkey(res[0]);
+  c->eq_residual = c->mE > 0 ? host_unkey(res[1]) : 0.0;
+  return s ? mhar_get_stats(c, s) : MHAR_OK;
+}
+
+}  // extern "C"

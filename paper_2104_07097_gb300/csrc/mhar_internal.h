@@ -1,0 +1,112 @@
+// mhar_internal.h -- the context layout and the kernel launchers shared by the
+// library's translation units.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include "../../include/mhar.h"
+
+namespace mhar {
+
+// Tile geometry of the tensor-core path (fixed by the kernel design).
+constexpr int kTcM = 128;        // rows of A per MMA tile (TMEM lanes)
+constexpr int kTcKChunk = 64;    // FP16 elements per 128-byte swizzled row chunk
+constexpr int kTcK = 16;         // K of one kind::f16 MMA
+
+struct DeviceBuffers {
+  // Problem (row-major, zero padded to the leading dimensions below).
+  double* A64 = nullptr;   // m x n_ld
+  double* b64 = nullptr;   // m
+  float* A32 = nullptr;    // m x n_ld (FP32 mode)
+  float* b32 = nullptr;    // m
+  double* AE64 = nullptr;  // mE x n_ld
+  float* AE32 = nullptr;   // mE x n_ld
+  double* bE64 = nullptr;  // mE
+  double* Lchol = nullptr; // mE x mE, lower Cholesky factor of A_E A_E^T
+  // Tensor-core operands: A split into FP16 hi/lo after a per-row power-of-two
+  // scale; rows padded to m_pad, columns to k_pad.
+  __half* Ah = nullptr;    // m_pad x k_pad
+  __half* Al = nullptr;    // m_pad x k_pad
+  float* row_scale = nullptr; // m_pad: A[i,:] = row_scale[i] * (Ah + Al)[i,:]
+  float* bS = nullptr;     // m_pad (FP32 b, 0 beyond m)
+
+  // Walker state.
+  double* X64 = nullptr;   // z x n_ld          (FP64 mode)
+  float* Xhi = nullptr;    // z x n_ld          (FP32 / mixed: double-float)
+  float* Xlo = nullptr;    // z x n_ld
+  double* D64 = nullptr;   // z x n_ld          (FP64 mode)
+  float* D32 = nullptr;    // z x n_ld          (FP32 mode; mixed: pre-projection scratch)
+  __half* Dh = nullptr;    // z x k_pad         (mixed)
+  __half* Dl = nullptr;    // z x k_pad         (mixed)
+  float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack, walkers contiguous)
+  float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix)
+  __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
+  __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
+  float* wscale = nullptr; // z_ld              (mixed: power-of-two scale of each walker)
+
+  // Chord bookkeeping.
+  unsigned long long* key_lo = nullptr;  // z: ordered key of lambda_min (atomic max)
+  unsigned long long* key_hi = nullptr;  // z: ordered key of lambda_max (atomic min)
+  double* lmin = nullptr;  // z
+  double* lmax = nullptr;  // z
+  double* theta = nullptr; // z
+  int* status = nullptr;   // [0] bits, [1] spare
+  unsigned long long* counters = nullptr;  // [0] stalls, [1] unbounded
+  uint64_t* step = nullptr;  // device iteration counter (graph replays read it)
+  double* emit = nullptr;  // z x n staging for host output
+  double* check = nullptr; // [0] max violation, [1] eq residual, [2] drift
+};
+
+}  // namespace mhar
+
+struct mhar_ctx {
+  int m = 0, n = 0, mE = 0, z = 0;
+  int n_ld = 0;   // walker-major leading dimension for X / D (FP32, FP64)
+  int k_pad = 0;  // FP16 operand leading dimension (multiple of 64)
+  int m_pad = 0;  // rows of A padded to the tensor-core tile (multiple of 128)
+  int kdim = 0;   // MMA reduction length actually used (multiple of 16, >= n)
+  mhar_opts opts{};
+  cudaStream_t stream = nullptr;
+  uint64_t step = 0;
+  int64_t since_refresh = 0;
+  int device = 0;
+  mhar::DeviceBuffers d;
+  void* tc = nullptr;  // tensor-core plan (tensor maps, launch shape)
+  cudaGraphExec_t g_chunk = nullptr;
+  cudaGraphExec_t g_one = nullptr;
+  int graph_len = 0;
+  int64_t launches = 0;        // kernels launched (graph replays add their nodes)
+  int64_t launches_chunk = 0;  // kernel nodes in g_chunk
+  int64_t launches_one = 0;    // kernel nodes in g_one
+  double last_drift = 0.0;
+  double max_violation = 0.0;
+  double eq_residual = 0.0;
+  int status_bits = 0;
+  char err[512] = {0};
+};
+
+namespace mhar {
+
+// ---- kernel launchers (kernels_simt.cu) -------------------------------------
+// Every launcher enqueues on ctx->stream and returns cudaGetLastError().
+// `j` is the iteration offset added to the device counter *d.step.
+cudaError_t launch_directions(mhar_ctx* ctx, int j);
+cudaError_t launch_projection(mhar_ctx* ctx);
+cudaError_t launch_chord_simt(mhar_ctx* ctx);
+cudaError_t launch_update_simt(mhar_ctx* ctx, int j);
+cudaError_t launch_advance(mhar_ctx* ctx, int steps);
+cudaError_t launch_emit(mhar_ctx* ctx, double* out_device);
+cudaError_t launch_check(mhar_ctx* ctx);
+cudaError_t launch_set_points(mhar_ctx* ctx, const double* X_dev);
+cudaError_t launch_prepare_tc_operands(mhar_ctx* ctx);
+cudaError_t launch_refresh_simt(mhar_ctx* ctx);
+cudaError_t launch_reproject(mhar_ctx* ctx);
+
+// ---- tensor-core path (kernels_tc.cu) ---------------------------------------
+int tc_plan_create(mhar_ctx* ctx);            // 0 or MHAR_E_*
+void tc_plan_destroy(mhar_ctx* ctx);
+cudaError_t launch_chord_tc(mhar_ctx* ctx, int j);
+cudaError_t launch_refresh_tc(mhar_ctx* ctx);       // X split + S = b - A X (2 launches)
+
+}  // namespace mhar

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libmhar (include/mhar.h): argument marshalling only.
+
+Every step of the sampler runs in the library's CUDA kernels.  If the shared
+library is missing or cannot be loaded this module raises; there is no CPU
+fallback.  The same names as the C ABI are exported (``mhar_create``,
+``mhar_run``, ...), plus a small ``Sampler`` convenience class.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64 = 0
+FP32 = 1
+MIXED_F16X3 = 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_F16X3, "f16x3": MIXED_F16X3}
+
+OK = 0
+E_ARG = -1
+E_X0_INFEASIBLE = -2
+E_UNBOUNDED = -3
+E_NONFINITE = -4
+E_CUDA = -5
+E_RANK = -6
+E_UNSUPPORTED = -7
+
+ST_UNBOUNDED = 1
+ST_STALL = 2
+ST_NONFINITE = 4
+
+# Every symbol include/mhar.h declares.
+EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
+           "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
+           "mhar_last_error", "mhar_strerror", "mhar_destroy")
+
+
+class MharOpts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("refresh_k", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
+                ("walker0", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("graph_chunk", ctypes.c_int32), ("refresh_fp64", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class MharStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_uint64), ("walker_steps", ctypes.c_int64),
+                ("stalls", ctypes.c_int64), ("unbounded", ctypes.c_int64),
+                ("status_bits", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("refresh_drift", ctypes.c_double), ("max_violation", ctypes.c_double),
+                ("eq_residual", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class MharError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads libmhar.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmhar.so not built ({path}); run paper_2104_07097_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    lib.mhar_default_opts.argtypes = [ctypes.POINTER(MharOpts)]
+    lib.mhar_default_opts.restype = None
+    lib.mhar_create.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
+                                ctypes.c_int, ctypes.POINTER(MharOpts), ctypes.POINTER(vp)]
+    lib.mhar_create.restype = ctypes.c_int
+    lib.mhar_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp]
+    lib.mhar_run.restype = ctypes.c_int
+    lib.mhar_get_state.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mhar_get_state.restype = ctypes.c_int
+    lib.mhar_set_state.argtypes = [vp, dp, ctypes.c_uint64]
+    lib.mhar_set_state.restype = ctypes.c_int
+    lib.mhar_get_chord.argtypes = [vp, dp, dp, dp]
+    lib.mhar_get_chord.restype = ctypes.c_int
+    lib.mhar_check.argtypes = [vp, ctypes.POINTER(MharStats)]
+    lib.mhar_check.restype = ctypes.c_int
+    lib.mhar_get_stats.argtypes = [vp, ctypes.POINTER(MharStats)]
+    lib.mhar_get_stats.restype = ctypes.c_int
+    lib.mhar_time_kernels.argtypes = [vp, ctypes.c_int, dp]
+    lib.mhar_time_kernels.restype = ctypes.c_int
+    lib.mhar_last_error.argtypes = [vp]
+    lib.mhar_last_error.restype = ctypes.c_char_p
+    lib.mhar_strerror.argtypes = [ctypes.c_int]
+    lib.mhar_strerror.restype = ctypes.c_char_p
+    lib.mhar_destroy.argtypes = [vp]
+    lib.mhar_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mhar_default_opts() -> MharOpts:
+    o = MharOpts()
+    load().mhar_default_opts(ctypes.byref(o))
+    return o
+
+
+def mhar_strerror(code: int) -> str:
+    return load().mhar_strerror(code).decode()
+
+
+def mhar_last_error(ctx) -> str:
+    return load().mhar_last_error(ctx).decode()
+
+
+def mhar_create(A, b, AE, bE, x0, z: int, opts: MharOpts):
+    A, b, x0 = _f64(A), _f64(b), _f64(x0)
+    m, n = A.shape
+    AE = None if AE is None or np.size(AE) == 0 else _f64(np.atleast_2d(AE))
+    bE = None if AE is None else _f64(np.atleast_1d(bE))
+    mE = 0 if AE is None else AE.shape[0]
+    ctx = ctypes.c_void_p()
+    rc = load().mhar_create(_dp(A), _dp(b), m, n, _dp(AE), _dp(bE), mE, _dp(x0), int(z),
+                            ctypes.byref(opts), ctypes.byref(ctx))
+    if rc != OK:
+        raise MharError(rc, f"mhar_create failed: {mhar_strerror(rc)}")
+    return ctx
+
+
+def mhar_run(ctx, steps: int, thin: int, out_ptr) -> int:
+    return load().mhar_run(ctx, int(steps), int(thin), out_ptr)
+
+
+def mhar_destroy(ctx) -> None:
+    if ctx:
+        load().mhar_destroy(ctx)
+
+
+def mhar_get_state(ctx, z: int, n: int):
+    X = np.zeros((z, n))
+    step = ctypes.c_uint64()
+    rc = load().mhar_get_state(ctx, _dp(X), ctypes.byref(step))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return X, int(step.value)
+
+
+def mhar_set_state(ctx, X, step: int) -> None:
+    X = _f64(X)
+    rc = load().mhar_set_state(ctx, _dp(X), int(step))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+
+
+def mhar_get_chord(ctx, z: int):
+    lo, hi, t = np.zeros(z), np.zeros(z), np.zeros(z)
+    rc = load().mhar_get_chord(ctx, _dp(lo), _dp(hi), _dp(t))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return lo, hi, t
+
+
+def mhar_check(ctx) -> MharStats:
+    s = MharStats()
+    rc = load().mhar_check(ctx, ctypes.byref(s))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return s
+
+
+def mhar_get_stats(ctx) -> MharStats:
+    s = MharStats()
+    rc = load().mhar_get_stats(ctx, ctypes.byref(s))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return s
+
+
+def mhar_time_kernels(ctx, iters: int):
+    ms = np.zeros(3)
+    rc = load().mhar_time_kernels(ctx, int(iters), _dp(ms))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return ms
+
+
+class Sampler:
+    """z MHAR walkers on {A x <= b, AE x = bE} (Algorithm 2), all starting at x0.
+
+    ``precision``: "fp64" | "fp32" | "mixed".  ``stream``: a torch.cuda.Stream,
+    a raw cudaStream_t (int) or None.
+    """
+
+    def __init__(self, A, b, x0, z: int, AE=None, bE=None, precision: str | int = "fp64",
+                 seed: int = 0, refresh_k: int = 64, walker0: int = 0, stream=None,
+                 graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False):
+        o = mhar_default_opts()
+        o.seed = int(seed)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.refresh_k = int(refresh_k)
+        o.walker0 = int(walker0)
+        o.graph_chunk = int(graph_chunk)
+        o.out_on_device = 1 if out_on_device else 0
+        o.refresh_fp64 = 1 if refresh_fp64 else 0
+        if stream is not None:
+            o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        A = _f64(A)
+        self.m, self.n = A.shape
+        self.z = int(z) if z > 0 else max(self.m, self.n) + 1
+        self.out_on_device = out_on_device
+        self._ctx = mhar_create(A, b, AE, bE, x0, self.z, o)
+
+    def run(self, steps: int, thin: int = 0, out=None):
+        """Advances `steps` iterations; with thin > 0 returns (or fills) the
+        floor(steps/thin) x z x n samples.  `out` may be a numpy array (host)
+        or, for out_on_device samplers, a CUDA tensor / raw device pointer."""
+        nsamp = steps // thin if thin > 0 else 0
+        ptr = None
+        if nsamp > 0:
+            if out is None:
+                if self.out_on_device:
+                    raise ValueError("out_on_device sampler needs a device `out`")
+                out = np.zeros((nsamp, self.z, self.n))
+            if isinstance(out, np.ndarray):
+                if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < nsamp * self.z * self.n:
+                    raise ValueError("out must be a C-contiguous float64 array of the sample shape")
+                ptr = ctypes.c_void_p(out.ctypes.data)
+            elif hasattr(out, "data_ptr"):
+                ptr = ctypes.c_void_p(out.data_ptr())
+            else:
+                ptr = ctypes.c_void_p(int(out))
+        rc = mhar_run(self._ctx, steps, thin, ptr)
+        if rc != OK:
+            raise MharError(rc, mhar_last_error(self._ctx))
+        return out
+
+    def state(self):
+        return mhar_get_state(self._ctx, self.z, self.n)
+
+    def set_state(self, X, step: int) -> None:
+        mhar_set_state(self._ctx, X, step)
+
+    def chord(self):
+        return mhar_get_chord(self._ctx, self.z)
+
+    def check(self) -> MharStats:
+        return mhar_check(self._ctx)
+
+    def stats(self) -> MharStats:
+        return mhar_get_stats(self._ctx)
+
+    def time_kernels(self, iters: int):
+        """Average device ms of (directions, chord+update, refresh)."""
+        return mhar_time_kernels(self._ctx, iters)
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            mhar_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

