@@ -163,7 +163,36 @@ int mhar_get_stats(const mhar_ctx* ctx, mhar_stats* stats);
  * The timed iterations are real: the chain and its counters advance. */
 int mhar_time_kernels(mhar_ctx* ctx, int iters, double* ms);
 
-/* Human-readable description of the last error on ctx (never NULL). */
+/* Chord of every walker without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate --
+ * a process that works inside a fixed device-memory budget reserved up front
+ * (so a cudaMalloc inside a library would break its accounting or fail), or a
+ * latency-critical loop that cannot take the device synchronisation cudaMalloc
+ * and cudaFree may bring.  It computes, in FP64, the same quantity as
+ * mhar_get_chord in MHAR_FP64 mode: for walker k, the chord
+ * (lmin[k], lmax[k]) of the line X[k] + lambda D[k] through {A x <= b}
+ * (Section 4.4 formulas; rows with a.d == 0 are skipped, a slack made negative
+ * by rounding counts as 0, an open side gives -inf / +inf).
+ *   A  m x n, b  m, X  z x n, D  z x n: device pointers, FP64, row-major, no
+ *      padding; only read.
+ *   lmin, lmax: z doubles each, device pointers, written.
+ *   stream: cudaStream_t to enqueue on (NULL: legacy default stream).  The
+ *      call returns once the work is enqueued; nothing is copied to the host.
+ * Its only working memory is a fixed 1 MiB array compiled into the library,
+ * which every GPU that loads the library holds until the process exits; it
+ * limits z to 65536 (larger z: MHAR_E_ARG).  The first call on each device
+ * looks up that array's device address (with that device current), so make
+ * the first call on a device before any stream capture.  All calls share the
+ * array and each call clears the part it uses; calls whose work overlaps on
+ * the GPU race on it and give wrong results.
+ * Returns MHAR_OK, MHAR_E_ARG or MHAR_E_CUDA; mhar_last_error(NULL) then
+ * describes the failure (per host thread). */
+int mhar_chord_noalloc(const double* A, const double* b, int m, int n,
+                       const double* X, const double* D, int z,
+                       double* lmin, double* lmax, void* stream);
+
+/* Human-readable description of the last error on ctx (never NULL); with
+ * ctx == NULL, the last mhar_chord_noalloc failure on this host thread. */
 const char* mhar_last_error(const mhar_ctx* ctx);
 
 /* Name of a return code. */

@@ -266,7 +266,7 @@ const char* mhar_strerror(int code) {
 }
 
 const char* mhar_last_error(const mhar_ctx* c) {
-  if (!c) return "null context";
+  if (!c) return mhar::noalloc_last_error();
   return c->err[0] ? c->err : "no error";
 }
 

@@ -103,6 +103,9 @@ cudaError_t launch_prepare_tc_operands(mhar_ctx* ctx);
 cudaError_t launch_refresh_simt(mhar_ctx* ctx);
 cudaError_t launch_reproject(mhar_ctx* ctx);
 
+// ---- allocation-free chord entry point (noalloc.cu) ---------------------------
+const char* noalloc_last_error();
+
 // ---- tensor-core path (kernels_tc.cu) ---------------------------------------
 int tc_plan_create(mhar_ctx* ctx);            // 0 or MHAR_E_*
 void tc_plan_destroy(mhar_ctx* ctx);

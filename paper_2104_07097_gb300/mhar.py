@@ -35,7 +35,7 @@ ST_NONFINITE = 4
 # Every symbol include/mhar.h declares.
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
            "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
-           "mhar_last_error", "mhar_strerror", "mhar_destroy")
+           "mhar_chord_noalloc", "mhar_last_error", "mhar_strerror", "mhar_destroy")
 
 
 class MharOpts(ctypes.Structure):
@@ -97,6 +97,9 @@ def load(path: str | None = None):
     lib.mhar_get_stats.restype = ctypes.c_int
     lib.mhar_time_kernels.argtypes = [vp, ctypes.c_int, dp]
     lib.mhar_time_kernels.restype = ctypes.c_int
+    lib.mhar_chord_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
+                                       vp, vp, vp]
+    lib.mhar_chord_noalloc.restype = ctypes.c_int
     lib.mhar_last_error.argtypes = [vp]
     lib.mhar_last_error.restype = ctypes.c_char_p
     lib.mhar_strerror.argtypes = [ctypes.c_int]
@@ -198,6 +201,16 @@ def mhar_time_kernels(ctx, iters: int):
     if rc != OK:
         raise MharError(rc, mhar_last_error(ctx))
     return ms
+
+
+def mhar_chord_noalloc(A_ptr, b_ptr, m: int, n: int, X_ptr, D_ptr, z: int, lmin_ptr, lmax_ptr,
+                       stream=None) -> int:
+    """Allocation-free chord of every walker; all array arguments are device
+    pointers (ints) to FP64 row-major buffers.  Returns the C return code."""
+    vp = ctypes.c_void_p
+    s = None if stream is None else vp(int(getattr(stream, "cuda_stream", stream)))
+    return load().mhar_chord_noalloc(vp(A_ptr), vp(b_ptr), int(m), int(n), vp(X_ptr), vp(D_ptr),
+                                     int(z), vp(lmin_ptr), vp(lmax_ptr), s)
 
 
 class Sampler:
