@@ -356,13 +356,15 @@ __global__ void check_kernel(int mode, int m, int n, int n_ld, int mE, const dou
   }
 }
 
-// Mixed mode: S[i][k] = b_i - a_i x_k recomputed in FP64 from the FP32-pair
-// points (tiles of 64 rows x 64 walkers, K staged through shared memory), and
-// the largest change |S_old - S_new| recorded (drift).
+// Mixed mode: S = b - A X recomputed in FP64 from the FP32-pair points (tiles
+// of 64 rows x 64 walkers, K staged through shared memory), stored as the
+// tensor-core path keeps it (divided by the row scale, blocked by 4 rows),
+// and the largest change |S_old - S_new| recorded (drift).
 __global__ void __launch_bounds__(kThreads)
 refresh_simt_kernel(int m, int n_ld, int z, int z_ld, const double* __restrict__ A,
                     const double* __restrict__ b, const float* __restrict__ Xhi,
-                    const float* __restrict__ Xlo, float* S, unsigned long long* drift_key) {
+                    const float* __restrict__ Xlo, const float* __restrict__ row_scale, float* S,
+                    unsigned long long* drift_key) {
   constexpr int BK = 8;
   __shared__ double As[BK][64];
   __shared__ double Xs[BK][64];
@@ -407,9 +409,10 @@ refresh_simt_kernel(int m, int n_ld, int z, int z_ld, const double* __restrict__
       const int gw = w0 + tx + 16 * c;
       if (gw >= z) continue;
       const double s = b[gi] - acc[r][c];
-      float* sp = S + static_cast<size_t>(gi) * z_ld + gw;
-      drift = fmax(drift, fabs(static_cast<double>(*sp) - s));
-      *sp = static_cast<float>(s);
+      const double sc = static_cast<double>(row_scale[gi]);
+      float* sp = S + (static_cast<size_t>(gi >> 2) * z_ld + gw) * 4 + (gi & 3);
+      drift = fmax(drift, fabs(static_cast<double>(*sp) * sc - s));
+      *sp = static_cast<float>(s / sc);
     }
   }
   red[tid] = drift;
@@ -487,7 +490,7 @@ __global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, 
   const double scale = ldexp(1.0, e);
   if (threadIdx.x == 0) {
     row_scale[r] = r < m ? static_cast<float>(scale) : 1.0f;
-    bS[r] = r < m ? static_cast<float>(b[r]) : 0.0f;
+    bS[r] = r < m ? static_cast<float>(b[r] / scale) : 0.0f;
   }
   for (int i = threadIdx.x; i < k_pad; i += blockDim.x) {
     float v = 0.0f;
@@ -598,7 +601,7 @@ cudaError_t launch_refresh_simt(mhar_ctx* c) {
   const int z_ld = (c->z + 127) / 128 * 128;
   dim3 grid(blocks_for(c->m, 64), blocks_for(c->z, 64));
   refresh_simt_kernel<<<grid, kThreads, 0, c->stream>>>(
-      c->m, c->n_ld, c->z, z_ld, c->d.A64, c->d.b64, c->d.Xhi, c->d.Xlo, c->d.S,
+      c->m, c->n_ld, c->z, z_ld, c->d.A64, c->d.b64, c->d.Xhi, c->d.Xlo, c->d.row_scale, c->d.S,
       reinterpret_cast<unsigned long long*>(c->d.check) + 2);
   return cudaGetLastError();
 }

@@ -55,9 +55,9 @@ enum : int { kModeChord = 0, kModeRefresh = 1 };
 struct TcParams {
   int mode;                 // kModeChord | kModeRefresh
   const float* row_scale;   // m_pad: A[i,:] = row_scale[i] (Ah + Al)[i,:]
-  const float* bS;          // m_pad: b in FP32 (refresh)
+  const float* bS;          // m_pad: b[i] / row_scale[i] in FP32 (refresh)
   const float* wscale;      // z_ld: X[k,:] = wscale[k] (Xh + Xl)[k,:] (refresh)
-  float* S;                 // m_pad x z_ld
+  float* S;                 // slack / row_scale, blocked: [(i/4) z_ld + k] * 4 + i%4
   float* Xhi;               // z x n_ld
   float* Xlo;
   const __half* Dh;         // z_ld x k_pad
@@ -128,7 +128,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   const uint32_t a = smem_u32(bar);
   if (mbar_try_wait(a, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(a, parity)) {
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(a, parity)) return true;
     if (*timed_out) return false;
     if (clock64() - t0 > kTimeoutCycles) {
       *timed_out = 1;
@@ -136,7 +139,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
       return false;
     }
   }
-  return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -239,11 +241,26 @@ __device__ __forceinline__ void epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
 }
 
-// Slack of 32 consecutive rows for one walker (rows are z_ld floats apart,
-// so each load is one coalesced 128-byte line across the warp's walkers).
-__device__ __forceinline__ void load_s32(const float* src, size_t stride, float (&v)[32]) {
+// The slack is stored blocked by 4 rows: element (i, k) sits at
+// ((i / 4) z_ld + k) 4 + i % 4, so one 16-byte access gives a walker four
+// consecutive rows and a warp's 32 consecutive walkers read 512 contiguous
+// bytes.  32 rows of one walker = eight such accesses, z_ld * 16 bytes apart.
+__device__ __forceinline__ float* s_block(const TcParams& p, int row, int k) {
+  return p.S + (static_cast<size_t>(row >> 2) * p.z_ld + k) * 4;
+}
+__device__ __forceinline__ void load_s32(const TcParams& p, const float* src, float (&v)[32]) {
+  const float4* q = reinterpret_cast<const float4*>(src);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = __ldcg(src + static_cast<size_t>(c) * stride);
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = __ldcg(q + static_cast<size_t>(i) * p.z_ld);
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void store_s32(const TcParams& p, float* dst, const float (&v)[32]) {
+  float4* q = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    __stcg(q + static_cast<size_t>(i) * p.z_ld, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
 }
 
 __global__ void __launch_bounds__(kThreadsTc, 1)
@@ -356,25 +373,25 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     float drift = 0.0f;
     for (int nt = 0; nt < ntiles; ++nt) {
       const int col = nt * kRowsTile + cg * 32;
-      float* Srow = p.S + static_cast<size_t>(row_base + col) * p.z_ld + k;
-      float old[32];
-      load_s32(Srow, p.z_ld, old);
+      float* Sb = s_block(p, row_base + col, k);
+      float sv[32];
+      load_s32(p, Sb, sv);
       mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
       tc_fence_after();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         float g[16];
         tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(col + 16 * half), g);
-        if (k < p.z) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int cc = 16 * half + c;
-            const float sn = fmaf(-g[c] * tail->scale[col + cc], ws, tail->brow[col + cc]);
-            drift = fmaxf(drift, fabsf(sn - old[cc]));
-            __stcg(Srow + static_cast<size_t>(cc) * p.z_ld, sn);
-          }
+        for (int c = 0; c < 16; ++c) {
+          const int cc = 16 * half + c;
+          const float sn = fmaf(-g[c], ws, tail->brow[col + cc]);
+          // drift in the units of the constraint: |change| * row scale
+          drift = fmaxf(drift, fabsf(sn - sv[cc]) * tail->scale[col + cc]);
+          sv[cc] = sn;
         }
       }
+      if (k < p.z) store_s32(p, Sb, sv);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
@@ -388,12 +405,10 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const int k = strip * kWalkers + wl;
     float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
     float s_cur[32], s_nxt[32];
-    if (ntiles > 0)
-      load_s32(p.S + static_cast<size_t>(row_base + cg * 32) * p.z_ld + k, p.z_ld, s_cur);
+    if (ntiles > 0) load_s32(p, s_block(p, row_base + cg * 32, k), s_cur);
     for (int nt = 0; nt < ntiles; ++nt) {
       const int col = nt * kRowsTile + cg * 32;
-      if (nt + 1 < ntiles)
-        load_s32(p.S + static_cast<size_t>(row_base + col + kRowsTile) * p.z_ld + k, p.z_ld, s_nxt);
+      if (nt + 1 < ntiles) load_s32(p, s_block(p, row_base + col + kRowsTile, k), s_nxt);
       mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
       tc_fence_after();
 #pragma unroll
@@ -403,11 +418,11 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
                       static_cast<uint32_t>(col + 16 * half), g);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const float gg = g[c] * tail->scale[col + 16 * half + c];
-          const float sv = s_cur[16 * half + c];
-          const float ss = fmaxf(sv, 0.0f);
+          // Both the slack and G are in units of the row's power-of-two
+          // scale, so their ratio is the paper's lambda_i unchanged.
+          const float gg = g[c];
+          const float ss = fmaxf(s_cur[16 * half + c], 0.0f);
           chk = fmaf(gg, 0.0f, chk);
-          chk = fmaf(sv, 0.0f, chk);
           // s/g improves the bound on its side iff s < bound * g (g > 0: upper
           // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
           const float bnd = gg > 0.0f ? hi : lo;
@@ -478,26 +493,20 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const float t = tail->theta[wl];
     if (__any_sync(0xffffffffu, t != 0.0f)) {
       float s_cur[32], s_nxt[32];
-      if (ntiles > 0)
-        load_s32(p.S + static_cast<size_t>(row_base + cg * 32) * p.z_ld + k, p.z_ld, s_cur);
+      if (ntiles > 0) load_s32(p, s_block(p, row_base + cg * 32, k), s_cur);
       for (int nt = 0; nt < ntiles; ++nt) {
         const int col = nt * kRowsTile + cg * 32;
-        if (nt + 1 < ntiles)
-          load_s32(p.S + static_cast<size_t>(row_base + col + kRowsTile) * p.z_ld + k, p.z_ld, s_nxt);
-        float* Srow = p.S + static_cast<size_t>(row_base + col) * p.z_ld + k;
+        if (nt + 1 < ntiles) load_s32(p, s_block(p, row_base + col + kRowsTile, k), s_nxt);
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           float g[16];
           // tcgen05.ld is warp-collective: every lane joins, lanes with theta == 0 skip the update.
           tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) +
                         static_cast<uint32_t>(col + 16 * half), g);
-          if (t != 0.0f) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-              __stcg(Srow + static_cast<size_t>(16 * half + c) * p.z_ld,
-                     fmaf(-t, g[c] * tail->scale[col + 16 * half + c], s_cur[16 * half + c]));
-          }
+          for (int c = 0; c < 16; ++c) s_cur[16 * half + c] = fmaf(-t, g[c], s_cur[16 * half + c]);
         }
+        if (t != 0.0f) store_s32(p, s_block(p, row_base + col, k), s_cur);
 #pragma unroll
         for (int c = 0; c < 32; ++c) s_cur[c] = s_nxt[c];
       }

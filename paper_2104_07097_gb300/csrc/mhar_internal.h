@@ -29,7 +29,7 @@ struct DeviceBuffers {
   __half* Ah = nullptr;    // m_pad x k_pad
   __half* Al = nullptr;    // m_pad x k_pad
   float* row_scale = nullptr; // m_pad: A[i,:] = row_scale[i] * (Ah + Al)[i,:]
-  float* bS = nullptr;     // m_pad (FP32 b, 0 beyond m)
+  float* bS = nullptr;     // m_pad (FP32 b / row_scale, 0 beyond m)
 
   // Walker state.
   double* X64 = nullptr;   // z x n_ld          (FP64 mode)
@@ -39,7 +39,8 @@ struct DeviceBuffers {
   float* D32 = nullptr;    // z x n_ld          (FP32 mode; mixed: pre-projection scratch)
   __half* Dh = nullptr;    // z x k_pad         (mixed)
   __half* Dl = nullptr;    // z x k_pad         (mixed)
-  float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack, walkers contiguous)
+  float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack / row_scale, blocked:
+                           //  element (i, k) at ((i / 4) z_ld + k) 4 + i % 4)
   float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix)
   __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
   __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
