@@ -160,7 +160,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--precision", default="mixed_rs", choices=["mixed_rs", "mixed", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -223,13 +223,17 @@ def main() -> None:
     st = s.check()
     peaks = load_peaks()
     m, n = p.m, p.n
-    if args.precision == "mixed":
-        flops = 6.0 * m * n * z          # 3 FP16 products of 2 m n per walker-step
+    if args.precision in ("mixed", "mixed_rs"):
+        # FP16 products of 2 m n flops each per walker-step: 4 for A D in the
+        # stored-slack mode; 3 for A D + 3 for A X in the recompute mode.
+        nprod = 4 if args.precision == "mixed" else 6
+        flops = 2.0 * nprod * m * n * z
         peak = peaks["bf16_tflops_sustained"]
         roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
                     "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
-                    "traffic": None, "kernel": "chord_tc_kernel",
-                    "algorithmic": "6 m n flops per walker-step (FP16 hi.hi + hi.lo + lo.hi)",
+                    "traffic": None,
+                    "kernel": "recompute_tc_kernel" if args.precision == "mixed_rs" else "walker_tc_kernel",
+                    "algorithmic": f"{2 * nprod} m n tensor flops per walker-step ({nprod} FP16 products)",
                     "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}
     else:
         bytes_ = 2.0 * m * n * z * (8 if args.precision == "fp64" else 4)
@@ -262,7 +266,7 @@ def main() -> None:
     # Plain FP32 MHAR (CUDA cores, the paper's recompute formulation) on the
     # same workload, for the mixed-vs-plain comparison.
     plain = None
-    if args.precision == "mixed":
+    if args.precision in ("mixed", "mixed_rs"):
         with mhar.Sampler(p.A, p.b, p.x0, z, precision="fp32", seed=0, walker0=rank * z,
                           stream=stream, out_on_device=True) as sp:
             sp.run(iters, thin=iters, out=out)
@@ -279,7 +283,8 @@ def main() -> None:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"mixed": "f16x3-f32acc", "fp32": "f32", "fp64": "f64"}[args.precision],
+                "dtype": {"mixed": "f16x4-f32acc", "mixed_rs": "f16x3-f32acc", "fp32": "f32",
+                          "fp64": "f64"}[args.precision],
                 "data": "synthetic (seeded random polytope, unit-norm Gaussian rows)",
                 "config": config(args.precision), "roofline": roofline,
                 "kernel_ms": {"directions": kms[0], "chord": kms[1], "refresh": kms[2]},

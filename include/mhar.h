@@ -56,14 +56,21 @@ extern "C" {
  *   FP16 high + low parts; three products (hi.hi + hi.lo + lo.hi) accumulate
  *   in FP32 in tensor memory, which carries A d to about 2^-22 relative.  The
  *   slack S = b - A X is stored (FP32), updated as S -= (A D) diag(theta) in
- *   the same kernel, and recomputed from X every refresh_k iterations. */
-#define MHAR_FP64          0
-#define MHAR_FP32          1
-#define MHAR_MIXED_F16X3  2
+ *   the same kernel, and recomputed from X every refresh_k iterations.
+ * MHAR_MIXED_RECOMPUTE: the paper's own formulation (Lemma 4.2) on the tensor
+ *   cores: every iteration one fused kernel forms A X and A D from FP16 pairs
+ *   (three products each, FP32 accumulation), the slack b - A X, the ratios
+ *   and the chord.  No slack is stored, so there is nothing to refresh and no
+ *   drift; refresh_k is ignored. */
+#define MHAR_FP64             0
+#define MHAR_FP32             1
+#define MHAR_MIXED_F16X3      2
+#define MHAR_MIXED_RECOMPUTE  3
 
 typedef struct {
   uint64_t seed;          /* Philox4x32-10 key (default 0)                      */
-  int32_t  precision;     /* MHAR_FP64 (default) | MHAR_FP32 | MHAR_MIXED_F16X3 */
+  int32_t  precision;     /* MHAR_FP64 (default) | MHAR_FP32 | MHAR_MIXED_F16X3 |
+                             MHAR_MIXED_RECOMPUTE                              */
   int32_t  refresh_k;     /* mixed mode: recompute S = b - A X every refresh_k
                              iterations (default 64; 0 = never)               */
   int32_t  out_on_device; /* 1: `out` of mhar_run is a device pointer          */

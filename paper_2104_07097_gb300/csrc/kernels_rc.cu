@@ -1,0 +1,426 @@
+// kernels_rc.cu -- the walker step with the slack recomputed on the tensor
+// cores every iteration (MHAR_MIXED_RECOMPUTE mode).
+//
+// This is the paper's own formulation of the line sets (Lemma 4.2: A X, then
+// B - A X, then A D, ratios, sign split, column min / max) executed as one
+// fused kernel:
+//   P = X A^T and G = D A^T   tcgen05.mma kind::f16, each operand an FP16
+//                             hi + lo pair, three products per matrix
+//                             (hi.hi + hi.lo + lo.hi), FP32 accumulation in
+//                             tensor memory
+//   s_i = b_i - p_i           (in units of the row's power-of-two scale)
+//   lambda_max = min{ s_i / g_i : g_i > 0 },  lambda_min = max{ s_i / g_i : g_i < 0 }
+//   theta = lambda_min + u (lambda_max - lambda_min)
+// The move X += D diag(theta) is applied by the next iteration's walker
+// preparation kernel (which also re-splits X), or by a flush before X is read.
+// Nothing of size m x z is stored: no slack array, no ratio matrix, no
+// drift and no refresh.  Per walker-step the tensor cores do 12 m n flops.
+//
+// Decomposition: 128 walkers per CTA (MMA M, one walker per TMEM lane), a
+// cluster of C CTAs along the constraint rows; each CTA streams its row tiles
+// (MMA N = 128) through a pair of double-buffered TMEM accumulators (G and P:
+// 4 x 128 columns), so the epilogue of tile t overlaps the MMAs of tile t+1.
+// The walker operands (D and X pairs) stay in shared memory for the whole
+// launch when n <= 128 and are streamed per tile otherwise; the A pairs stream
+// through five 16 KB slots (hi and lo staged separately) so loads run about a
+// tile ahead of the MMAs.  Each CTA pushes its partial chords into every
+// peer's shared memory before one cluster barrier, after which CTAs finish
+// independently.
+//
+// Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM
+// owner, warps 2..17 epilogue (four per TMEM lane quarter, each taking 32 of
+// every tile's 128 columns).  Every mbarrier wait is bounded (~2 s); on expiry
+// the kernel flags the error word and still passes every cluster barrier.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cstdio>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+#include "tc_common.cuh"
+
+namespace mhar {
+namespace {
+
+using namespace tc;
+
+constexpr int kWSlots = 2;                           // walker-operand slots
+constexpr int kASlots = 5;                           // A half-slots (Ah or Al of one chunk)
+constexpr int kWBytes = 4 * kOperandBytes;           // Dh, Dl, Xh, Xl chunk
+constexpr int kABytes = kOperandBytes;               // Ah or Al chunk
+constexpr int kEpiWarps = 16;
+constexpr int kThreadsRc = (2 + kEpiWarps) * 32;
+constexpr int kMaxTiles = 32;                        // rows per CTA <= 4096
+constexpr int kMaxCluster = 8;
+
+struct RcParams {
+  const float* bS;          // m_pad: b_i / row_scale_i (FP32)
+  const float* wscale;      // z_ld: X[k,:] = wscale[k] (Xh + Xl)[k,:]
+  float* pend;              // z_ld: the move theta each walker still has to make
+  double* lmin;
+  double* lmax;
+  double* theta;
+  int* status;
+  unsigned long long* counters;
+  int* err;
+  const uint64_t* step_ptr;
+  uint64_t seed;
+  int j;
+  uint32_t walker0;
+  int z, kdim, k_chunks, tiles_per_cta, m_tiles;
+};
+
+struct RcTail {
+  uint64_t w_full[kWSlots];
+  uint64_t w_empty[kWSlots];
+  uint64_t a_full[kASlots];
+  uint64_t a_empty[kASlots];
+  uint64_t t_full[2];
+  uint64_t t_empty[2];
+  uint32_t tmem_base;
+  int timed_out;
+  float part_lo[4][kWalkers];
+  float part_hi[4][kWalkers];
+  float recv_lo[kMaxCluster][kWalkers];   // partial chords pushed by every CTA of the cluster
+  float recv_hi[kMaxCluster][kWalkers];
+};
+
+constexpr size_t kSmemRc = 1024 + static_cast<size_t>(kWSlots) * kWBytes +
+                           static_cast<size_t>(kASlots) * kABytes + sizeof(RcTail);
+
+__device__ __forceinline__ void st_dsmem_f32(float* local, uint32_t rank, float v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsRc, 1)
+recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+                    const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
+                    const __grid_constant__ CUtensorMap tm_xh, const __grid_constant__ CUtensorMap tm_xl,
+                    const RcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* wslot = base;                                   // kWSlots x 64 KB
+  uint8_t* aslot = base + kWSlots * kWBytes;               // kASlots x 32 KB
+  RcTail* tail = reinterpret_cast<RcTail*>(aslot + kASlots * kABytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = blockIdx.x;
+  const uint32_t csize = gridDim.x;
+  const int strip = blockIdx.y;
+  const int tile0 = static_cast<int>(rank) * p.tiles_per_cta;
+  int ntiles = p.m_tiles - tile0;
+  ntiles = ntiles < 0 ? 0 : (ntiles > p.tiles_per_cta ? p.tiles_per_cta : ntiles);
+  const int row_base = tile0 * kRowsTile;
+  const bool resident = p.k_chunks <= kWSlots;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
+    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    tail->timed_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)), "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tail->tmem_base;
+  volatile int* timed_out = &tail->timed_out;
+
+  if (warp == 0) {
+    // ---- TMA producer --------------------------------------------------------
+    if (lane == 0) {
+      int w_it = 0, a_it = 0;
+      const int yw = strip * kWalkers;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        for (int kc = 0; kc < p.k_chunks; ++kc) {
+          const int x = kc * kTcKChunk;
+          if (!resident || nt == 0) {
+            const int s = w_it % kWSlots;
+            if (w_it >= kWSlots) mbar_wait(&tail->w_empty[s], ((w_it / kWSlots) - 1) & 1, timed_out, p.err);
+            uint8_t* dst = wslot + s * kWBytes;
+            mbar_expect_tx(&tail->w_full[s], kWBytes);
+            tma_load_2d(dst, &tm_dh, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + kOperandBytes, &tm_dl, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + 2 * kOperandBytes, &tm_xh, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + 3 * kOperandBytes, &tm_xl, &tail->w_full[s], x, yw);
+            ++w_it;
+          }
+          const int yr = row_base + nt * kRowsTile;
+          for (int half = 0; half < 2; ++half, ++a_it) {
+            const int s = a_it % kASlots;
+            if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, p.err);
+            mbar_expect_tx(&tail->a_full[s], kABytes);
+            tma_load_2d(aslot + s * kABytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s], x, yr);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer: G = (Dh + Dl) A^T and P = (Xh + Xl) A^T, 3 products each --
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      int w_it = 0, a_it = 0;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        const int b = nt & 1;
+        if (nt >= 2) mbar_wait(&tail->t_empty[b], ((nt >> 1) - 1) & 1, timed_out, p.err);
+        tc_fence_after();
+        const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
+        const uint32_t p_tmem = g_tmem + 128u;
+        for (int kc = 0; kc < p.k_chunks; ++kc) {
+          int ws;
+          if (resident) {
+            ws = kc;
+            if (nt == 0) mbar_wait(&tail->w_full[ws], 0, timed_out, p.err);
+          } else {
+            ws = w_it % kWSlots;
+            mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
+          }
+          const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
+          const uint32_t dh = w0, dl = w0 + kOperandBytes;
+          const uint32_t xh = w0 + 2 * kOperandBytes, xl = w0 + 3 * kOperandBytes;
+          int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
+          ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
+          // A hi: the four products that read it; then release its slot.
+          int as = a_it % kASlots;
+          mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
+          tc_fence_after();
+          uint32_t a0 = smem_u32(aslot + as * kABytes);
+          for (int ks = 0; ks < ks_n; ++ks) {
+            const uint32_t off = static_cast<uint32_t>(ks * kTcK * 2);
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t d_a = sw128_desc(a0 + off);
+            mma_f16(g_tmem, sw128_desc(dh + off), d_a, idesc, acc);
+            mma_f16(g_tmem, sw128_desc(dl + off), d_a, idesc, 1u);
+            mma_f16(p_tmem, sw128_desc(xh + off), d_a, idesc, acc);
+            mma_f16(p_tmem, sw128_desc(xl + off), d_a, idesc, 1u);
+          }
+          mma_commit(&tail->a_empty[as]);
+          ++a_it;
+          // A lo: hi parts of the walker operands times it.
+          as = a_it % kASlots;
+          mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
+          tc_fence_after();
+          a0 = smem_u32(aslot + as * kABytes);
+          for (int ks = 0; ks < ks_n; ++ks) {
+            const uint32_t off = static_cast<uint32_t>(ks * kTcK * 2);
+            const uint64_t d_a = sw128_desc(a0 + off);
+            mma_f16(g_tmem, sw128_desc(dh + off), d_a, idesc, 1u);
+            mma_f16(p_tmem, sw128_desc(xh + off), d_a, idesc, 1u);
+          }
+          mma_commit(&tail->a_empty[as]);
+          ++a_it;
+          if (!resident) {
+            mma_commit(&tail->w_empty[ws]);
+            ++w_it;
+          }
+        }
+        mma_commit(&tail->t_full[b]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    const float ws = p.wscale[k];
+    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    for (int nt = 0; nt < ntiles; ++nt) {
+      const int b = nt & 1;
+      mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err);
+      tc_fence_after();
+      const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+      const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);
+      float g0[16], g1[16], p0[16], p1[16];
+      tmem_ld16(gcol, g0);
+      tmem_ld16(gcol + 16, g1);
+      tmem_ld16(gcol + 128, p0);
+      tmem_ld16(gcol + 144, p1);
+      // The accumulators of this buffer are in registers: let the MMA reuse it.
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tail->t_empty[b]);
+      const float4* br4 = reinterpret_cast<const float4*>(p.bS + row_base + nt * kRowsTile + cg * 32);
+      float br[32];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 v = __ldg(br4 + i);
+        br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float gg = c < 16 ? g0[c] : g1[c - 16];
+        const float pp = c < 16 ? p0[c] : p1[c - 16];
+        const float sv = fmaf(-pp, ws, br[c]);
+        const float ss = fmaxf(sv, 0.0f);
+        chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
+        // s/g improves the bound on its side iff s < bound * g (g > 0: upper
+        // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
+        const float bnd = gg > 0.0f ? hi : lo;
+        if (ss < bnd * gg) {
+          const float r = __fdividef(ss, gg);
+          if (gg > 0.0f) hi = r; else lo = r;
+        }
+      }
+    }
+    tail->part_lo[cg][wl] = lo;
+    tail->part_hi[cg][wl] = hi;
+    named_bar<kEpiWarps * 32>();
+    if (cg == 0) {
+      const float L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
+      const float H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
+      // Push this CTA's partial chord into slot `rank` of the cluster's rank 0,
+      // which combines them.
+      st_dsmem_f32(&tail->recv_lo[rank][wl], 0, L);
+      st_dsmem_f32(&tail->recv_hi[rank][wl], 0, H);
+    }
+    if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+  }
+
+  // Every push is visible after this barrier; no remote access follows it.
+  tc_fence_before();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+
+  if (rank == 0 && warp >= 2 && ((warp - 2) >> 2) == 0) {
+    const int q = warp & 3;
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    float L = -INFINITY, H = INFINITY;
+    for (uint32_t r = 0; r < csize; ++r) {
+      L = fmaxf(L, tail->recv_lo[r][wl]);
+      H = fminf(H, tail->recv_hi[r][wl]);
+    }
+    if (k < p.z) {
+      float t = 0.0f;
+      int flag = 0;
+      if (isinf(L) || isinf(H)) {
+        flag = MHAR_ST_UNBOUNDED;
+      } else if (L > H) {
+        flag = MHAR_ST_STALL;
+      } else {
+        const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+        const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
+                                  kStreamChord);
+        const double u = open_unit_f64(w.x);
+        t = static_cast<float>(static_cast<double>(L) +
+                               u * (static_cast<double>(H) - static_cast<double>(L)));
+      }
+      p.lmin[k] = L;
+      p.lmax[k] = H;
+      p.theta[k] = t;
+      p.pend[k] = t;
+      if (flag) {
+        atomicOr(p.status, flag);
+        atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+      }
+    }
+  }
+}
+
+struct RcShape {
+  int C = 1;
+  int tiles_per_cta = 1;
+};
+
+RcShape rc_shape(const mhar_ctx* c, const TcPlan* plan) {
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  RcShape s;
+  // Fill the SMs with (row groups x walker strips) CTAs, one per SM.
+  int C = sms / plan->strips;
+  C = C < 1 ? 1 : (C > 8 ? 8 : C);
+  C = C > plan->m_tiles ? plan->m_tiles : C;
+  s.tiles_per_cta = (plan->m_tiles + C - 1) / C;
+  while (s.tiles_per_cta > kMaxTiles && C < kMaxCluster) {
+    ++C;
+    s.tiles_per_cta = (plan->m_tiles + C - 1) / C;
+  }
+  s.C = (plan->m_tiles + s.tiles_per_cta - 1) / s.tiles_per_cta;
+  return s;
+}
+
+}  // namespace
+
+int rc_prepare(mhar_ctx* c) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  const RcShape s = rc_shape(c, plan);
+  if (s.C > kMaxCluster || s.tiles_per_cta > kMaxTiles) {
+    snprintf(c->err, sizeof(c->err),
+             "recompute mode covers m <= %d inequality rows (got %d row tiles)",
+             kMaxCluster * kMaxTiles * kRowsTile, plan->m_tiles);
+    return MHAR_E_UNSUPPORTED;
+  }
+  cudaError_t e = cudaFuncSetAttribute(recompute_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemRc));
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "recompute kernel attributes: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    return MHAR_E_CUDA;
+  }
+  return MHAR_OK;
+}
+
+cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  const RcShape s = rc_shape(c, plan);
+  RcParams p;
+  p.bS = c->d.bS;
+  p.wscale = c->d.wscale;
+  p.pend = c->d.pend;
+  p.lmin = c->d.lmin;
+  p.lmax = c->d.lmax;
+  p.theta = c->d.theta;
+  p.status = c->d.status;
+  p.counters = c->d.counters;
+  p.err = c->d.status + 1;
+  p.step_ptr = c->d.step;
+  p.seed = c->opts.seed;
+  p.j = j;
+  p.walker0 = c->opts.walker0;
+  p.z = c->z;
+  p.kdim = c->kdim;
+  p.k_chunks = c->k_pad / kTcKChunk;
+  p.tiles_per_cta = s.tiles_per_cta;
+  p.m_tiles = plan->m_tiles;
+
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(s.C, plan->strips, 1);
+  cfg.blockDim = dim3(kThreadsRc, 1, 1);
+  cfg.dynamicSmemBytes = kSmemRc;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = s.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, plan->ah, plan->al, plan->dh, plan->dl,
+                            plan->xh, plan->xl, p);
+}
+
+}  // namespace mhar

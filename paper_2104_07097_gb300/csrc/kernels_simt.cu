@@ -300,6 +300,86 @@ __global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr,
   }
 }
 
+// Recompute mode, one warp per walker:
+//  (1) apply the walker's pending move x += theta (d - A_E^T c') left by the
+//      last chord kernel (Section 4.5), and clear it;
+//  (2) split the point into the FP16 pair of the tensor-core operand, scaled
+//      by a power of two 2^e with max |x_i| 2^-e in [0.5, 1);
+//  (3) draw the next iteration's directions (Section 4.3): into the FP16 pair
+//      directly when there are no equalities, else into the FP32 scratch that
+//      the projection kernel reads.
+// `flags`: bit 0 apply, bit 1 split, bit 2 draw.
+__global__ void prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j,
+                                    uint32_t walker0, int z, int z_ld, int n, int n_ld, int k_pad,
+                                    int mE, float* pend, float* Xhi, float* Xlo, __half* Dh,
+                                    __half* Dl, float* D32, const float* AE32, const float* corr,
+                                    __half* Xh, __half* Xl, float* wscale) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (kThreads / 32) + warp;
+  if (k >= z) return;
+  const size_t xr = static_cast<size_t>(k) * n_ld;
+  const size_t dr = static_cast<size_t>(k) * k_pad;
+  float mx = 0.0f;
+  const float t = (flags & 1) ? pend[k] : 0.0f;
+  if (t != 0.0f) {
+    for (int i = lane; i < n; i += 32) {
+      const float d = __half2float(Dh[dr + i]) + __half2float(Dl[dr + i]);
+      float hi = Xhi[xr + i], lo = Xlo[xr + i];
+      df_axpy(hi, lo, t, d);
+      if (corr != nullptr) {
+        float dlt = 0.0f;
+        for (int e = 0; e < mE; ++e)
+          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
+        lo = fmaf(-t, dlt, lo);
+      }
+      Xhi[xr + i] = hi;
+      Xlo[xr + i] = lo;
+      mx = fmaxf(mx, fabsf(hi));
+    }
+    if (lane == 0) pend[k] = 0.0f;
+  } else if (flags & 2) {
+    for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(Xhi[xr + i]));
+  }
+  if (flags & 2) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
+    const float inv = ldexpf(1.0f, -ex);
+    if (lane == 0) wscale[k] = ldexpf(1.0f, ex);
+    for (int i = lane; i < n; i += 32) {
+      const float v = (Xhi[xr + i] + Xlo[xr + i]) * inv;
+      const __half h = __float2half_rn(v);
+      Xh[dr + i] = h;
+      Xl[dr + i] = __float2half_rn(v - __half2float(h));
+    }
+  }
+  if (flags & 4) {
+    __syncwarp();  // every lane has read the old direction before it is overwritten
+    const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+    const int quads = (n + 3) >> 2;
+    for (int q = lane; q < quads; q += 32) {
+      const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k),
+                                static_cast<uint32_t>(q), kStreamDirection);
+      float v[4];
+      box_muller_f32(w.x, w.y, v[0], v[1]);
+      box_muller_f32(w.z, w.w, v[2], v[3]);
+      const int i0 = 4 * q;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (i0 + e >= n) break;
+        if (mE == 0) {
+          const __half h = __float2half_rn(v[e]);
+          Dh[dr + i0 + e] = h;
+          Dl[dr + i0 + e] = __float2half_rn(v[e] - __half2float(h));
+        } else {
+          D32[xr + i0 + e] = v[e];
+        }
+      }
+    }
+  }
+}
+
 __global__ void advance_kernel(uint64_t* step_ptr, int steps) { *step_ptr += steps; }
 
 __global__ void emit_kernel(int mode, int z, int n, int n_ld, const double* X64, const float* Xhi,
@@ -531,7 +611,8 @@ cudaError_t launch_projection(mhar_ctx* c) {
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
         nullptr, nullptr);
   } else {
-    const int split = c->opts.precision == MHAR_MIXED_F16X3 ? 1 : 0;
+    const int split =
+        (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
         c->d.Dh, c->d.Dl, c->d.corr);
@@ -559,6 +640,15 @@ cudaError_t launch_update_simt(mhar_ctx* c, int j) {
       mode, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->d.key_lo,
       c->d.key_hi, c->d.lmin, c->d.lmax, c->d.theta, c->d.status, c->d.counters, c->d.X64,
       c->d.D64, c->d.Xhi, c->d.Xlo, c->d.D32, c->mE, c->d.AE32, c->d.corr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
+  const int z_ld = (c->z + 127) / 128 * 128;
+  prep_walkers_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
+      flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
+      c->mE, c->d.pend, c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.D32, c->d.AE32, c->d.corr,
+      c->d.Xh, c->d.Xl, c->d.wscale);
   return cudaGetLastError();
 }
 

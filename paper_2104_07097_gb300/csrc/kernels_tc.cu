@@ -35,20 +35,18 @@
 
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
+#include "tc_common.cuh"
 
 namespace mhar {
 namespace {
 
+using namespace tc;
+
 constexpr int kStages = 3;
-constexpr int kWalkers = 128;                         // MMA M
-constexpr int kRowsTile = 128;                        // MMA N per tile
 constexpr int kMaxTilesPerCta = 4;                    // 512 TMEM columns
-constexpr int kOperandBytes = 128 * kTcKChunk * 2;    // one 128 x 64 FP16 tile = 16 KB
 constexpr int kStageBytes = 4 * kOperandBytes;        // A hi, A lo, W hi, W lo
 constexpr int kEpiWarps = 16;                         // 4 per TMEM lane quarter
 constexpr int kThreadsTc = (2 + kEpiWarps) * 32;
-constexpr long long kTimeoutCycles = 4000000000ll;    // ~2 s at 2 GHz
-constexpr int kErrTimeout = 1;
 
 enum : int { kModeChord = 0, kModeRefresh = 1 };
 
@@ -94,152 +92,6 @@ struct SmemTail {
 };
 
 constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + sizeof(SmemTail);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; returns false (and flags the CTA) once the budget is spent or
-// an earlier wait of this CTA already expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* timed_out,
-                                          int* err) {
-  const uint32_t a = smem_u32(bar);
-  if (mbar_try_wait(a, parity)) return true;
-  const long long t0 = clock64();
-  for (;;) {
-#pragma unroll 1
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait(a, parity)) return true;
-    if (*timed_out) return false;
-    if (clock64() - t0 > kTimeoutCycles) {
-      *timed_out = 1;
-      atomicOr(err, kErrTimeout);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor for a K-major operand stored as 128-byte
-// rows with the 128B swizzle (8-row atoms of 1024 bytes).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address
-  d |= static_cast<uint64_t>(1) << 16;                    // leading byte offset (unused)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;            // stride byte offset: 8 rows
-  d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
-  d |= static_cast<uint64_t>(2) << 61;                    // 128B swizzle
-  return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = FP16, D = FP32, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
-__device__ __forceinline__ float ld_dsmem_f32(const float* local, uint32_t rank) {
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
-  return v;
-}
-
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void epi_bar() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-}
 
 // The slack is stored blocked by 4 rows: element (i, k) sits at
 // ((i / 4) z_ld + k) 4 + i % 4, so one 16-byte access gives a walker four
@@ -438,7 +290,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     tail->part_lo[cg][wl] = lo;
     tail->part_hi[cg][wl] = hi;
     const int bad = !(chk == 0.0f);
-    epi_bar();
+    named_bar<kEpiWarps * 32>();
     if (cg == 0) {
       tail->cta_lo[wl] = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
       tail->cta_hi[wl] = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
@@ -488,7 +340,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
       }
       tail->theta[wl] = t;
     }
-    epi_bar();
+    named_bar<kEpiWarps * 32>();
     // ---- chord epilogue, pass 2: S -= G diag(theta) -----------------------------
     const float t = tail->theta[wl];
     if (__any_sync(0xffffffffu, t != 0.0f)) {
@@ -512,26 +364,31 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
       }
     }
     // ---- X += D diag(theta) on this CTA's slice of coordinates ---------------
+    // One flat loop over (walker, coordinate) pairs so every thread keeps
+    // several independent loads in flight.
     const int slice = (p.n + static_cast<int>(csize) - 1) / static_cast<int>(csize);
     const int i_begin = static_cast<int>(rank) * slice;
-    const int i_end = min(p.n, i_begin + slice);
-    for (int w = e; w < kWalkers; w += kEpiWarps) {
+    const int len = max(0, min(p.n, i_begin + slice) - i_begin);
+    const int total = kWalkers * len;
+    const int k_pad = p.k_chunks * kTcKChunk;
+#pragma unroll 4
+    for (int idx = e * 32 + lane; idx < total; idx += kEpiWarps * 32) {
+      const int w = idx / len;
+      const int i = i_begin + (idx - w * len);
       const int kk = strip * kWalkers + w;
       const float tw = tail->theta[w];
       if (kk >= p.z || tw == 0.0f) continue;
-      const size_t xr = static_cast<size_t>(kk) * p.n_ld;
-      const size_t dr = static_cast<size_t>(kk) * (p.k_chunks * kTcKChunk);
-      for (int i = i_begin + lane; i < i_end; i += 32) {
-        const float d = __half2float(p.Dh[dr + i]) + __half2float(p.Dl[dr + i]);
-        df_axpy(p.Xhi[xr + i], p.Xlo[xr + i], tw, d);
-        if (p.corr != nullptr) {
-          // Exact null-space correction of the rounded direction (see projection).
-          float dlt = 0.0f;
-          for (int q2 = 0; q2 < p.mE; ++q2)
-            dlt = fmaf(p.AE32[static_cast<size_t>(q2) * p.n_ld + i],
-                       p.corr[static_cast<size_t>(kk) * p.mE + q2], dlt);
-          p.Xlo[xr + i] = fmaf(-tw, dlt, p.Xlo[xr + i]);
-        }
+      const size_t xr = static_cast<size_t>(kk) * p.n_ld + i;
+      const size_t dr = static_cast<size_t>(kk) * k_pad + i;
+      const float d = __half2float(p.Dh[dr]) + __half2float(p.Dl[dr]);
+      df_axpy(p.Xhi[xr], p.Xlo[xr], tw, d);
+      if (p.corr != nullptr) {
+        // Exact null-space correction of the rounded direction (see projection).
+        float dlt = 0.0f;
+        for (int q2 = 0; q2 < p.mE; ++q2)
+          dlt = fmaf(p.AE32[static_cast<size_t>(q2) * p.n_ld + i],
+                     p.corr[static_cast<size_t>(kk) * p.mE + q2], dlt);
+        p.Xlo[xr] = fmaf(-tw, dlt, p.Xlo[xr]);
       }
     }
   }
@@ -572,42 +429,6 @@ __global__ void split_points_kernel(int z, int z_ld, int n, int n_ld, int k_pad,
     Xh[static_cast<size_t>(k) * k_pad + i] = h;
     Xl[static_cast<size_t>(k) * k_pad + i] = __float2half_rn(v - __half2float(h));
   }
-}
-
-struct TcPlan {
-  CUtensorMap ah, al, dh, dl, xh, xl;
-  int C = 1;
-  int tiles_per_cta = 1;
-  int m_tiles = 1;
-  int strips = 1;
-};
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
-  return fn;
-}
-
-// 2D FP16 map over a (rows x cols) row-major array with 128 x 64 boxes and
-// the 128-byte swizzle the MMA descriptors expect.
-bool make_map(CUtensorMap* map, const void* ptr, int cols, int rows) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * 2};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(kTcKChunk), 128u};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
 }
 
 TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j) {
@@ -676,7 +497,7 @@ int tc_plan_create(mhar_ctx* c) {
   plan->C = (plan->m_tiles + plan->tiles_per_cta - 1) / plan->tiles_per_cta;
   const int z_ld = (c->z + kWalkers - 1) / kWalkers * kWalkers;
   plan->strips = z_ld / kWalkers;
-  if (plan->C > 16) {
+  if (plan->C > 16 && c->opts.precision == MHAR_MIXED_F16X3) {
     delete plan;
     snprintf(c->err, sizeof(c->err),
              "tensor-core mode covers m <= 8192 inequality rows (got m=%d)", c->m);
@@ -710,12 +531,16 @@ void tc_plan_destroy(mhar_ctx* c) {
 
 cudaError_t launch_chord_tc(mhar_ctx* c, int j) { return launch_walker_tc(c, kModeChord, j); }
 
-cudaError_t launch_refresh_tc(mhar_ctx* c) {
+cudaError_t launch_split_points(mhar_ctx* c) {
   const int z_ld = (c->z + kWalkers - 1) / kWalkers * kWalkers;
   split_points_kernel<<<(z_ld + 7) / 8, 256, 0, c->stream>>>(c->z, z_ld, c->n, c->n_ld, c->k_pad,
                                                           c->d.Xhi, c->d.Xlo, c->d.Xh, c->d.Xl,
                                                           c->d.wscale);
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_tc(mhar_ctx* c) {
+  cudaError_t e = launch_split_points(c);
   if (e != cudaSuccess) return e;
   return launch_walker_tc(c, kModeRefresh, 0);
 }

@@ -70,12 +70,18 @@ bool all_finite(const double* p, size_t n) {
   return true;
 }
 
-bool mixed(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_F16X3; }
+// Tensor-core modes (FP16-pair operands).
+bool mixed(const mhar_ctx* c) {
+  return c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE;
+}
+// Stored-slack mode (slack array, refresh).
+bool stored(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_F16X3; }
+bool recompute(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_RECOMPUTE; }
 
 void free_all(mhar_ctx* c) {
   mhar::DeviceBuffers& d = c->d;
   void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.AE64, d.AE32, d.bE64, d.Lchol, d.Ah, d.Al,
-                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale,
+                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale, d.pend,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
                   d.emit, d.check};
   for (void* p : ptrs)
@@ -135,16 +141,35 @@ int kernels_per_iteration(const mhar_ctx* c) {
   return 1 + (c->mE > 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
 }
 
+// Direction draw of one iteration (Section 4.3); in recompute mode the same
+// launch first applies the previous iteration's moves and re-splits X.
+cudaError_t enqueue_directions(mhar_ctx* c, int j) {
+  cudaError_t e = recompute(c) ? mhar::launch_prep_walkers(c, j, 7) : mhar::launch_directions(c, j);
+  if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
+  return e;
+}
+
+// The kernels of one iteration after the direction draw (Sections 4.4-4.5).
+cudaError_t enqueue_chord(mhar_ctx* c, int j) {
+  if (stored(c)) return mhar::launch_chord_tc(c, j);
+  if (recompute(c)) return mhar::launch_recompute_tc(c, j);
+  cudaError_t e = mhar::launch_chord_simt(c);
+  return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
+}
+
+// Recompute mode keeps each walker's last move pending until the next
+// iteration; anything that reads X applies it first.
+int flush_pending(mhar_ctx* c) {
+  if (!recompute(c)) return MHAR_OK;
+  MHAR_CUDA(mhar::launch_prep_walkers(c, 0, 1), "flush kernel");
+  ++c->launches;
+  return MHAR_OK;
+}
+
 int enqueue_iterations(mhar_ctx* c, int count) {
   for (int j = 0; j < count; ++j) {
-    MHAR_CUDA(mhar::launch_directions(c, j), "directions kernel");
-    if (c->mE > 0) MHAR_CUDA(mhar::launch_projection(c), "projection kernel");
-    if (mixed(c)) {
-      MHAR_CUDA(mhar::launch_chord_tc(c, j), "tensor-core chord kernel");
-    } else {
-      MHAR_CUDA(mhar::launch_chord_simt(c), "chord kernel");
-      MHAR_CUDA(mhar::launch_update_simt(c, j), "update kernel");
-    }
+    MHAR_CUDA(enqueue_directions(c, j), "direction kernels");
+    MHAR_CUDA(enqueue_chord(c, j), "chord kernels");
   }
   MHAR_CUDA(mhar::launch_advance(c, count), "advance kernel");
   return MHAR_OK;
@@ -215,6 +240,8 @@ int refresh(mhar_ctx* c) {
 }
 
 int emit_to(mhar_ctx* c, double* out, bool out_device) {
+  int rc = flush_pending(c);
+  if (rc) return rc;
   ++c->launches;
   if (out_device) {
     MHAR_CUDA(mhar::launch_emit(c, out), "emit kernel");
@@ -395,10 +422,11 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     if ((rc = dmalloc(c, &d.Ah, opnd)) || (rc = dmalloc(c, &d.Al, opnd)) ||
         (rc = dmalloc(c, &d.row_scale, c->m_pad)) || (rc = dmalloc(c, &d.bS, c->m_pad)) ||
         (rc = dmalloc(c, &d.Dh, dsz)) || (rc = dmalloc(c, &d.Dl, dsz)) ||
-        (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld)) ||
         (rc = dmalloc(c, &d.Xh, dsz)) || (rc = dmalloc(c, &d.Xl, dsz)) ||
         (rc = dmalloc(c, &d.wscale, z_ld)))
       return rc;
+    if (stored(c) && (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld))) return rc;
+    if (recompute(c) && (rc = dmalloc(c, &d.pend, z_ld))) return rc;
   }
 
   // Projector factor on the device.
@@ -432,7 +460,8 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
   if (mixed(c)) {
     MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
     if ((rc = mhar::tc_plan_create(c))) return rc;
-    if ((rc = reset_drift(c)) || (rc = refresh(c))) return rc;
+    if (recompute(c) && (rc = mhar::rc_prepare(c))) return rc;
+    if (stored(c) && ((rc = reset_drift(c)) || (rc = refresh(c)))) return rc;
   }
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "create sync");
   return MHAR_OK;
@@ -455,7 +484,7 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
     set_err(c, "this build handles 0 <= mE <= %d and mE < n (got mE=%d, n=%d)", kMaxEqualities,
             mE, n);
     rc = MHAR_E_UNSUPPORTED;
-  } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_F16X3 ||
+  } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
              c->opts.refresh_k < 0 || c->opts.graph_chunk < 0) {
     set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d)", c->opts.precision,
             c->opts.refresh_k, c->opts.graph_chunk);
@@ -494,9 +523,9 @@ int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
   if (steps == 0) return MHAR_OK;
   MHAR_CUDA(cudaMemsetAsync(c->d.status, 0, 2 * sizeof(int), c->stream), "status reset");
   int rc;
-  if (mixed(c) && (rc = reset_drift(c))) return rc;
+  if (stored(c) && (rc = reset_drift(c))) return rc;
   int64_t done = 0, emitted = 0;
-  const int64_t k = mixed(c) ? c->opts.refresh_k : 0;
+  const int64_t k = stored(c) ? c->opts.refresh_k : 0;
   while (done < steps) {
     int64_t adv = steps - done;
     if (thin > 0) adv = std::min<int64_t>(adv, thin - (done % thin));
@@ -519,7 +548,7 @@ int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
   MHAR_CUDA(cudaMemcpyAsync(st, c->d.status, sizeof(st), cudaMemcpyDeviceToHost, c->stream),
             "status copy");
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "run sync");
-  if (mixed(c)) {
+  if (stored(c)) {
     unsigned long long kd = 0;
     MHAR_CUDA(cudaMemcpy(&kd, reinterpret_cast<unsigned long long*>(c->d.check) + 2, sizeof(kd),
                          cudaMemcpyDeviceToHost), "drift copy");
@@ -563,10 +592,13 @@ int mhar_set_state(mhar_ctx* c, const double* X, uint64_t step) {
   MHAR_CUDA(cudaMemcpyAsync(c->d.emit, X, sizeof(double) * zn, cudaMemcpyHostToDevice, c->stream),
             "copy X");
   MHAR_CUDA(mhar::launch_set_points(c, c->d.emit), "set points kernel");
+  if (recompute(c))
+    MHAR_CUDA(cudaMemsetAsync(c->d.pend, 0, sizeof(float) * ((c->z + 127) / 128 * 128), c->stream),
+              "clear pending moves");
   MHAR_CUDA(cudaMemcpyAsync(c->d.step, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream),
             "copy step");
   c->step = step;
-  if (mixed(c)) {
+  if (stored(c)) {
     int rc;
     if ((rc = refresh(c))) return rc;
   }
@@ -646,26 +678,19 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   // (1) `iters` real iterations, replayed back to back from one graph.
   auto full = [&]() -> cudaError_t {
     for (int it = 0; it < iters; ++it) {
-      cudaError_t e = mhar::launch_directions(c, it);
-      if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
-      if (e == cudaSuccess) {
-        if (mixed(c)) {
-          e = mhar::launch_chord_tc(c, it);
-        } else {
-          e = mhar::launch_chord_simt(c);
-          if (e == cudaSuccess) e = mhar::launch_update_simt(c, it);
-        }
-      }
+      cudaError_t e = enqueue_directions(c, it);
+      if (e == cudaSuccess) e = enqueue_chord(c, it);
       if (e != cudaSuccess) return e;
     }
     return mhar::launch_advance(c, iters);
   };
   // (2) the direction kernels alone, `iters` times for the current iteration
   // (idempotent: they rewrite the same directions).
+  // (In recompute mode the first of these also applies the last pending
+  // moves; the rest find none.)
   auto dirs = [&]() -> cudaError_t {
     for (int it = 0; it < iters; ++it) {
-      cudaError_t e = mhar::launch_directions(c, 0);
-      if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
+      cudaError_t e = enqueue_directions(c, 0);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -678,7 +703,7 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   e = time_graph(c, dirs, &t_dir);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
   c->launches += static_cast<int64_t>(iters) * (1 + (c->mE > 0 ? 1 : 0));
-  if (mixed(c)) {
+  if (stored(c)) {
     auto ref = [&]() -> cudaError_t {
       cudaError_t e2 = cudaSuccess;
       if (c->mE > 0) e2 = mhar::launch_reproject(c);
@@ -700,6 +725,8 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
 int mhar_check(mhar_ctx* c, mhar_stats* s) {
   if (!c) return MHAR_E_ARG;
   const unsigned long long init[2] = {host_key(-INFINITY), host_key(0.0)};
+  int frc = flush_pending(c);
+  if (frc) return frc;
   MHAR_CUDA(cudaMemcpyAsync(c->d.check, init, sizeof(init), cudaMemcpyHostToDevice, c->stream),
             "check init");
   MHAR_CUDA(mhar::launch_check(c), "check kernel");

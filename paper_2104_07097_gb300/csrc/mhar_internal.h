@@ -45,6 +45,7 @@ struct DeviceBuffers {
   __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
   __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
   float* wscale = nullptr; // z_ld              (mixed: power-of-two scale of each walker)
+  float* pend = nullptr;   // z_ld              (recompute: move theta not yet applied to X)
 
   // Chord bookkeeping.
   unsigned long long* key_lo = nullptr;  // z: ordered key of lambda_min (atomic max)
@@ -97,6 +98,8 @@ cudaError_t launch_projection(mhar_ctx* ctx);
 cudaError_t launch_chord_simt(mhar_ctx* ctx);
 cudaError_t launch_update_simt(mhar_ctx* ctx, int j);
 cudaError_t launch_advance(mhar_ctx* ctx, int steps);
+// Recompute mode: flags bit 0 apply pending moves, bit 1 split X, bit 2 draw D.
+cudaError_t launch_prep_walkers(mhar_ctx* ctx, int j, int flags);
 cudaError_t launch_emit(mhar_ctx* ctx, double* out_device);
 cudaError_t launch_check(mhar_ctx* ctx);
 cudaError_t launch_set_points(mhar_ctx* ctx, const double* X_dev);
@@ -112,5 +115,10 @@ int tc_plan_create(mhar_ctx* ctx);            // 0 or MHAR_E_*
 void tc_plan_destroy(mhar_ctx* ctx);
 cudaError_t launch_chord_tc(mhar_ctx* ctx, int j);
 cudaError_t launch_refresh_tc(mhar_ctx* ctx);       // X split + S = b - A X (2 launches)
+cudaError_t launch_split_points(mhar_ctx* ctx);     // X -> FP16 pair + per-walker scale
+
+// ---- recompute-slack tensor-core path (kernels_rc.cu) ------------------------
+int rc_prepare(mhar_ctx* ctx);                      // 0 or MHAR_E_*
+cudaError_t launch_recompute_tc(mhar_ctx* ctx, int j);
 
 }  // namespace mhar

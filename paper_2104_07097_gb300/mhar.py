@@ -17,7 +17,9 @@ from . import build as _build
 FP64 = 0
 FP32 = 1
 MIXED_F16X3 = 2
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_F16X3, "f16x3": MIXED_F16X3}
+MIXED_RECOMPUTE = 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_F16X3, "f16x3": MIXED_F16X3,
+              "mixed_rs": MIXED_RECOMPUTE}
 
 OK = 0
 E_ARG = -1
@@ -216,7 +218,8 @@ def mhar_chord_noalloc(A_ptr, b_ptr, m: int, n: int, X_ptr, D_ptr, z: int, lmin_
 class Sampler:
     """z MHAR walkers on {A x <= b, AE x = bE} (Algorithm 2), all starting at x0.
 
-    ``precision``: "fp64" | "fp32" | "mixed".  ``stream``: a torch.cuda.Stream,
+    ``precision``: "fp64" | "fp32" | "mixed" (stored slack) | "mixed_rs"
+    (slack recomputed on the tensor cores every iteration).  ``stream``: a torch.cuda.Stream,
     a raw cudaStream_t (int) or None.
     """
 

@@ -14,7 +14,7 @@ from paper_2104_07097_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-4, "mixed": 1e-4}
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "mixed": 1e-4, "mixed_rs": 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +64,7 @@ def test_fp64_free_running_50(body, z):
         assert st.eq_residual <= 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_step_for_step_parity_50(body, z, prec):
     """Each of the first 50 iterations, started from the oracle's own state
@@ -88,7 +88,7 @@ def test_step_for_step_parity_50(body, z, prec):
     assert worst <= TOL[prec], worst
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_free_running_parity(body, z, prec):
     """Free-running chains: within 1e-4 over the first 10 iterations.  Over 50
@@ -105,7 +105,7 @@ def test_free_running_parity(body, z, prec):
         assert st.eq_residual <= 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "mixed_rs"])
 def test_feasible_at_every_step(prec):
     p = wl.simplex_cuts(40, 200, seed=21)
     z = 257
@@ -128,7 +128,7 @@ def test_graph_and_eager_identical():
     np.testing.assert_array_equal(outs[0], outs[2])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_rs"])
 def test_continuation_and_thinning(prec):
     p = wl.random_polytope(30, 250, seed=4)
     with mhar.Sampler(p.A, p.b, p.x0, 96, precision=prec, seed=8) as s:
@@ -142,13 +142,16 @@ def test_continuation_and_thinning(prec):
     np.testing.assert_array_equal(X, a[-1])
 
 
-def test_walker_shards_reproduce_whole_run():
+@pytest.mark.parametrize("prec", ["fp64", "mixed_rs"])
+def test_walker_shards_reproduce_whole_run(prec):
+    # Walkers are independent (Section 4.1) and the generator is counter-based,
+    # so shards with walker0 offsets reproduce the whole ensemble bit for bit.
     p = wl.random_polytope(16, 80, seed=5)
-    with mhar.Sampler(p.A, p.b, p.x0, 100, precision="fp64", seed=4) as s:
+    with mhar.Sampler(p.A, p.b, p.x0, 300, precision=prec, seed=4) as s:
         whole = s.run(10, thin=10)[0]
     parts = []
-    for w0, cnt in ((0, 37), (37, 63)):
-        with mhar.Sampler(p.A, p.b, p.x0, cnt, precision="fp64", seed=4, walker0=w0) as s:
+    for w0, cnt in ((0, 128), (128, 172)):
+        with mhar.Sampler(p.A, p.b, p.x0, cnt, precision=prec, seed=4, walker0=w0) as s:
             parts.append(s.run(10, thin=10)[0])
     np.testing.assert_array_equal(np.vstack(parts), whole)
 
@@ -200,7 +203,7 @@ def test_rank_deficient_equalities_rejected():
     assert e.value.code == mhar.E_RANK
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "mixed_rs"])
 def test_unbounded_body_reported(prec):
     # A half-space: every chord is open on one side (Section 2.1 assumes
     # bounded bodies); the walkers stay and the run reports MHAR_E_UNBOUNDED.

@@ -24,9 +24,10 @@ def rand100():
     return wl.random_polytope(100, 2000, seed=2)
 
 
-def test_full_size_sampled_parity(rand100):
+@pytest.mark.parametrize("prec", ["mixed", "mixed_rs"])
+def test_full_size_sampled_parity(rand100, prec):
     p, z, steps = rand100, 4096, 10
-    with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed", seed=0) as s:
+    with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=0) as s:
         got = s.run(steps, thin=1)
     for w0, cnt in ((0, 12), (2048, 12), (4084, 12)):
         ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (cnt, 1)), steps=steps, thin=1, seed=0,
@@ -35,6 +36,18 @@ def test_full_size_sampled_parity(rand100):
             want = ref["samples"][j]
             err = np.abs(got[j, w0:w0 + cnt] - want).max() / max(1.0, np.abs(want).max())
             assert err <= 1e-4, (w0, j, err)
+
+
+def test_full_size_feasibility_recompute(rand100):
+    # Recomputed slack: every iteration's step is taken from b - A x formed
+    # afresh, so there is no drift to bound; check points every 16 iterations.
+    p, z = rand100, 4096
+    with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=3) as s:
+        samples = s.run(640, thin=16)
+        st = s.check()
+    worst = max(float((X @ p.A.T - p.b).max()) for X in samples)
+    assert worst <= 1e-6, worst
+    assert st.max_violation <= 1e-6 and st.stalls == 0 and st.unbounded == 0
 
 
 @pytest.mark.parametrize("refresh_fp64", [False, True])
@@ -51,10 +64,11 @@ def test_full_size_feasibility_and_drift(rand100, refresh_fp64):
     assert st.stalls == 0 and st.unbounded == 0
 
 
-def test_simplex_cuts_equalities_hold():
+@pytest.mark.parametrize("prec", ["mixed", "mixed_rs"])
+def test_simplex_cuts_equalities_hold(prec):
     p = wl.simplex_cuts(1000, 4000, seed=3)
     z = 1024
-    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision="mixed", seed=1) as s:
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=1) as s:
         samples = s.run(200, thin=50)
         st = s.check()
     for X in samples:
@@ -65,11 +79,12 @@ def test_simplex_cuts_equalities_hold():
     assert np.abs(samples[-1] - p.x0).max() > 1e-3
 
 
-def test_time_kernels_reports_device_times(rand100):
+@pytest.mark.parametrize("prec", ["mixed", "mixed_rs"])
+def test_time_kernels_reports_device_times(rand100, prec):
     p = rand100
-    with mhar.Sampler(p.A, p.b, p.x0, 4096, precision="mixed", seed=0) as s:
+    with mhar.Sampler(p.A, p.b, p.x0, 4096, precision=prec, seed=0) as s:
         ms = s.time_kernels(32)
         X, step = s.state()
     assert step == 32
-    assert 0 < ms[0] < 1.0 and 0 < ms[1] < 5.0 and 0 < ms[2] < 5.0
+    assert 0 < ms[0] < 1.0 and 0 < ms[1] < 5.0 and 0 <= ms[2] < 5.0
     assert (X @ p.A.T - p.b).max() <= 1e-6
