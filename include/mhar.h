@@ -84,7 +84,11 @@ typedef struct {
                              cores from the same FP16-pair operands the walk
                              uses (FP32 accumulation); 1 recomputes it in FP64
                              on CUDA cores (exact, far slower on GB300)       */
-  int32_t  reserved[6];   /* must be zero                                     */
+  int32_t  smem_operands; /* recompute mode: 0 (default) keeps the walker operands
+                             in tensor memory when n <= 128; 1 always streams
+                             them through shared memory (the kernel used for
+                             larger n)                                        */
+  int32_t  reserved[5];   /* must be zero                                     */
 } mhar_opts;
 
 typedef struct {

@@ -191,24 +191,26 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
             ws = w_it % kWSlots;
             mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
           }
+          // Descriptors are built once per slot; one K step of 16 FP16 moves the
+          // start address by 32 bytes, i.e. adds 2 to the descriptor.
           const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
-          const uint32_t dh = w0, dl = w0 + kOperandBytes;
-          const uint32_t xh = w0 + 2 * kOperandBytes, xl = w0 + 3 * kOperandBytes;
+          const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
+          const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
           int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
           ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
           // A hi: the four products that read it; then release its slot.
           int as = a_it % kASlots;
           mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
           tc_fence_after();
-          uint32_t a0 = smem_u32(aslot + as * kABytes);
+          uint64_t ad = sw128_desc(smem_u32(aslot + as * kABytes));
+#pragma unroll 4
           for (int ks = 0; ks < ks_n; ++ks) {
-            const uint32_t off = static_cast<uint32_t>(ks * kTcK * 2);
+            const uint64_t o = static_cast<uint64_t>(2 * ks);
             const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t d_a = sw128_desc(a0 + off);
-            mma_f16(g_tmem, sw128_desc(dh + off), d_a, idesc, acc);
-            mma_f16(g_tmem, sw128_desc(dl + off), d_a, idesc, 1u);
-            mma_f16(p_tmem, sw128_desc(xh + off), d_a, idesc, acc);
-            mma_f16(p_tmem, sw128_desc(xl + off), d_a, idesc, 1u);
+            mma_f16(g_tmem, dh + o, ad + o, idesc, acc);
+            mma_f16(g_tmem, dl + o, ad + o, idesc, 1u);
+            mma_f16(p_tmem, xh + o, ad + o, idesc, acc);
+            mma_f16(p_tmem, xl + o, ad + o, idesc, 1u);
           }
           mma_commit(&tail->a_empty[as]);
           ++a_it;
@@ -216,12 +218,12 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
           as = a_it % kASlots;
           mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
           tc_fence_after();
-          a0 = smem_u32(aslot + as * kABytes);
+          ad = sw128_desc(smem_u32(aslot + as * kABytes));
+#pragma unroll 4
           for (int ks = 0; ks < ks_n; ++ks) {
-            const uint32_t off = static_cast<uint32_t>(ks * kTcK * 2);
-            const uint64_t d_a = sw128_desc(a0 + off);
-            mma_f16(g_tmem, sw128_desc(dh + off), d_a, idesc, 1u);
-            mma_f16(p_tmem, sw128_desc(xh + off), d_a, idesc, 1u);
+            const uint64_t o = static_cast<uint64_t>(2 * ks);
+            mma_f16(g_tmem, dh + o, ad + o, idesc, 1u);
+            mma_f16(p_tmem, xh + o, ad + o, idesc, 1u);
           }
           mma_commit(&tail->a_empty[as]);
           ++a_it;
@@ -245,7 +247,7 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
     for (int nt = 0; nt < ntiles; ++nt) {
       const int b = nt & 1;
-      mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err);
+      mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err, true);
       tc_fence_after();
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
       const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);

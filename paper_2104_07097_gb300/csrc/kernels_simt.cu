@@ -99,7 +99,7 @@ template <typename T>
 __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
                                   const double* __restrict__ AE64, const double* __restrict__ L,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
-                                  float* corr) {
+                                  float* corr, int z_ld, int inter) {
   __shared__ double cbuf[kThreads / 32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
@@ -122,8 +122,9 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     if (split) {
       const float v = static_cast<float>(s);
       const __half hh = __float2half_rn(v);
-      Dh[static_cast<size_t>(k) * k_pad + i] = hh;
-      Dl[static_cast<size_t>(k) * k_pad + i] = __float2half_rn(v - __half2float(hh));
+      const size_t o = op_off(k, i, k_pad, z_ld, inter);
+      Dh[o] = hh;
+      Dl[o] = __float2half_rn(v - __half2float(hh));
     } else {
       h[i] = s;
     }
@@ -136,8 +137,8 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     for (int i = lane; i < n; i += 32) {
       double v;
       if (split)
-        v = static_cast<double>(__half2float(Dh[static_cast<size_t>(k) * k_pad + i])) +
-            static_cast<double>(__half2float(Dl[static_cast<size_t>(k) * k_pad + i]));
+        v = static_cast<double>(__half2float(Dh[op_off(k, i, k_pad, z_ld, inter)])) +
+            static_cast<double>(__half2float(Dl[op_off(k, i, k_pad, z_ld, inter)]));
       else
         v = static_cast<double>(h[i]);
       acc += AE64[static_cast<size_t>(e) * n_ld + i] * v;
@@ -313,17 +314,17 @@ __global__ void prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* st
                                     uint32_t walker0, int z, int z_ld, int n, int n_ld, int k_pad,
                                     int mE, float* pend, float* Xhi, float* Xlo, __half* Dh,
                                     __half* Dl, float* D32, const float* AE32, const float* corr,
-                                    __half* Xh, __half* Xl, float* wscale) {
+                                    __half* Xh, __half* Xl, float* wscale, int inter) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
   if (k >= z) return;
   const size_t xr = static_cast<size_t>(k) * n_ld;
-  const size_t dr = static_cast<size_t>(k) * k_pad;
+  auto opo = [&](int i) { return op_off(k, i, k_pad, z_ld, inter); };
   float mx = 0.0f;
   const float t = (flags & 1) ? pend[k] : 0.0f;
   if (t != 0.0f) {
     for (int i = lane; i < n; i += 32) {
-      const float d = __half2float(Dh[dr + i]) + __half2float(Dl[dr + i]);
+      const float d = __half2float(Dh[opo(i)]) + __half2float(Dl[opo(i)]);
       float hi = Xhi[xr + i], lo = Xlo[xr + i];
       df_axpy(hi, lo, t, d);
       if (corr != nullptr) {
@@ -350,8 +351,8 @@ __global__ void prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* st
     for (int i = lane; i < n; i += 32) {
       const float v = (Xhi[xr + i] + Xlo[xr + i]) * inv;
       const __half h = __float2half_rn(v);
-      Xh[dr + i] = h;
-      Xl[dr + i] = __float2half_rn(v - __half2float(h));
+      Xh[opo(i)] = h;
+      Xl[opo(i)] = __float2half_rn(v - __half2float(h));
     }
   }
   if (flags & 4) {
@@ -370,8 +371,8 @@ __global__ void prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* st
         if (i0 + e >= n) break;
         if (mE == 0) {
           const __half h = __float2half_rn(v[e]);
-          Dh[dr + i0 + e] = h;
-          Dl[dr + i0 + e] = __float2half_rn(v[e] - __half2float(h));
+          Dh[opo(i0 + e)] = h;
+          Dl[opo(i0 + e)] = __float2half_rn(v[e] - __half2float(h));
         } else {
           D32[xr + i0 + e] = v[e];
         }
@@ -609,13 +610,13 @@ cudaError_t launch_projection(mhar_ctx* c) {
   if (c->opts.precision == MHAR_FP64) {
     projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr);
+        nullptr, nullptr, 0, 0);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
-        c->d.Dh, c->d.Dl, c->d.corr);
+        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -648,7 +649,7 @@ cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
   prep_walkers_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
       flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
       c->mE, c->d.pend, c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.D32, c->d.AE32, c->d.corr,
-      c->d.Xh, c->d.Xl, c->d.wscale);
+      c->d.Xh, c->d.Xl, c->d.wscale, c->use_ts ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -228,7 +228,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
       float* Sb = s_block(p, row_base + col, k);
       float sv[32];
       load_s32(p, Sb, sv);
-      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
+      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err, true);
       tc_fence_after();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
@@ -261,7 +261,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     for (int nt = 0; nt < ntiles; ++nt) {
       const int col = nt * kRowsTile + cg * 32;
       if (nt + 1 < ntiles) load_s32(p, s_block(p, row_base + col + kRowsTile, k), s_nxt);
-      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err);
+      mbar_wait(&tail->tfull[nt], 0, timed_out, p.err, true);
       tc_fence_after();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {

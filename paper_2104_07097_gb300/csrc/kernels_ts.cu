@@ -1,0 +1,436 @@
+// kernels_ts.cu -- the recompute-slack walker step with the walker operands
+// resident in tensor memory (MHAR_MIXED_RECOMPUTE mode, n <= 128).
+//
+// Same arithmetic as kernels_rc.cu (Lemma 4.2 on the tensor cores: P = X A^T
+// and G = D A^T from FP16 pairs, three products each, FP32 accumulation;
+// s = b - p; the chord; theta), organised for the case where one walker's
+// operands fit in tensor memory:
+//   * the four walker operands (D hi/lo, X hi/lo: 128 walkers x k_pad FP16,
+//     stored interleaved by 8-element chunks so the loads are coalesced)
+//     are written once into tensor memory (256 columns) and serve as the A
+//     operand of every MMA (tcgen05.mma with A in TMEM), so shared memory
+//     only feeds the rows of A -- half the operand bytes per MMA of the
+//     shared-memory form, which is what limited that form;
+//   * the rows of A stream in 128-row tiles (MMA N = 128) through twelve
+//     16 KB slots (hi and lo staged separately), more than a tile ahead;
+//   * the G and P accumulators of a tile (128 + 128 columns) take the other
+//     256 TMEM columns; the epilogue copies a tile's accumulators to
+//     registers and releases them at once, so the MMAs of the next tile wait
+//     only for that copy.
+// Measured on GB300: an MMA whose operands both come from shared memory needs
+// the SM's whole shared-memory bandwidth at full rate, so the loads of the
+// other warps and the TMA writes slow it; with A in tensor memory it needs
+// half.
+// The cluster layout (C CTAs along the rows, 128 walkers per CTA), the pushed
+// partial chords, the pending-move convention and the bounded waits are those
+// of kernels_rc.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cstdio>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+#include "tc_common.cuh"
+
+namespace mhar {
+namespace {
+
+using namespace tc;
+
+constexpr int kTile = 128;                           // MMA N: rows of A per tile
+constexpr int kSlotBytes = kTile * kTcKChunk * 2;    // 128 x 64 FP16 = 16 KB
+constexpr int kSlots = 12;
+constexpr int kEpiWarps = 16;
+constexpr int kThreadsTs = (2 + kEpiWarps) * 32;
+constexpr int kMaxCluster = 8;
+constexpr uint32_t kOpCol = 256;                     // first TMEM column of the walker operands
+
+struct TsParams {
+  const float* bS;          // m_pad: b_i / row_scale_i
+  const float* wscale;      // z_ld
+  const __half* Dh;         // z_ld x k_pad (operands copied into TMEM at start)
+  const __half* Dl;
+  const __half* Xh;
+  const __half* Xl;
+  float* pend;
+  double* lmin;
+  double* lmax;
+  double* theta;
+  int* status;
+  unsigned long long* counters;
+  int* err;
+  const uint64_t* step_ptr;
+  uint64_t seed;
+  int j;
+  uint32_t walker0;
+  int z, z_ld, kdim, k_chunks, k_pad, tiles_per_cta, m_tiles;
+};
+
+struct TsTail {
+  uint64_t a_full[kSlots];
+  uint64_t a_empty[kSlots];
+  uint64_t t_full;
+  uint64_t t_empty;
+  uint32_t tmem_base;
+  int timed_out;
+  float part_lo[4][kWalkers];
+  float part_hi[4][kWalkers];
+  float recv_lo[kMaxCluster][kWalkers];
+  float recv_hi[kMaxCluster][kWalkers];
+};
+
+constexpr size_t kSmemTs = 1024 + static_cast<size_t>(kSlots) * kSlotBytes + sizeof(TsTail);
+
+__device__ __forceinline__ void st_dsmem(float* local, uint32_t rank, float v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsTs, 1)
+recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+                    const TsParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  TsTail* tail = reinterpret_cast<TsTail*>(base + kSlots * kSlotBytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = blockIdx.x;
+  const int strip = blockIdx.y;
+  const int tile0 = static_cast<int>(rank) * p.tiles_per_cta;
+  int ntiles = p.m_tiles - tile0;
+  ntiles = ntiles < 0 ? 0 : (ntiles > p.tiles_per_cta ? p.tiles_per_cta : ntiles);
+  const int row_base = tile0 * kTile;
+
+  if (threadIdx.x == 32) {
+    prefetch_tmap(&tm_ah);
+    prefetch_tmap(&tm_al);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
+    mbar_init(&tail->t_full, 1);
+    mbar_init(&tail->t_empty, kEpiWarps);
+    tail->timed_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)), "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tail->tmem_base;
+  volatile int* timed_out = &tail->timed_out;
+
+  // ---- walker operands into tensor memory: warp (quarter q, operand op) ------
+  // writes its 32 walkers' row of operand op, 2 FP16 per 32-bit column.
+  if (warp >= 2) {
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int op = e >> 2;
+    const int k = strip * kWalkers + q * 32 + lane;
+    const __half* src = op == 0 ? p.Dh : op == 1 ? p.Dl : op == 2 ? p.Xh : p.Xl;
+    // Operands are interleaved by 8-element chunks: chunk c of walker k is the
+    // 16 bytes at (c z_ld + k) 16, so each load below is one contiguous
+    // 512-byte line for the warp.
+    const uint4* ops = reinterpret_cast<const uint4*>(src);
+    const uint32_t col0 = kOpCol + static_cast<uint32_t>(op * 64);
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    uint32_t r0[32], r1[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint4 v = __ldg(ops + static_cast<size_t>(i) * p.z_ld + k);
+      r0[4 * i] = v.x; r0[4 * i + 1] = v.y; r0[4 * i + 2] = v.z; r0[4 * i + 3] = v.w;
+    }
+    if (p.k_pad > 64) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint4 v = __ldg(ops + static_cast<size_t>(8 + i) * p.z_ld + k);
+        r1[4 * i] = v.x; r1[4 * i + 1] = v.y; r1[4 * i + 2] = v.z; r1[4 * i + 3] = v.w;
+      }
+    }
+    tmem_st32(tmem + lane_off + col0, r0);
+    if (p.k_pad > 64) tmem_st32(tmem + lane_off + col0 + 32u, r1);
+    tmem_st_wait();
+    tc_fence_before();
+    // Operands ready: release the MMA warp (the producer never waits on this).
+    asm volatile("bar.arrive 2, %0;" ::"n"((kEpiWarps + 1) * 32) : "memory");
+  }
+
+  if (warp == 0) {
+    // ---- TMA producer: A rows, 64-row tiles, hi and lo in separate slots ------
+    if (lane == 0) {
+      int it = 0;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        const int yr = row_base + nt * kTile;
+        for (int kc = 0; kc < p.k_chunks; ++kc) {
+          for (int half = 0; half < 2; ++half, ++it) {
+            const int s = it % kSlots;
+            if (it >= kSlots) mbar_wait(&tail->a_empty[s], ((it / kSlots) - 1) & 1, timed_out, p.err);
+            mbar_expect_tx(&tail->a_full[s], kSlotBytes);
+            tma_load_2d(base + s * kSlotBytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s],
+                        kc * kTcKChunk, yr);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------
+    asm volatile("bar.sync 2, %0;" ::"n"((kEpiWarps + 1) * 32) : "memory");
+    tc_fence_after();
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(kWalkers, kTile);
+      const uint32_t op_dh = tmem + kOpCol, op_dl = op_dh + 64u, op_xh = op_dh + 128u,
+                     op_xl = op_dh + 192u;
+      int it = 0;
+      const uint32_t g_tmem = tmem;
+      const uint32_t p_tmem = tmem + 128u;
+      for (int nt = 0; nt < ntiles; ++nt) {
+        // The accumulators are single-buffered: wait until the epilogue has
+        // copied the previous tile out.
+        if (nt >= 1) mbar_wait(&tail->t_empty, (nt - 1) & 1, timed_out, p.err);
+        tc_fence_after();
+        for (int kc = 0; kc < p.k_chunks; ++kc) {
+          int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
+          ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
+          // A hi: D hi, D lo, X hi, X lo times it.  The slot's descriptor is
+          // built once; a K step of 16 FP16 adds 2 to it (32 bytes).
+          int s = it % kSlots;
+          mbar_wait(&tail->a_full[s], (it / kSlots) & 1, timed_out, p.err);
+          tc_fence_after();
+          uint64_t bd = sw128_desc(smem_u32(base + s * kSlotBytes));
+          const uint32_t ac0 = static_cast<uint32_t>(kc * 32);
+#pragma unroll 4
+          for (int ks = 0; ks < ks_n; ++ks) {
+            const uint32_t ac = ac0 + static_cast<uint32_t>(ks * 8);   // 2 FP16 per column
+            const uint64_t b = bd + static_cast<uint64_t>(2 * ks);
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_f16_ts(g_tmem, op_dh + ac, b, idesc, acc);
+            mma_f16_ts(g_tmem, op_dl + ac, b, idesc, 1u);
+            mma_f16_ts(p_tmem, op_xh + ac, b, idesc, acc);
+            mma_f16_ts(p_tmem, op_xl + ac, b, idesc, 1u);
+          }
+          mma_commit(&tail->a_empty[s]);
+          ++it;
+          // A lo: D hi and X hi times it.
+          s = it % kSlots;
+          mbar_wait(&tail->a_full[s], (it / kSlots) & 1, timed_out, p.err);
+          tc_fence_after();
+          bd = sw128_desc(smem_u32(base + s * kSlotBytes));
+#pragma unroll 4
+          for (int ks = 0; ks < ks_n; ++ks) {
+            const uint32_t ac = ac0 + static_cast<uint32_t>(ks * 8);
+            const uint64_t b = bd + static_cast<uint64_t>(2 * ks);
+            mma_f16_ts(g_tmem, op_dh + ac, b, idesc, 1u);
+            mma_f16_ts(p_tmem, op_xh + ac, b, idesc, 1u);
+          }
+          mma_commit(&tail->a_empty[s]);
+          ++it;
+        }
+        mma_commit(&tail->t_full);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;              // 32-column group of each 128-column tile
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    const float ws = p.wscale[k];
+    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    for (int nt = 0; nt < ntiles; ++nt) {
+      mbar_wait(&tail->t_full, nt & 1, timed_out, p.err);
+      tc_fence_after();
+      const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(cg * 32);
+      float g0[16], g1[16], p0[16], p1[16];
+      tmem_ld16(gcol, g0);
+      tmem_ld16(gcol + 16, g1);
+      tmem_ld16(gcol + 128, p0);
+      tmem_ld16(gcol + 144, p1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) arrive(&tail->t_empty);
+      const float4* br4 = reinterpret_cast<const float4*>(p.bS + row_base + nt * kTile + cg * 32);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float br[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v = __ldg(br4 + 4 * h + i);
+          br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float gg = h == 0 ? g0[c] : g1[c];
+          const float pv = h == 0 ? p0[c] : p1[c];
+          const float sv = fmaf(-pv, ws, br[c]);
+          const float ss = fmaxf(sv, 0.0f);
+          chk = fmaf(gg, 0.0f, fmaf(pv, 0.0f, chk));
+          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
+          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
+          const float bnd = gg > 0.0f ? hi : lo;
+          if (ss < bnd * gg) {
+            const float r = __fdividef(ss, gg);
+            if (gg > 0.0f) hi = r; else lo = r;
+          }
+        }
+      }
+    }
+    tail->part_lo[cg][wl] = lo;
+    tail->part_hi[cg][wl] = hi;
+    named_bar<kEpiWarps * 32>();
+    if (cg == 0) {
+      const float L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
+      const float H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
+      st_dsmem(&tail->recv_lo[rank][wl], 0, L);
+      st_dsmem(&tail->recv_hi[rank][wl], 0, H);
+    }
+    if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+  }
+
+  // Every push is visible after this barrier; no remote access follows it.
+  tc_fence_before();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+
+  if (rank == 0 && warp >= 2 && ((warp - 2) >> 2) == 0) {
+    const int q = warp & 3;
+    const int wl = q * 32 + lane;
+    const int k = strip * kWalkers + wl;
+    float L = -INFINITY, H = INFINITY;
+    for (uint32_t r = 0; r < gridDim.x; ++r) {
+      L = fmaxf(L, tail->recv_lo[r][wl]);
+      H = fminf(H, tail->recv_hi[r][wl]);
+    }
+    if (k < p.z) {
+      float t = 0.0f;
+      int flag = 0;
+      if (isinf(L) || isinf(H)) {
+        flag = MHAR_ST_UNBOUNDED;
+      } else if (L > H) {
+        flag = MHAR_ST_STALL;
+      } else {
+        const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+        const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
+                                  kStreamChord);
+        const double u = open_unit_f64(w.x);
+        t = static_cast<float>(static_cast<double>(L) +
+                               u * (static_cast<double>(H) - static_cast<double>(L)));
+      }
+      p.lmin[k] = L;
+      p.lmax[k] = H;
+      p.theta[k] = t;
+      p.pend[k] = t;
+      if (flag) {
+        atomicOr(p.status, flag);
+        atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+      }
+    }
+  }
+}
+
+struct TsShape {
+  int C = 1;
+  int tiles_per_cta = 1;
+  int m_tiles = 1;
+};
+
+TsShape ts_shape(const mhar_ctx* c, const TcPlan* plan) {
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  TsShape s;
+  s.m_tiles = c->m_pad / kTile;
+  int C = sms / plan->strips;
+  C = C < 1 ? 1 : (C > kMaxCluster ? kMaxCluster : C);
+  C = C > s.m_tiles ? s.m_tiles : C;
+  s.tiles_per_cta = (s.m_tiles + C - 1) / C;
+  s.C = (s.m_tiles + s.tiles_per_cta - 1) / s.tiles_per_cta;
+  return s;
+}
+
+}  // namespace
+
+bool ts_eligible(const mhar_ctx* c) { return c->k_pad <= 128; }
+
+int ts_prepare(mhar_ctx* c) {
+  auto* plan = static_cast<TcPlan*>(c->tc);
+  if (!make_map_rows(&plan->ah64, c->d.Ah, c->k_pad, c->m_pad, kTile) ||
+      !make_map_rows(&plan->al64, c->d.Al, c->k_pad, c->m_pad, kTile)) {
+    snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed (64-row maps)");
+    return MHAR_E_CUDA;
+  }
+  cudaError_t e = cudaFuncSetAttribute(recompute_ts_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemTs));
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "recompute (TMEM operand) kernel attributes: %s",
+             cudaGetErrorString(e));
+    cudaGetLastError();
+    return MHAR_E_CUDA;
+  }
+  return MHAR_OK;
+}
+
+cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  const TsShape s = ts_shape(c, plan);
+  TsParams p;
+  p.bS = c->d.bS;
+  p.wscale = c->d.wscale;
+  p.Dh = c->d.Dh;
+  p.Dl = c->d.Dl;
+  p.Xh = c->d.Xh;
+  p.Xl = c->d.Xl;
+  p.pend = c->d.pend;
+  p.lmin = c->d.lmin;
+  p.lmax = c->d.lmax;
+  p.theta = c->d.theta;
+  p.status = c->d.status;
+  p.counters = c->d.counters;
+  p.err = c->d.status + 1;
+  p.step_ptr = c->d.step;
+  p.seed = c->opts.seed;
+  p.j = j;
+  p.walker0 = c->opts.walker0;
+  p.z = c->z;
+  p.z_ld = plan->strips * kWalkers;
+  p.kdim = c->kdim;
+  p.k_chunks = c->k_pad / kTcKChunk;
+  p.k_pad = c->k_pad;
+  p.tiles_per_cta = s.tiles_per_cta;
+  p.m_tiles = s.m_tiles;
+
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(s.C, plan->strips, 1);
+  cfg.blockDim = dim3(kThreadsTs, 1, 1);
+  cfg.dynamicSmemBytes = kSmemTs;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = s.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, recompute_ts_kernel, plan->ah64, plan->al64, p);
+}
+
+}  // namespace mhar

@@ -152,7 +152,7 @@ cudaError_t enqueue_directions(mhar_ctx* c, int j) {
 // The kernels of one iteration after the direction draw (Sections 4.4-4.5).
 cudaError_t enqueue_chord(mhar_ctx* c, int j) {
   if (stored(c)) return mhar::launch_chord_tc(c, j);
-  if (recompute(c)) return mhar::launch_recompute_tc(c, j);
+  if (recompute(c)) return c->use_ts ? mhar::launch_recompute_ts(c, j) : mhar::launch_recompute_tc(c, j);
   cudaError_t e = mhar::launch_chord_simt(c);
   return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
 }
@@ -460,7 +460,10 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
   if (mixed(c)) {
     MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
     if ((rc = mhar::tc_plan_create(c))) return rc;
-    if (recompute(c) && (rc = mhar::rc_prepare(c))) return rc;
+    if (recompute(c)) {
+      c->use_ts = mhar::ts_eligible(c) && c->opts.smem_operands == 0;
+      if ((rc = c->use_ts ? mhar::ts_prepare(c) : mhar::rc_prepare(c))) return rc;
+    }
     if (stored(c) && ((rc = reset_drift(c)) || (rc = refresh(c)))) return rc;
   }
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "create sync");

@@ -76,6 +76,15 @@ __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float& 
   z1 = r * s;
 }
 
+// Offset of element (walker k, coordinate i) of a tensor-core walker operand
+// (FP16 pair of D or X): row-major k * k_pad + i, or interleaved by 8-element
+// chunks, ((i / 8) z_ld + k) 8 + i % 8, so that the same chunk of consecutive
+// walkers is contiguous (one 512-byte line for a warp's 32 walkers).
+__device__ __forceinline__ size_t op_off(int k, int i, int k_pad, int z_ld, int inter) {
+  return inter ? ((static_cast<size_t>(i >> 3) * z_ld + k) << 3) + (i & 7)
+               : static_cast<size_t>(k) * k_pad + i;
+}
+
 // ---- ordered keys for floating-point atomic min / max ---------------------
 // Monotone map: a < b  <=>  key(a) < key(b) (as unsigned), for non-NaN values.
 __device__ __forceinline__ unsigned long long f64_key(double f) {

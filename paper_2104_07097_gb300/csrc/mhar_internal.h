@@ -81,6 +81,7 @@ struct mhar_ctx {
   int64_t launches = 0;        // kernels launched (graph replays add their nodes)
   int64_t launches_chunk = 0;  // kernel nodes in g_chunk
   int64_t launches_one = 0;    // kernel nodes in g_one
+  bool use_ts = false;         // recompute mode: TMEM-operand kernel (n <= 128)
   double last_drift = 0.0;
   double max_violation = 0.0;
   double eq_residual = 0.0;
@@ -120,5 +121,10 @@ cudaError_t launch_split_points(mhar_ctx* ctx);     // X -> FP16 pair + per-walk
 // ---- recompute-slack tensor-core path (kernels_rc.cu) ------------------------
 int rc_prepare(mhar_ctx* ctx);                      // 0 or MHAR_E_*
 cudaError_t launch_recompute_tc(mhar_ctx* ctx, int j);
+
+// ---- recompute-slack, walker operands in tensor memory (kernels_ts.cu) -------
+bool ts_eligible(const mhar_ctx* ctx);              // n <= 128
+int ts_prepare(mhar_ctx* ctx);
+cudaError_t launch_recompute_ts(mhar_ctx* ctx, int j);
 
 }  // namespace mhar

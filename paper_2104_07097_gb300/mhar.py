@@ -45,7 +45,7 @@ class MharOpts(ctypes.Structure):
                 ("refresh_k", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
                 ("walker0", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("graph_chunk", ctypes.c_int32), ("refresh_fp64", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("smem_operands", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class MharStats(ctypes.Structure):
@@ -225,7 +225,8 @@ class Sampler:
 
     def __init__(self, A, b, x0, z: int, AE=None, bE=None, precision: str | int = "fp64",
                  seed: int = 0, refresh_k: int = 64, walker0: int = 0, stream=None,
-                 graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False):
+                 graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False,
+                 smem_operands: bool = False):
         o = mhar_default_opts()
         o.seed = int(seed)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -234,6 +235,7 @@ class Sampler:
         o.graph_chunk = int(graph_chunk)
         o.out_on_device = 1 if out_on_device else 0
         o.refresh_fp64 = 1 if refresh_fp64 else 0
+        o.smem_operands = 1 if smem_operands else 0
         if stream is not None:
             o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         A = _f64(A)

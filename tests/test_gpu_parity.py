@@ -64,7 +64,7 @@ def test_fp64_free_running_50(body, z):
         assert st.eq_residual <= 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs", "mixed_rs_smem"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_step_for_step_parity_50(body, z, prec):
     """Each of the first 50 iterations, started from the oracle's own state
@@ -74,7 +74,10 @@ def test_step_for_step_parity_50(body, z, prec):
     X0 = np.tile(p.x0, (z, 1))
     ref = oracle.mhar_run(p.A, p.b, X0, steps=50, thin=1, seed=5, AE=p.AE, trace=True)
     worst = 0.0
-    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5) as s:
+    kw = {}
+    if prec == "mixed_rs_smem":   # the shared-memory-operand kernel used for n > 128
+        prec, kw = "mixed_rs", {"smem_operands": True}
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5, **kw) as s:
         for j in range(50):
             start = X0 if j == 0 else ref["samples"][j - 1]
             s.set_state(start, j)
