@@ -11,7 +11,10 @@ Functions follow the paper:
   * ``chord_uniform``     -- the uniform that places theta on the chord,
   * ``projector``         -- Section 3.2, P = I - A_E^T (A_E A_E^T)^{-1} A_E,
   * ``chord``             -- Section 4.4, (lambda_min, lambda_max),
-  * ``mhar_run``          -- Algorithm 2 (z walks, thinning).
+  * ``mhar_run``          -- Algorithm 2 (z walks, thinning),
+  * ``stream_normals``    -- the same Box-Muller normals on any Philox stream,
+  * ``mhar_run_pre``      -- Algorithm 2 with preconditioned directions
+                             d = P (delta * h + U g) (``oracle.precond`` fits them).
 """
 from __future__ import annotations
 
@@ -31,6 +34,11 @@ _LIB = os.path.join(_BUILD, "libmhar_oracle.so")
 UNBOUNDED = 1
 STALL = 2
 NONFINITE = 4
+
+STREAM_DIRECTION = 0
+STREAM_CHORD = 1
+STREAM_LOWRANK = 2
+STREAM_FIT = 3
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +81,14 @@ def _load():
                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                      ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
         lib.orc_mhar_run.restype = ctypes.c_int
+        lib.orc_stream_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_uint32, ctypes.c_int, dp]
+        lib.orc_stream_normals.restype = None
+        lib.orc_mhar_run_pre.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                         ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_int64, ctypes.c_int64, dp, dp, ctypes.c_int,
+                                         dp, dp, dp, dp]
+        lib.orc_mhar_run_pre.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -101,6 +117,14 @@ def direction_normals(seed: int, step: int, walker: int, n: int) -> np.ndarray:
     h = np.zeros(n, dtype=np.float64)
     lib.orc_direction_normals(seed, step, walker, n, _ptr(h))
     return h
+
+
+def stream_normals(seed: int, step: int, walker: int, stream: int, count: int) -> np.ndarray:
+    """``count`` N(0,1) values of Philox stream ``stream`` for (step, walker)."""
+    lib = _load()
+    h = np.zeros(max(count, 1), dtype=np.float64)
+    lib.orc_stream_normals(seed, step, walker, stream, count, _ptr(h))
+    return h[:count]
 
 
 def chord_uniform(seed: int, step: int, walker: int) -> float:
@@ -138,6 +162,16 @@ def mhar_run(A, b, X0, steps: int, thin: int = 1, seed: int = 0, step0: int = 0,
     ``status`` and, when ``trace``, ``t``, ``lmin``, ``lmax`` (steps x z).
     ``P`` may be passed to reuse a projector; otherwise it is built from ``AE``.
     """
+    return mhar_run_pre(A, b, X0, steps, None, None, thin=thin, seed=seed, step0=step0, AE=AE,
+                        walker0=walker0, P=P, trace=trace)
+
+
+def mhar_run_pre(A, b, X0, steps: int, delta, U, thin: int = 1, seed: int = 0, step0: int = 0,
+                 AE=None, walker0: int = 0, P=None, trace: bool = False):
+    """Algorithm 2 with directions d = P (delta * h + U g); ``delta`` None = isotropic.
+
+    ``U`` is n x r (r <= 32) or None (diagonal preconditioner only).
+    """
     A = _f64(A)
     b = _f64(b)
     m, n = A.shape
@@ -148,6 +182,16 @@ def mhar_run(A, b, X0, steps: int, thin: int = 1, seed: int = 0, step0: int = 0,
     if P is None and AE is not None and np.size(AE) > 0:
         P = projector(AE)
     P = None if P is None else _f64(P)
+    r = 0
+    if delta is not None:
+        delta = _f64(delta).reshape(n)
+        if U is not None:
+            U = _f64(U).reshape(n, -1)
+            r = U.shape[1]
+            if r > 32:
+                raise ValueError("rank must be <= 32")
+    elif U is not None:
+        raise ValueError("U needs delta")
     nsamp = steps // thin if thin > 0 else 0
     out = np.zeros((nsamp, z, n), dtype=np.float64)
     t_tr = lmin_tr = lmax_tr = None
@@ -155,9 +199,10 @@ def mhar_run(A, b, X0, steps: int, thin: int = 1, seed: int = 0, step0: int = 0,
         t_tr = np.zeros((steps, z))
         lmin_tr = np.zeros((steps, z))
         lmax_tr = np.zeros((steps, z))
-    st = _load().orc_mhar_run(_ptr(A), _ptr(b), m, n, _ptr(P), _ptr(X), z, walker0, seed, step0,
-                              steps, thin, _ptr(out) if nsamp > 0 else None, _ptr(t_tr),
-                              _ptr(lmin_tr), _ptr(lmax_tr))
+    st = _load().orc_mhar_run_pre(_ptr(A), _ptr(b), m, n, _ptr(P), _ptr(X), z, walker0, seed,
+                                  step0, steps, thin, _ptr(delta), _ptr(U if r > 0 else None), r,
+                                  _ptr(out) if nsamp > 0 else None, _ptr(t_tr), _ptr(lmin_tr),
+                                  _ptr(lmax_tr))
     if st < 0:
         raise MemoryError("oracle allocation failed")
     res = {"X": X, "samples": out, "status": st}

@@ -68,12 +68,13 @@ static void box_muller(double ua, double ub, double* z0, double* z1) {
   *z1 = r * sin(th);
 }
 
-void orc_direction_normals(uint64_t seed, uint64_t step, uint32_t walker, int n, double* h) {
+void orc_stream_normals(uint64_t seed, uint64_t step, uint32_t walker, uint32_t stream, int n,
+                        double* h) {
   uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   int quads = (n + 3) / 4;
   for (int q = 0; q < quads; ++q) {
     uint32_t ctr[4], w[4];
-    make_counter((uint32_t)q, walker, step, ORC_STREAM_DIRECTION, ctr);
+    make_counter((uint32_t)q, walker, step, stream, ctr);
     orc_philox4x32_10(ctr, key, w);
     double z[4];
     box_muller(word_to_open_uniform(w[0]), word_to_open_uniform(w[1]), &z[0], &z[1]);
@@ -83,6 +84,10 @@ void orc_direction_normals(uint64_t seed, uint64_t step, uint32_t walker, int n,
       if (i < n) h[i] = z[e];
     }
   }
+}
+
+void orc_direction_normals(uint64_t seed, uint64_t step, uint32_t walker, int n, double* h) {
+  orc_stream_normals(seed, step, walker, ORC_STREAM_DIRECTION, n, h);
 }
 
 double orc_chord_uniform(uint64_t seed, uint64_t step, uint32_t walker) {
@@ -189,13 +194,15 @@ int orc_chord(const double* A, const double* b, int m, int n,
 /* Walks are independent (Section 4.1), so the loop over k is just the         */
 /* columns of the padded matrices taken one at a time.                         */
 /* ------------------------------------------------------------------------- */
-int orc_mhar_run(const double* A, const double* b, int m, int n,
-                 const double* P, double* X, int z, uint32_t walker0,
-                 uint64_t seed, uint64_t step0, int64_t steps, int64_t thin,
-                 double* out, double* t_tr, double* lmin_tr, double* lmax_tr) {
+int orc_mhar_run_pre(const double* A, const double* b, int m, int n,
+                     const double* P, double* X, int z, uint32_t walker0,
+                     uint64_t seed, uint64_t step0, int64_t steps, int64_t thin,
+                     const double* delta, const double* U, int r,
+                     double* out, double* t_tr, double* lmin_tr, double* lmax_tr) {
   double* h = (double*)malloc((size_t)n * sizeof(double));
   double* d = (double*)malloc((size_t)n * sizeof(double));
-  if (!h || !d) { free(h); free(d); return -1; }
+  double* g = (double*)malloc((size_t)(r > 0 ? r : 1) * sizeof(double));
+  if (!h || !d || !g) { free(h); free(d); free(g); return -1; }
   int status = 0;
   int64_t emitted = 0;
   for (int64_t j = 0; j < steps; ++j) {
@@ -205,12 +212,21 @@ int orc_mhar_run(const double* A, const double* b, int m, int n,
       double* x = X + (size_t)k * n;
       /* Generate h^k (Section 4.3). */
       orc_direction_normals(seed, step, walker, n, h);
+      /* Preconditioned draw: h <- delta .* h + U g (centrally symmetric). */
+      if (delta) {
+        if (r > 0) orc_stream_normals(seed, step, walker, ORC_STREAM_LOWRANK, r, g);
+        for (int i = 0; i < n; ++i) {
+          double s = delta[i] * h[i];
+          for (int c = 0; c < r; ++c) s += U[(size_t)i * r + c] * g[c];
+          h[i] = s;
+        }
+      }
       /* d^k = h^k, or P h^k when there are equalities. */
       if (P) {
-        for (int r = 0; r < n; ++r) {
+        for (int row = 0; row < n; ++row) {
           double s = 0.0;
-          for (int c = 0; c < n; ++c) s += P[(size_t)r * n + c] * h[c];
-          d[r] = s;
+          for (int c = 0; c < n; ++c) s += P[(size_t)row * n + c] * h[c];
+          d[row] = s;
         }
       } else {
         memcpy(d, h, (size_t)n * sizeof(double));
@@ -230,7 +246,7 @@ int orc_mhar_run(const double* A, const double* b, int m, int n,
         t = lo + u * (hi - lo);
       }
       status |= st;
-      for (int r = 0; r < n; ++r) x[r] += t * d[r];
+      for (int i = 0; i < n; ++i) x[i] += t * d[i];
       if (t_tr) t_tr[(size_t)j * z + k] = t;
       if (lmin_tr) lmin_tr[(size_t)j * z + k] = lo;
       if (lmax_tr) lmax_tr[(size_t)j * z + k] = hi;
@@ -243,5 +259,15 @@ int orc_mhar_run(const double* A, const double* b, int m, int n,
   }
   free(h);
   free(d);
+  free(g);
   return status;
+}
+
+/* Algorithm 2 with isotropic directions (Section 4.3). */
+int orc_mhar_run(const double* A, const double* b, int m, int n,
+                 const double* P, double* X, int z, uint32_t walker0,
+                 uint64_t seed, uint64_t step0, int64_t steps, int64_t thin,
+                 double* out, double* t_tr, double* lmin_tr, double* lmax_tr) {
+  return orc_mhar_run_pre(A, b, m, n, P, X, z, walker0, seed, step0, steps, thin, NULL, NULL, 0,
+                          out, t_tr, lmin_tr, lmax_tr);
 }

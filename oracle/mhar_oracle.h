@@ -35,6 +35,8 @@ extern "C" {
 /* Random-stream ids, carried in the top byte of counter word 3. */
 #define ORC_STREAM_DIRECTION 0u
 #define ORC_STREAM_CHORD     1u
+#define ORC_STREAM_LOWRANK   2u   /* the r low-rank normals of a preconditioned direction */
+#define ORC_STREAM_FIT       3u   /* the starting block of the preconditioner fit        */
 
 /* Status bits returned by orc_chord / orc_mhar_run (OR-ed over walkers). */
 #define ORC_UNBOUNDED 1   /* no row with a.d > 0 or no row with a.d < 0      */
@@ -49,6 +51,12 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * key = (seed_lo32, seed_hi32).  Each 32-bit word w maps to u = (w + 1/2) 2^-32;
  * Box-Muller on (u0,u1) gives h[4q], h[4q+1]; on (u2,u3) gives h[4q+2], h[4q+3]. */
 void orc_direction_normals(uint64_t seed, uint64_t step, uint32_t walker, int n, double* h);
+
+/* `count` N(0,1) values of stream `stream` for (step, walker): quads q with
+ * counter (q, walker, step_lo32, (step_hi24 << 8) | stream), Box-Muller as
+ * above.  Stream 0 is orc_direction_normals. */
+void orc_stream_normals(uint64_t seed, uint64_t step, uint32_t walker, uint32_t stream, int count,
+                        double* out);
 
 /* u in (0,1) for the point drawn on walker `walker`'s chord at step `step`:
  * counter (0, walker, step_lo32, (step_hi24 << 8) | STREAM_CHORD), word 0. */
@@ -77,6 +85,17 @@ int orc_mhar_run(const double* A, const double* b, int m, int n,
                  const double* P, double* X, int z, uint32_t walker0,
                  uint64_t seed, uint64_t step0, int64_t steps, int64_t thin,
                  double* out, double* t_tr, double* lmin_tr, double* lmax_tr);
+
+/* Same with a direction preconditioner: each direction is
+ *   d = P (delta .* h + U g),   h ~ N(0, I_n) (stream 0),  g ~ N(0, I_r) (stream 2),
+ * delta (n), U (n x r row-major), 1 <= r <= 32 or r == 0 with U NULL (diagonal only).
+ * The law of d is centrally symmetric, so the chain still targets the
+ * uniform distribution on the body. */
+int orc_mhar_run_pre(const double* A, const double* b, int m, int n,
+                     const double* P, double* X, int z, uint32_t walker0,
+                     uint64_t seed, uint64_t step0, int64_t steps, int64_t thin,
+                     const double* delta, const double* U, int r,
+                     double* out, double* t_tr, double* lmin_tr, double* lmax_tr);
 
 #ifdef __cplusplus
 }
