@@ -7,6 +7,15 @@ One bench step = one full run of the workload: z = 4096 walkers advanced
 the final points written to a device buffer.  Metric: walker-steps/s
 (= z x iterations / time, the paper's "samples per second" of Section 6.2).
 
+The same line carries the mixing side of the metric ("ess"): on the
+ill-conditioned random polytope (n = 500, m = 10000, axes scaled by s with
+log s ~ U[ln 1e-3, 0], z = 16384) it times a learned-preconditioner run (500
+warm-up iterations in four fit rounds, rank-32 + diagonal fit on the device,
+then 5000 frozen iterations, tensor-core recompute mode) against plain isotropic runs (FP32 on
+CUDA cores, and the same tensor-core mode), each with 500 + 5000 iterations,
+and reports min-ESS (over coordinates, from a trace of 64 walkers every 5th
+iteration, scaled to all z walkers) per second of device time.
+
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
 """
@@ -31,6 +40,9 @@ WORKLOAD = dict(name="rand100x2000", n=100, m=2000, seed=2, z=4096, iterations=2
 METRIC = "walker-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
+ESS_WORKLOAD = dict(name="illcond500x10000", n=500, m=10000, seed=5, z=16384, warmup=500,
+                    iterations=5000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
+                    snapshots=5, power_iters=4)
 REF_SAMPLE = dict(walkers=64, iterations=20)
 
 
@@ -154,6 +166,52 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def ess_leg(stream, torch, mhar) -> dict:
+    """min-ESS/s of learned-preconditioned vs plain MHAR on the ill-conditioned body."""
+    from paper_2104_07097_gb300 import diagnostics
+    E = ESS_WORKLOAD
+    p = wl.ill_conditioned(E["n"], E["m"], seed=E["seed"])
+    z, T, W, every = E["z"], E["iterations"], E["trace_walkers"], E["trace_every"]
+    out = torch.empty((T // every, W, p.n), dtype=torch.float64, device="cuda")
+    arms = {}
+    for name, prec, learned in (("learned_mixed_rs", "mixed_rs", True),
+                                ("plain_mixed_rs", "mixed_rs", False),
+                                ("plain_fp32", "fp32", False)):
+        with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=0, stream=stream,
+                          out_on_device=True, emit_walkers=W) as smp:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            if learned:
+                # Each round warms up with the previous round's directions and refits.
+                for _ in range(E["fit_rounds"]):
+                    smp.fit_preconditioner(E["warmup"] // E["fit_rounds"], E["snapshots"],
+                                           E["rank"], E["power_iters"])
+            else:
+                smp.run(E["warmup"])
+            smp.run(T, thin=every, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            secs = a.elapsed_time(b) / 1e3
+            st = smp.check()
+        trace = out.cpu().numpy()
+        ess = diagnostics.ess_per_coordinate(trace) * (z / W)
+        arms[name] = {"min_ess": float(ess.min()), "median_ess": float(np.median(ess)),
+                      "seconds": secs, "min_ess_per_s": float(ess.min()) / secs,
+                      "walker_steps_per_s": z * (E["warmup"] + T) / secs,
+                      "max_violation": st.max_violation}
+    return {"workload": f"{E['name']} z={z}: {E['warmup']} warm-up + {T} iterations",
+            "trace": f"{W} walkers, every {every}th iteration; ESS scaled by z/{W}; Geyer initial "
+                     f"monotone sequence",
+            "learned": f"rank {E['rank']} + diagonal, fitted on the device in {E['fit_rounds']} rounds "
+                       f"of {E['warmup'] // E['fit_rounds']} warm-up iterations ({E['snapshots']} "
+                       f"snapshots, {E['power_iters']} power iterations each), then frozen; "
+                       f"warm-up and fits are inside the timed region",
+            "arms": arms,
+            "min_ess_per_s_learned_vs_plain_fp32":
+                arms["learned_mixed_rs"]["min_ess_per_s"] / arms["plain_fp32"]["min_ess_per_s"]}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,6 +220,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed_rs", choices=["mixed_rs", "mixed", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ess", action="store_true", help="skip the min-ESS/s comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -292,6 +351,8 @@ def main() -> None:
                 "feasibility": {"max_violation": st.max_violation, "refresh_drift": st.refresh_drift,
                                 "stalls": st.stalls},
                 "plain_fp32": plain}
+        if world == 1 and not args.no_ess:
+            line["ess"] = ess_leg(stream, torch, mhar)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)

@@ -88,7 +88,10 @@ typedef struct {
                              in tensor memory when n <= 128; 1 always streams
                              them through shared memory (the kernel used for
                              larger n)                                        */
-  int32_t  reserved[5];   /* must be zero                                     */
+  int32_t  emit_walkers;  /* samples written by mhar_run hold walkers 0..W-1
+                             only (0 = all z); e.g. a trace of a subset for
+                             effective-sample-size estimates                 */
+  int32_t  reserved[4];   /* must be zero                                     */
 } mhar_opts;
 
 typedef struct {
@@ -134,8 +137,8 @@ int mhar_create(const double* A, const double* b, int m, int n,
 
 /* Advances every walker `steps` iterations (Algorithm 2's loop) and writes
  * floor(steps / thin) samples to `out`, laid out out[s][k][i] (s-th sample,
- * walker k, coordinate i; FP64): the points after iterations thin, 2 thin, ...
- * of this call.  `out` may be NULL when steps < thin.  It is host memory
+ * walker k < W, coordinate i; FP64; W = opts.emit_walkers, or z when 0): the
+ * points after iterations thin, 2 thin, ... of this call.  `out` may be NULL when steps < thin.  It is host memory
  * unless opts.out_on_device.  Iteration counters (and thus the random
  * streams) continue across calls.  Returns MHAR_E_UNBOUNDED /
  * MHAR_E_NONFINITE if any walker met that condition during the call (the
@@ -201,6 +204,55 @@ int mhar_time_kernels(mhar_ctx* ctx, int iters, double* ms);
 int mhar_chord_noalloc(const double* A, const double* b, int m, int n,
                        const double* X, const double* D, int z,
                        double* lmin, double* lmax, void* stream);
+
+/* ---- learned direction preconditioner ----------------------------------- */
+/* The paper draws isotropic directions (Section 4.3) and assumes the body was
+ * brought to near-isotropic position beforehand (Sections 1.2 and 3.1).  With
+ * a preconditioner set, walker k's direction at every iteration becomes
+ *     d = P (delta .* h + U g),
+ * h ~ N(0, I_n) the Section 4.3 draw (Philox stream 0), g ~ N(0, I_r) from
+ * Philox stream 2 (quad q of walker k at step t: counter (q, k, t_lo,
+ * (t_hi << 8) | 2)), P the projector of Section 3.2 (identity when mE == 0).
+ * The law of d does not depend on the walker's position and is centrally
+ * symmetric, so the uniform distribution on the body stays the target of
+ * the walk; only the speed of mixing changes.
+ * In the tensor-core modes the library also rescales each coordinate of the
+ * FP16 operands by a power of two chosen from diag(delta^2) + diag(U U^T)
+ * (A's columns take the inverse scale; A x and A d are unchanged), so bodies
+ * whose axes differ by orders of magnitude keep their relative precision. */
+
+/* Sets the preconditioner (delta != NULL) or removes it (delta == NULL:
+ * isotropic directions again).  delta: n values, finite, >= 0; U: n x rank,
+ * row-major, NULL when rank == 0; 0 <= rank <= 32.  The library copies both.
+ * Moves still pending from the last iteration are applied first; the next
+ * mhar_run re-captures its graphs.  MHAR_E_ARG on a bad rank or pointer,
+ * MHAR_E_NONFINITE on a non-finite entry. */
+int mhar_set_preconditioner(mhar_ctx* ctx, const double* delta, const double* U, int32_t rank);
+
+/* Current preconditioner: *rank = -1 when none is set (delta and U are then
+ * left untouched), else its rank, delta (n values) and U (n x rank,
+ * row-major).  Any pointer may be NULL. */
+int mhar_get_preconditioner(const mhar_ctx* ctx, double* delta, double* U, int32_t* rank);
+
+/* Learns a preconditioner from the chain itself and freezes it.
+ * Runs `warmup` iterations with the directions in force (their points are not
+ * emitted), and keeps `snapshots` copies of all z points: after iterations
+ * warmup - (snapshots - 1 - s) gap, s = 0..snapshots-1, gap =
+ * max(1, floor(warmup / (2 snapshots))).  From those N = z snapshots points:
+ *   Sigma = sum (x - mu)(x - mu)^T / (N - 1)                      (FP64)
+ *   Y = Sigma Omega, Omega n x rank with column c = Philox stream 3 normals
+ *     of walker c at step 0; `power_iters` times Q = orth(Y), Y = Sigma Q;
+ *     Q = orth(Y) (Q factor of the thin QR with a positive diagonal in R)
+ *   T = Q^T Sigma Q = V Lambda V^T; U = Q V Lambda_+^{1/2} (largest first)
+ *   delta_i^2 = max(Sigma_ii - (U U^T)_ii, 1e-2 Sigma_ii, 1e-9 trace(Sigma)/n)
+ * then sets (delta, U) as mhar_set_preconditioner does.  All of it runs on
+ * the device; scratch memory (about 8 n^2 bytes) is allocated for the call.
+ * Requires warmup >= 1, 1 <= snapshots <= warmup, z * snapshots >= 2,
+ * 0 <= rank <= min(32, n), 0 <= power_iters <= 64 (else MHAR_E_ARG).  Returns
+ * what the warm-up mhar_run returned if that failed, MHAR_E_NONFINITE if the
+ * covariance is not finite. */
+int mhar_fit_preconditioner(mhar_ctx* ctx, int64_t warmup, int32_t snapshots, int32_t rank,
+                            int32_t power_iters);
 
 /* Human-readable description of the last error on ctx (never NULL); with
  * ctx == NULL, the last mhar_chord_noalloc failure on this host thread. */

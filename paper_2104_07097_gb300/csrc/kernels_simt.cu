@@ -99,7 +99,7 @@ template <typename T>
 __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
                                   const double* __restrict__ AE64, const double* __restrict__ L,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
-                                  float* corr, int z_ld, int inter) {
+                                  float* corr, int z_ld, int inter, const float* sigma) {
   __shared__ double cbuf[kThreads / 32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
@@ -120,7 +120,7 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     T s = h[i];
     for (int e = 0; e < mE; ++e) s -= AE[static_cast<size_t>(e) * n_ld + i] * static_cast<T>(c[e]);
     if (split) {
-      const float v = static_cast<float>(s);
+      const float v = static_cast<float>(s) / sigma[i];  // power of two: exact
       const __half hh = __float2half_rn(v);
       const size_t o = op_off(k, i, k_pad, z_ld, inter);
       Dh[o] = hh;
@@ -137,8 +137,9 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     for (int i = lane; i < n; i += 32) {
       double v;
       if (split)
-        v = static_cast<double>(__half2float(Dh[op_off(k, i, k_pad, z_ld, inter)])) +
-            static_cast<double>(__half2float(Dl[op_off(k, i, k_pad, z_ld, inter)]));
+        v = (static_cast<double>(__half2float(Dh[op_off(k, i, k_pad, z_ld, inter)])) +
+             static_cast<double>(__half2float(Dl[op_off(k, i, k_pad, z_ld, inter)]))) *
+            static_cast<double>(sigma[i]);
       else
         v = static_cast<double>(h[i]);
       acc += AE64[static_cast<size_t>(e) * n_ld + i] * v;
@@ -151,6 +152,72 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
   if (lane == 0) {
     cholesky_solve(L, mE, c);
     for (int e = 0; e < mE; ++e) corr[static_cast<size_t>(k) * mE + e] = static_cast<float>(c[e]);
+  }
+}
+
+// ---- preconditioned directions ---------------------------------------------
+// d = delta .* h + U g for a block of 32 walkers x 128 coordinates: the block
+// draws the 32 walkers' low-rank normals g (Philox stream 2, Box-Muller as in
+// Section 4.3) into shared memory; each thread keeps its coordinate's row of U
+// in registers and walks the 32 walkers (coalesced along coordinates).
+// In place on the FP64 / FP32 normals, or (split) into the FP16 operand pair
+// as d_i / sigma_i.  The projection (when m_E > 0) follows on the result.
+constexpr int kPcWalkers = 32;
+constexpr int kPcThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kPcThreads)
+precondition_kernel(uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0, int z,
+                    int n, int n_ld, int rank, const T* __restrict__ delta,
+                    const T* __restrict__ U, T* D, int split, int k_pad, int z_ld, int inter,
+                    const float* sigma, __half* Dh, __half* Dl) {
+  __shared__ T g[kPcWalkers][kMaxPcRank + 1];
+  const int k0 = blockIdx.y * kPcWalkers;
+  for (int t = threadIdx.x; t < kPcWalkers * (kMaxPcRank + 1); t += kPcThreads)
+    g[t / (kMaxPcRank + 1)][t % (kMaxPcRank + 1)] = T(0);
+  __syncthreads();
+  const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+  const int quads = (rank + 3) >> 2;
+  for (int t = threadIdx.x; t < kPcWalkers * quads; t += kPcThreads) {
+    const int w = t / quads, q = t - (t / quads) * quads;
+    if (k0 + w >= z) continue;
+    const U4 r = philox_block(seed, step, walker0 + static_cast<uint32_t>(k0 + w),
+                              static_cast<uint32_t>(q), kStreamLowRank);
+    T v[4];
+    if constexpr (sizeof(T) == 8) {
+      box_muller_f64(open_unit_f64(r.x), open_unit_f64(r.y), v[0], v[1]);
+      box_muller_f64(open_unit_f64(r.z), open_unit_f64(r.w), v[2], v[3]);
+    } else {
+      box_muller_f32(r.x, r.y, v[0], v[1]);
+      box_muller_f32(r.z, r.w, v[2], v[3]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * q + e < rank) g[w][4 * q + e] = v[e];
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kPcThreads + threadIdx.x;
+  if (i >= n) return;
+  T u[kMaxPcRank];
+#pragma unroll
+  for (int c = 0; c < kMaxPcRank; ++c) u[c] = U[static_cast<size_t>(i) * kMaxPcRank + c];
+  const T di = delta[i];
+  const float inv_sigma = split ? 1.0f / sigma[i] : 1.0f;  // power of two: exact
+  const int wend = min(kPcWalkers, z - k0);
+  for (int w = 0; w < wend; ++w) {
+    const int k = k0 + w;
+    T acc = di * D[static_cast<size_t>(k) * n_ld + i];
+#pragma unroll
+    for (int c = 0; c < kMaxPcRank; ++c) acc = fma(u[c], g[w][c], acc);
+    if (split) {
+      const float v = static_cast<float>(acc) * inv_sigma;
+      const __half h = __float2half_rn(v);
+      const size_t o = op_off(k, i, k_pad, z_ld, inter);
+      Dh[o] = h;
+      Dl[o] = __float2half_rn(v - __half2float(h));
+    } else {
+      D[static_cast<size_t>(k) * n_ld + i] = acc;
+    }
   }
 }
 
@@ -301,81 +368,159 @@ __global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr,
   }
 }
 
-// Recompute mode, one warp per walker:
+// Recompute mode, per iteration and walker:
 //  (1) apply the walker's pending move x += theta (d - A_E^T c') left by the
 //      last chord kernel (Section 4.5), and clear it;
-//  (2) split the point into the FP16 pair of the tensor-core operand, scaled
-//      by a power of two 2^e with max |x_i| 2^-e in [0.5, 1);
+//  (2) split the point into the FP16 pair of the tensor-core operand, as
+//      x_i / (sigma_i 2^e) with 2^e a power of two such that
+//      max_i |x_i| / sigma_i 2^-e lies in [0.5, 1);
 //  (3) draw the next iteration's directions (Section 4.3): into the FP16 pair
-//      directly when there are no equalities, else into the FP32 scratch that
-//      the projection kernel reads.
+//      directly when neither a projection nor a preconditioner follows, else
+//      into the FP32 scratch those kernels read.
 // `flags`: bit 0 apply, bit 1 split, bit 2 draw.
-__global__ void prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j,
-                                    uint32_t walker0, int z, int z_ld, int n, int n_ld, int k_pad,
-                                    int mE, float* pend, float* Xhi, float* Xlo, __half* Dh,
-                                    __half* Dl, float* D32, const float* AE32, const float* corr,
-                                    __half* Xh, __half* Xl, float* wscale, int inter) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * (kThreads / 32) + warp;
-  if (k >= z) return;
+// Layout: 32 walkers per block, one per lane; each warp takes 8-coordinate
+// chunks (warp, warp + warps, ...).  A thread reads and writes whole chunks:
+// 32 B of each FP32 row and 16 B of each FP16 operand, so in the interleaved
+// operand layout a warp's 32 walkers fill one contiguous 512-byte line.
+constexpr int kPrepWalkers = 32;
+constexpr int kPrepMaxWarps = 16;
+
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void st8(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void ld8h(const __half* p, float* v) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[2 * e] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] & 0xffffu)));
+    v[2 * e + 1] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] >> 16)));
+  }
+}
+__device__ __forceinline__ uint32_t pack2h(__half a, __half b) {
+  return static_cast<uint32_t>(__half_as_ushort(a)) |
+         (static_cast<uint32_t>(__half_as_ushort(b)) << 16);
+}
+__device__ __forceinline__ void st8h(__half* p, const __half* h) {
+  *reinterpret_cast<uint4*>(p) =
+      make_uint4(pack2h(h[0], h[1]), pack2h(h[2], h[3]), pack2h(h[4], h[5]), pack2h(h[6], h[7]));
+}
+
+__global__ void __launch_bounds__(kPrepMaxWarps * 32)
+prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
+                    int z, int z_ld, int n, int n_ld, int k_pad, int mE, float* pend, float* Xhi,
+                    float* Xlo, __half* Dh, __half* Dl, float* D32, const float* AE32,
+                    const float* corr, __half* Xh, __half* Xl, float* wscale, int inter,
+                    const float* sigma, int draw32) {
+  __shared__ float red[kPrepMaxWarps][kPrepWalkers];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int k = blockIdx.x * kPrepWalkers + lane;
+  const bool live = k < z;
+  const int chunks = (n + 7) >> 3;
   const size_t xr = static_cast<size_t>(k) * n_ld;
   auto opo = [&](int i) { return op_off(k, i, k_pad, z_ld, inter); };
+  const float t = (live && (flags & 1)) ? pend[k] : 0.0f;
+
+  // (1) pending move, and the walker's largest scaled coordinate.
   float mx = 0.0f;
-  const float t = (flags & 1) ? pend[k] : 0.0f;
-  if (t != 0.0f) {
-    for (int i = lane; i < n; i += 32) {
-      const float d = __half2float(Dh[opo(i)]) + __half2float(Dl[opo(i)]);
-      float hi = Xhi[xr + i], lo = Xlo[xr + i];
-      df_axpy(hi, lo, t, d);
-      if (corr != nullptr) {
-        float dlt = 0.0f;
-        for (int e = 0; e < mE; ++e)
-          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
-        lo = fmaf(-t, dlt, lo);
-      }
-      Xhi[xr + i] = hi;
-      Xlo[xr + i] = lo;
-      mx = fmaxf(mx, fabsf(hi));
-    }
-    if (lane == 0) pend[k] = 0.0f;
-  } else if (flags & 2) {
-    for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(Xhi[xr + i]));
-  }
-  if (flags & 2) {
+  if (live && (t != 0.0f || (flags & 2))) {
+    for (int c = warp; c < chunks; c += nwarps) {
+      const int i0 = 8 * c;
+      float hi[8], lo[8];
+      ld8(Xhi + xr + i0, hi);
+      if (t != 0.0f) {
+        float dh[8], dl[8];
+        ld8(Xlo + xr + i0, lo);
+        ld8h(Dh + opo(i0), dh);
+        ld8h(Dl + opo(i0), dl);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        for (int e = 0; e < 8; ++e) {
+          const int i = i0 + e;
+          if (i >= n) continue;
+          const float d = (dh[e] + dl[e]) * sigma[i];
+          df_axpy(hi[e], lo[e], t, d);
+          if (corr != nullptr) {
+            float dlt = 0.0f;
+            for (int q = 0; q < mE; ++q)
+              dlt = fmaf(AE32[static_cast<size_t>(q) * n_ld + i], corr[static_cast<size_t>(k) * mE + q], dlt);
+            lo[e] = fmaf(-t, dlt, lo[e]);
+          }
+        }
+        st8(Xhi + xr + i0, hi);
+        st8(Xlo + xr + i0, lo);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e < n) mx = fmaxf(mx, fabsf(hi[e]) / sigma[i0 + e]);
+    }
+  }
+  if (flags & 2) red[warp][lane] = mx;
+  __syncthreads();  // every warp has read pend[k] and its old direction chunks
+  if (live && t != 0.0f && warp == 0) pend[k] = 0.0f;
+
+  // (2) FP16 pair of the scaled point.
+  if ((flags & 2) && live) {
+    for (int w = 0; w < nwarps; ++w) mx = fmaxf(mx, red[w][lane]);
     int ex = 0;
     if (mx > 0.0f) frexpf(mx, &ex);
     const float inv = ldexpf(1.0f, -ex);
-    if (lane == 0) wscale[k] = ldexpf(1.0f, ex);
-    for (int i = lane; i < n; i += 32) {
-      const float v = (Xhi[xr + i] + Xlo[xr + i]) * inv;
-      const __half h = __float2half_rn(v);
-      Xh[opo(i)] = h;
-      Xl[opo(i)] = __float2half_rn(v - __half2float(h));
+    if (warp == 0) wscale[k] = ldexpf(1.0f, ex);
+    for (int c = warp; c < chunks; c += nwarps) {
+      const int i0 = 8 * c;
+      float hi[8], lo[8];
+      ld8(Xhi + xr + i0, hi);
+      ld8(Xlo + xr + i0, lo);
+      __half h8[8], l8[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = i0 + e;
+        const float v = i < n ? (hi[e] + lo[e]) * inv / sigma[i] : 0.0f;
+        h8[e] = __float2half_rn(v);
+        l8[e] = __float2half_rn(v - __half2float(h8[e]));
+      }
+      st8h(Xh + opo(i0), h8);
+      st8h(Xl + opo(i0), l8);
     }
   }
-  if (flags & 4) {
-    __syncwarp();  // every lane has read the old direction before it is overwritten
+
+  // (3) next directions: quads 2c and 2c + 1 of the chunk.
+  if ((flags & 4) && live) {
     const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
-    const int quads = (n + 3) >> 2;
-    for (int q = lane; q < quads; q += 32) {
-      const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k),
-                                static_cast<uint32_t>(q), kStreamDirection);
-      float v[4];
-      box_muller_f32(w.x, w.y, v[0], v[1]);
-      box_muller_f32(w.z, w.w, v[2], v[3]);
-      const int i0 = 4 * q;
+    for (int c = warp; c < chunks; c += nwarps) {
+      const int i0 = 8 * c;
+      float v[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (i0 + e >= n) break;
-        if (mE == 0) {
-          const __half h = __float2half_rn(v[e]);
-          Dh[opo(i0 + e)] = h;
-          Dl[opo(i0 + e)] = __float2half_rn(v[e] - __half2float(h));
+      for (int h = 0; h < 2; ++h) {
+        if (i0 + 4 * h < n) {
+          const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k),
+                                    static_cast<uint32_t>(2 * c + h), kStreamDirection);
+          box_muller_f32(w.x, w.y, v[4 * h], v[4 * h + 1]);
+          box_muller_f32(w.z, w.w, v[4 * h + 2], v[4 * h + 3]);
         } else {
-          D32[xr + i0 + e] = v[e];
+          v[4 * h] = v[4 * h + 1] = v[4 * h + 2] = v[4 * h + 3] = 0.0f;
         }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e >= n) v[e] = 0.0f;
+      if (!draw32) {
+        __half h8[8], l8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          h8[e] = __float2half_rn(v[e]);
+          l8[e] = __float2half_rn(v[e] - __half2float(h8[e]));
+        }
+        st8h(Dh + opo(i0), h8);
+        st8h(Dl + opo(i0), l8);
+      } else {
+        st8(D32 + xr + i0, v);
       }
     }
   }
@@ -547,18 +692,20 @@ __global__ void reproject_kernel(int z, int n, int n_ld, int mE, const double* A
   }
 }
 
-// Tensor-core operands: per-row power-of-two scale s_i with max_k |a_ik| / s_i
-// in [0.5, 1), then A/s split into FP16 hi + lo.  FP32 copy of b padded.
+// Tensor-core operands: columns multiplied by the coordinate scales sigma
+// (powers of two), then a per-row power-of-two scale s_r with
+// max_i |a_ri sigma_i| / s_r in [0.5, 1), then the row split into FP16 hi + lo.
+// FP32 copy of b / s_r, padded.
 __global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, const double* A,
                                   const double* b, __half* Ah, __half* Al, float* row_scale,
-                                  float* bS) {
+                                  float* bS, const float* sigma) {
   const int r = blockIdx.x;
   if (r >= m_pad) return;
   __shared__ double red[kThreads];
   double mx = 0.0;
   if (r < m)
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-      mx = fmax(mx, fabs(A[static_cast<size_t>(r) * n_ld + i]));
+      mx = fmax(mx, fabs(A[static_cast<size_t>(r) * n_ld + i] * static_cast<double>(sigma[i])));
   red[threadIdx.x] = mx;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -575,7 +722,9 @@ __global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, 
   }
   for (int i = threadIdx.x; i < k_pad; i += blockDim.x) {
     float v = 0.0f;
-    if (r < m && i < n) v = static_cast<float>(A[static_cast<size_t>(r) * n_ld + i] / scale);
+    if (r < m && i < n)
+      v = static_cast<float>(A[static_cast<size_t>(r) * n_ld + i] * static_cast<double>(sigma[i]) /
+                             scale);
     const __half h = __float2half_rn(v);
     Ah[static_cast<size_t>(r) * k_pad + i] = h;
     Al[static_cast<size_t>(r) * k_pad + i] = __float2half_rn(v - __half2float(h));
@@ -600,7 +749,8 @@ cudaError_t launch_directions(mhar_ctx* c, int j) {
   const int mode = c->opts.precision == MHAR_FP64 ? 0 : (c->opts.precision == MHAR_FP32 ? 1 : 2);
   const long long threads = static_cast<long long>(c->z) * ((c->n + 3) / 4);
   directions_kernel<<<blocks_for(threads, kThreads), kThreads, 0, c->stream>>>(
-      mode, c->mE == 0 ? 1 : 0, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld,
+      mode, (c->mE == 0 && c->pc_rank < 0) ? 1 : 0, c->opts.seed, c->d.step, j, c->opts.walker0,
+      c->z, c->n, c->n_ld,
       c->k_pad, c->d.D64, c->d.D32, c->d.Dh, c->d.Dl);
   return cudaGetLastError();
 }
@@ -610,13 +760,29 @@ cudaError_t launch_projection(mhar_ctx* c) {
   if (c->opts.precision == MHAR_FP64) {
     projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr, 0, 0);
+        nullptr, nullptr, 0, 0, nullptr);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
-        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0);
+        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0, c->d.sigma);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precondition(mhar_ctx* c, int j, int split) {
+  dim3 grid(blocks_for(c->n, kPcThreads), blocks_for(c->z, kPcWalkers));
+  const int z_ld = (c->z + 127) / 128 * 128;
+  if (c->opts.precision == MHAR_FP64) {
+    precondition_kernel<double><<<grid, kPcThreads, 0, c->stream>>>(
+        c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
+        c->d.pc_delta64, c->d.pc_U64, c->d.D64, 0, c->k_pad, z_ld, 0, nullptr, nullptr, nullptr);
+  } else {
+    precondition_kernel<float><<<grid, kPcThreads, 0, c->stream>>>(
+        c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
+        c->d.pc_delta32, c->d.pc_U32, c->d.D32, split, c->k_pad, z_ld, c->use_ts ? 1 : 0,
+        c->d.sigma, c->d.Dh, c->d.Dl);
   }
   return cudaGetLastError();
 }
@@ -646,10 +812,13 @@ cudaError_t launch_update_simt(mhar_ctx* c, int j) {
 
 cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
   const int z_ld = (c->z + 127) / 128 * 128;
-  prep_walkers_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
+  const int chunks = (c->n + 7) / 8;
+  const int warps = chunks < kPrepMaxWarps ? chunks : kPrepMaxWarps;
+  prep_walkers_kernel<<<blocks_for(c->z, kPrepWalkers), warps * 32, 0, c->stream>>>(
       flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
       c->mE, c->d.pend, c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.D32, c->d.AE32, c->d.corr,
-      c->d.Xh, c->d.Xl, c->d.wscale, c->use_ts ? 1 : 0);
+      c->d.Xh, c->d.Xl, c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma,
+      (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -658,11 +827,11 @@ cudaError_t launch_advance(mhar_ctx* c, int steps) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(mhar_ctx* c, double* out_device) {
+cudaError_t launch_emit(mhar_ctx* c, double* out_device, int walkers) {
   const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
-  const long long count = static_cast<long long>(c->z) * c->n;
+  const long long count = static_cast<long long>(walkers) * c->n;
   emit_kernel<<<blocks_for(count, kThreads), kThreads, 0, c->stream>>>(
-      mode, c->z, c->n, c->n_ld, c->d.X64, c->d.Xhi, c->d.Xlo, out_device);
+      mode, walkers, c->n, c->n_ld, c->d.X64, c->d.Xhi, c->d.Xlo, out_device);
   return cudaGetLastError();
 }
 
@@ -706,7 +875,7 @@ cudaError_t launch_reproject(mhar_ctx* c) {
 cudaError_t launch_prepare_tc_operands(mhar_ctx* c) {
   prepare_tc_kernel<<<c->m_pad, kThreads, 0, c->stream>>>(c->m, c->n, c->n_ld, c->m_pad, c->k_pad,
                                                          c->d.A64, c->d.b64, c->d.Ah, c->d.Al,
-                                                         c->d.row_scale, c->d.bS);
+                                                         c->d.row_scale, c->d.bS, c->d.sigma);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ struct TcParams {
   float* Xlo;
   const __half* Dh;         // z_ld x k_pad
   const __half* Dl;
+  const float* sigma;       // n_ld: coordinate scales (operands hold x / sigma, d / sigma)
   const float* AE32;        // mE x n_ld (equality rows) or null
   const float* corr;        // z x mE residual corrections or null
   double* lmin;
@@ -380,7 +381,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
       if (kk >= p.z || tw == 0.0f) continue;
       const size_t xr = static_cast<size_t>(kk) * p.n_ld + i;
       const size_t dr = static_cast<size_t>(kk) * k_pad + i;
-      const float d = __half2float(p.Dh[dr]) + __half2float(p.Dl[dr]);
+      const float d = (__half2float(p.Dh[dr]) + __half2float(p.Dl[dr])) * p.sigma[i];
       df_axpy(p.Xhi[xr], p.Xlo[xr], tw, d);
       if (p.corr != nullptr) {
         // Exact null-space correction of the rounded direction (see projection).
@@ -408,13 +409,15 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
 // Refresh operands: each walker's point x = hi + lo scaled by a power of two
 // 2^e (max |x_i| 2^-e in [0.5, 1)) and split into FP16 hi + lo.
 __global__ void split_points_kernel(int z, int z_ld, int n, int n_ld, int k_pad, const float* Xhi,
-                                    const float* Xlo, __half* Xh, __half* Xl, float* wscale) {
+                                    const float* Xlo, __half* Xh, __half* Xl, float* wscale,
+                                    const float* sigma) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + warp;
   if (k >= z_ld) return;
   float mx = 0.0f;
   if (k < z)
-    for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(Xhi[static_cast<size_t>(k) * n_ld + i]));
+    for (int i = lane; i < n; i += 32)
+      mx = fmaxf(mx, fabsf(Xhi[static_cast<size_t>(k) * n_ld + i]) / sigma[i]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   int ex = 0;
@@ -424,7 +427,8 @@ __global__ void split_points_kernel(int z, int z_ld, int n, int n_ld, int k_pad,
   for (int i = lane; i < k_pad; i += 32) {
     float v = 0.0f;
     if (k < z && i < n)
-      v = (Xhi[static_cast<size_t>(k) * n_ld + i] + Xlo[static_cast<size_t>(k) * n_ld + i]) * inv;
+      v = (Xhi[static_cast<size_t>(k) * n_ld + i] + Xlo[static_cast<size_t>(k) * n_ld + i]) * inv /
+          sigma[i];
     const __half h = __float2half_rn(v);
     Xh[static_cast<size_t>(k) * k_pad + i] = h;
     Xl[static_cast<size_t>(k) * k_pad + i] = __float2half_rn(v - __half2float(h));
@@ -442,6 +446,7 @@ TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j) {
   p.Xlo = c->d.Xlo;
   p.Dh = c->d.Dh;
   p.Dl = c->d.Dl;
+  p.sigma = c->d.sigma;
   p.AE32 = c->d.AE32;
   p.corr = c->d.corr;
   p.lmin = c->d.lmin;
@@ -535,7 +540,7 @@ cudaError_t launch_split_points(mhar_ctx* c) {
   const int z_ld = (c->z + kWalkers - 1) / kWalkers * kWalkers;
   split_points_kernel<<<(z_ld + 7) / 8, 256, 0, c->stream>>>(c->z, z_ld, c->n, c->n_ld, c->k_pad,
                                                           c->d.Xhi, c->d.Xlo, c->d.Xh, c->d.Xl,
-                                                          c->d.wscale);
+                                                          c->d.wscale, c->d.sigma);
   return cudaGetLastError();
 }
 

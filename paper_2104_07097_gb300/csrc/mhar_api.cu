@@ -83,7 +83,7 @@ void free_all(mhar_ctx* c) {
   void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.AE64, d.AE32, d.bE64, d.Lchol, d.Ah, d.Al,
                   d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale, d.pend,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
-                  d.emit, d.check};
+                  d.emit, d.check, d.pc_delta64, d.pc_U64, d.pc_delta32, d.pc_U32, d.sigma};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = mhar::DeviceBuffers();
@@ -138,13 +138,21 @@ __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const 
 }
 
 int kernels_per_iteration(const mhar_ctx* c) {
-  return 1 + (c->mE > 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
+  return 1 + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
+}
+
+int emit_count(const mhar_ctx* c) {
+  return c->opts.emit_walkers > 0 ? c->opts.emit_walkers : c->z;
 }
 
 // Direction draw of one iteration (Section 4.3); in recompute mode the same
 // launch first applies the previous iteration's moves and re-splits X.
 cudaError_t enqueue_directions(mhar_ctx* c, int j) {
   cudaError_t e = recompute(c) ? mhar::launch_prep_walkers(c, j, 7) : mhar::launch_directions(c, j);
+  // Preconditioned draw d = delta .* h + U g; the tensor-core modes split it
+  // into the FP16 pair here unless the projection still has to run.
+  if (e == cudaSuccess && c->pc_rank >= 0)
+    e = mhar::launch_precondition(c, j, (mixed(c) && c->mE == 0) ? 1 : 0);
   if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
   return e;
 }
@@ -239,18 +247,66 @@ int refresh(mhar_ctx* c) {
   return MHAR_OK;
 }
 
-int emit_to(mhar_ctx* c, double* out, bool out_device) {
+int emit_to(mhar_ctx* c, double* out, bool out_device, int walkers) {
   int rc = flush_pending(c);
   if (rc) return rc;
   ++c->launches;
   if (out_device) {
-    MHAR_CUDA(mhar::launch_emit(c, out), "emit kernel");
+    MHAR_CUDA(mhar::launch_emit(c, out, walkers), "emit kernel");
   } else {
-    MHAR_CUDA(mhar::launch_emit(c, c->d.emit), "emit kernel");
-    MHAR_CUDA(cudaMemcpyAsync(out, c->d.emit, sizeof(double) * c->z * c->n, cudaMemcpyDeviceToHost,
-                              c->stream),
+    MHAR_CUDA(mhar::launch_emit(c, c->d.emit, walkers), "emit kernel");
+    MHAR_CUDA(cudaMemcpyAsync(out, c->d.emit, sizeof(double) * walkers * c->n,
+                              cudaMemcpyDeviceToHost, c->stream),
               "sample copy");
   }
+  return MHAR_OK;
+}
+
+void drop_graphs(mhar_ctx* c) {
+  if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
+  if (c->g_one) cudaGraphExecDestroy(c->g_one);
+  c->g_chunk = nullptr;
+  c->g_one = nullptr;
+  c->graph_len = 0;
+}
+
+// Makes (delta, U, sigma) current: padded copies are on the device already;
+// re-splits A with the new coordinate scales and, in the stored-slack mode,
+// recomputes the slack from the points.
+int adopt_preconditioner(mhar_ctx* c, int rank) {
+  c->pc_rank = rank;
+  drop_graphs(c);
+  if (mixed(c)) {
+    MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
+    ++c->launches;
+    if (stored(c)) {
+      int rc = refresh(c);
+      if (rc) return rc;
+    }
+  }
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "preconditioner sync");
+  return MHAR_OK;
+}
+
+int alloc_preconditioner(mhar_ctx* c) {
+  mhar::DeviceBuffers& d = c->d;
+  const size_t nl = static_cast<size_t>(c->n_ld);
+  int rc;
+  if (!d.pc_delta64 &&
+      ((rc = dmalloc(c, &d.pc_delta64, nl)) || (rc = dmalloc(c, &d.pc_U64, nl * mhar::kMaxPcRank)) ||
+       (rc = dmalloc(c, &d.pc_delta32, nl)) || (rc = dmalloc(c, &d.pc_U32, nl * mhar::kMaxPcRank))))
+    return rc;
+  if (mixed(c) && !d.D32 && (rc = dmalloc(c, &d.D32, static_cast<size_t>(c->z) * c->n_ld)))
+    return rc;
+  return MHAR_OK;
+}
+
+int set_unit_sigma(mhar_ctx* c) {
+  if (!c->d.sigma) return MHAR_OK;
+  std::vector<float> ones(c->n_ld, 1.0f);
+  MHAR_CUDA(cudaMemcpyAsync(c->d.sigma, ones.data(), sizeof(float) * ones.size(),
+                            cudaMemcpyHostToDevice, c->stream), "copy sigma");
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "sigma sync");
   return MHAR_OK;
 }
 
@@ -427,6 +483,7 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       return rc;
     if (stored(c) && (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld))) return rc;
     if (recompute(c) && (rc = dmalloc(c, &d.pend, z_ld))) return rc;
+    if ((rc = dmalloc(c, &d.sigma, c->n_ld)) || (rc = set_unit_sigma(c))) return rc;
   }
 
   // Projector factor on the device.
@@ -488,9 +545,10 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
             mE, n);
     rc = MHAR_E_UNSUPPORTED;
   } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
-             c->opts.refresh_k < 0 || c->opts.graph_chunk < 0) {
-    set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d)", c->opts.precision,
-            c->opts.refresh_k, c->opts.graph_chunk);
+             c->opts.refresh_k < 0 || c->opts.graph_chunk < 0 || c->opts.emit_walkers < 0 ||
+             c->opts.emit_walkers > z) {
+    set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d emit_walkers=%d)",
+            c->opts.precision, c->opts.refresh_k, c->opts.graph_chunk, c->opts.emit_walkers);
     rc = MHAR_E_ARG;
   } else if (!all_finite(A, static_cast<size_t>(m) * n) || !all_finite(b, m) ||
              !all_finite(x0, n) || (mE > 0 && (!all_finite(AE, static_cast<size_t>(mE) * n) ||
@@ -541,8 +599,8 @@ int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
       if (c->since_refresh >= k && (rc = refresh(c))) return rc;
     }
     if (thin > 0 && done % thin == 0 && emitted < nsamp) {
-      if ((rc = emit_to(c, out + static_cast<size_t>(emitted) * c->z * c->n,
-                        c->opts.out_on_device != 0)))
+      if ((rc = emit_to(c, out + static_cast<size_t>(emitted) * emit_count(c) * c->n,
+                        c->opts.out_on_device != 0, emit_count(c))))
         return rc;
       ++emitted;
     }
@@ -577,7 +635,7 @@ int mhar_get_state(const mhar_ctx* cc, double* X, uint64_t* step) {
   mhar_ctx* c = const_cast<mhar_ctx*>(cc);
   if (!c) return MHAR_E_ARG;
   if (X) {
-    int rc = emit_to(c, X, false);
+    int rc = emit_to(c, X, false, c->z);
     if (rc) return rc;
   }
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "state sync");
@@ -618,6 +676,136 @@ int mhar_get_chord(const mhar_ctx* cc, double* lmin, double* lmax, double* theta
   if (theta) MHAR_CUDA(cudaMemcpyAsync(theta, c->d.theta, bytes, cudaMemcpyDeviceToHost, c->stream), "copy");
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "chord sync");
   return MHAR_OK;
+}
+
+int mhar_set_preconditioner(mhar_ctx* c, const double* delta, const double* U, int32_t rank) {
+  if (!c) return MHAR_E_ARG;
+  int rc = flush_pending(c);
+  if (rc) return rc;
+  if (!delta) {
+    if (c->pc_rank < 0) return MHAR_OK;
+    if ((rc = set_unit_sigma(c))) return rc;
+    return adopt_preconditioner(c, -1);
+  }
+  if (rank < 0 || rank > mhar::kMaxPcRank || (rank > 0 && !U)) {
+    set_err(c, "preconditioner rank must be 0..%d with U given when rank > 0 (got %d)",
+            mhar::kMaxPcRank, rank);
+    return MHAR_E_ARG;
+  }
+  const int n = c->n, nl = c->n_ld, R = mhar::kMaxPcRank;
+  if (!all_finite(delta, n) || (rank > 0 && !all_finite(U, static_cast<size_t>(n) * rank))) {
+    set_err(c, "non-finite preconditioner entry");
+    return MHAR_E_NONFINITE;
+  }
+  for (int i = 0; i < n; ++i)
+    if (delta[i] < 0.0) {
+      set_err(c, "delta[%d] < 0", i);
+      return MHAR_E_ARG;
+    }
+  if ((rc = alloc_preconditioner(c))) return rc;
+  std::vector<double> d64(nl, 0.0), u64(static_cast<size_t>(nl) * R, 0.0);
+  std::vector<float> sig(nl, 1.0f);
+  for (int i = 0; i < n; ++i) {
+    d64[i] = delta[i];
+    double var = delta[i] * delta[i];
+    for (int q = 0; q < rank; ++q) {
+      const double u = U[static_cast<size_t>(i) * rank + q];
+      u64[static_cast<size_t>(i) * R + q] = u;
+      var += u * u;
+    }
+    // Coordinate scale 2^e with sqrt(var) = f 2^e, f in [0.5, 1).
+    if (var > 0.0 && std::isfinite(var)) {
+      int e = 0;
+      std::frexp(std::sqrt(var), &e);
+      sig[i] = static_cast<float>(std::ldexp(1.0, e));
+    }
+  }
+  std::vector<float> d32(d64.begin(), d64.end()), u32(u64.begin(), u64.end());
+  mhar::DeviceBuffers& d = c->d;
+  MHAR_CUDA(cudaMemcpy(d.pc_delta64, d64.data(), sizeof(double) * nl, cudaMemcpyHostToDevice), "copy delta");
+  MHAR_CUDA(cudaMemcpy(d.pc_U64, u64.data(), sizeof(double) * u64.size(), cudaMemcpyHostToDevice), "copy U");
+  MHAR_CUDA(cudaMemcpy(d.pc_delta32, d32.data(), sizeof(float) * nl, cudaMemcpyHostToDevice), "copy delta");
+  MHAR_CUDA(cudaMemcpy(d.pc_U32, u32.data(), sizeof(float) * u32.size(), cudaMemcpyHostToDevice), "copy U");
+  if (d.sigma)
+    MHAR_CUDA(cudaMemcpy(d.sigma, sig.data(), sizeof(float) * nl, cudaMemcpyHostToDevice), "copy sigma");
+  return adopt_preconditioner(c, rank);
+}
+
+int mhar_get_preconditioner(const mhar_ctx* cc, double* delta, double* U, int32_t* rank) {
+  mhar_ctx* c = const_cast<mhar_ctx*>(cc);
+  if (!c) return MHAR_E_ARG;
+  if (rank) *rank = c->pc_rank;
+  if (c->pc_rank < 0) return MHAR_OK;
+  const int n = c->n, R = mhar::kMaxPcRank, r = c->pc_rank;
+  MHAR_CUDA(cudaStreamSynchronize(c->stream), "preconditioner sync");
+  if (delta) MHAR_CUDA(cudaMemcpy(delta, c->d.pc_delta64, sizeof(double) * n, cudaMemcpyDeviceToHost), "copy delta");
+  if (U && r > 0) {
+    std::vector<double> u64(static_cast<size_t>(n) * R);
+    MHAR_CUDA(cudaMemcpy(u64.data(), c->d.pc_U64, sizeof(double) * u64.size(), cudaMemcpyDeviceToHost), "copy U");
+    for (int i = 0; i < n; ++i)
+      for (int q = 0; q < r; ++q) U[static_cast<size_t>(i) * r + q] = u64[static_cast<size_t>(i) * R + q];
+  }
+  return MHAR_OK;
+}
+
+int mhar_fit_preconditioner(mhar_ctx* c, int64_t warmup, int32_t snapshots, int32_t rank,
+                            int32_t power_iters) {
+  if (!c) return MHAR_E_ARG;
+  if (warmup < 1 || snapshots < 1 || snapshots > warmup ||
+      static_cast<int64_t>(c->z) * snapshots < 2 || rank < 0 ||
+      rank > std::min(mhar::kMaxPcRank, c->n) || power_iters < 0 || power_iters > 64) {
+    set_err(c, "bad fit arguments (warmup=%lld snapshots=%d rank=%d power_iters=%d, z=%d n=%d)",
+            static_cast<long long>(warmup), snapshots, rank, power_iters, c->z, c->n);
+    return MHAR_E_ARG;
+  }
+  const int n = c->n;
+  mhar::FitScratch f;
+  int rc = MHAR_OK;
+  auto release = [&]() {
+    cudaStreamSynchronize(c->stream);
+    void* ptrs[] = {f.shift, f.s1, f.s2, f.sigma, f.Y, f.Q, f.flag};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  };
+  const size_t nn = static_cast<size_t>(n) * n;
+  if ((rc = dmalloc(c, &f.shift, n)) || (rc = dmalloc(c, &f.s1, n)) || (rc = dmalloc(c, &f.s2, nn)) ||
+      (rc = dmalloc(c, &f.sigma, nn)) || (rc = dmalloc(c, &f.Y, static_cast<size_t>(n) * mhar::kMaxPcRank)) ||
+      (rc = dmalloc(c, &f.Q, static_cast<size_t>(n) * mhar::kMaxPcRank)) || (rc = dmalloc(c, &f.flag, 1)) ||
+      (rc = alloc_preconditioner(c))) {
+    release();
+    return rc;
+  }
+  const int64_t gap = std::max<int64_t>(1, warmup / (2 * static_cast<int64_t>(snapshots)));
+  const int64_t first = warmup - (snapshots - 1) * gap;
+  for (int s = 0; s < snapshots && rc == MHAR_OK; ++s) {
+    rc = mhar_run(c, s == 0 ? first : gap, 0, nullptr);
+    if (rc == MHAR_OK) rc = flush_pending(c);
+    if (rc != MHAR_OK) break;
+    cudaError_t e = cudaSuccess;
+    if (s == 0) e = mhar::launch_fit_shift(c, &f);
+    if (e == cudaSuccess) e = mhar::launch_fit_accumulate(c, &f);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "covariance kernel");
+    c->launches += s == 0 ? 2 : 1;
+  }
+  if (rc == MHAR_OK) {
+    cudaError_t e = mhar::launch_fit_factor(c, &f, static_cast<long long>(c->z) * snapshots, rank,
+                                            power_iters);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "preconditioner fit kernels");
+    c->launches += rank > 0 ? 5 + 2 * power_iters : 2;
+  }
+  int flag = 0;
+  if (rc == MHAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(&flag, f.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "fit sync");
+  }
+  release();
+  if (rc != MHAR_OK) return rc;
+  if (flag) {
+    set_err(c, "the warm-up covariance is not finite");
+    return MHAR_E_NONFINITE;
+  }
+  return adopt_preconditioner(c, rank);
 }
 
 int mhar_get_stats(const mhar_ctx* c, mhar_stats* s) {

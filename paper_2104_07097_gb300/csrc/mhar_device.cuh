@@ -5,7 +5,9 @@
 // independently from its published definition.  Counter layout of one block:
 //   ctr = (q, walker, step_lo32, (step_hi24 << 8) | stream),  key = (seed_lo, seed_hi)
 // stream 0 draws direction entries (quad q covers coordinates 4q..4q+3),
-// stream 1 draws the chord uniform (q = 0, word 0).
+// stream 1 draws the chord uniform (q = 0, word 0), stream 2 the r low-rank
+// normals g of a preconditioned direction, stream 3 the starting block of the
+// preconditioner fit (column c drawn as walker c at step 0).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -14,6 +16,9 @@ namespace mhar {
 
 constexpr uint32_t kStreamDirection = 0u;
 constexpr uint32_t kStreamChord = 1u;
+constexpr uint32_t kStreamLowRank = 2u;
+constexpr uint32_t kStreamFit = 3u;
+constexpr int kMaxPcRank = 32;  // columns of the low-rank factor U
 
 struct U4 { uint32_t x, y, z, w; };
 

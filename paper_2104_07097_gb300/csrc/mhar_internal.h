@@ -58,6 +58,18 @@ struct DeviceBuffers {
   uint64_t* step = nullptr;  // device iteration counter (graph replays read it)
   double* emit = nullptr;  // z x n staging for host output
   double* check = nullptr; // [0] max violation, [1] eq residual, [2] drift
+
+  // Direction preconditioner d = P (delta .* h + U g) (allocated when set).
+  double* pc_delta64 = nullptr;  // n_ld
+  double* pc_U64 = nullptr;      // n_ld x 32, row i = U[i, :], zero beyond the rank
+  float* pc_delta32 = nullptr;   // n_ld
+  float* pc_U32 = nullptr;       // n_ld x 32
+  // Tensor-core modes: power-of-two scale of each coordinate.  The FP16
+  // operands hold x_i / sigma_i and d_i / sigma_i, and A's columns are
+  // multiplied by sigma_i, so A x and A d are unchanged while coordinates of
+  // very different size keep their relative precision.  All ones unless a
+  // preconditioner chose them.
+  float* sigma = nullptr;        // n_ld
 };
 
 }  // namespace mhar
@@ -82,6 +94,7 @@ struct mhar_ctx {
   int64_t launches_chunk = 0;  // kernel nodes in g_chunk
   int64_t launches_one = 0;    // kernel nodes in g_one
   bool use_ts = false;         // recompute mode: TMEM-operand kernel (n <= 128)
+  int pc_rank = -1;            // -1: isotropic directions; else rank of U (0..32)
   double last_drift = 0.0;
   double max_violation = 0.0;
   double eq_residual = 0.0;
@@ -101,12 +114,30 @@ cudaError_t launch_update_simt(mhar_ctx* ctx, int j);
 cudaError_t launch_advance(mhar_ctx* ctx, int steps);
 // Recompute mode: flags bit 0 apply pending moves, bit 1 split X, bit 2 draw D.
 cudaError_t launch_prep_walkers(mhar_ctx* ctx, int j, int flags);
-cudaError_t launch_emit(mhar_ctx* ctx, double* out_device);
+cudaError_t launch_emit(mhar_ctx* ctx, double* out_device, int walkers);  // walkers 0..walkers-1
 cudaError_t launch_check(mhar_ctx* ctx);
 cudaError_t launch_set_points(mhar_ctx* ctx, const double* X_dev);
 cudaError_t launch_prepare_tc_operands(mhar_ctx* ctx);
 cudaError_t launch_refresh_simt(mhar_ctx* ctx);
 cudaError_t launch_reproject(mhar_ctx* ctx);
+// d <- delta .* d + U g on the drawn normals (FP64 / FP32 scratch), writing the
+// FP16 pair (divided by sigma) when `split`.
+cudaError_t launch_precondition(mhar_ctx* ctx, int j, int split);
+
+// ---- preconditioner fit (kernels_fit.cu) --------------------------------------
+struct FitScratch {
+  double* shift = nullptr;   // n: centre subtracted before the products
+  double* s1 = nullptr;      // n: sum of (x - shift)
+  double* s2 = nullptr;      // n x n: sum of (x - shift)(x - shift)^T (upper tiles)
+  double* sigma = nullptr;   // n x n covariance
+  double* Y = nullptr;       // n x 32
+  double* Q = nullptr;       // n x 32
+  int* flag = nullptr;       // [0] set when a fit kernel met a non-finite value
+};
+cudaError_t launch_fit_shift(mhar_ctx* ctx, FitScratch* f);   // shift = walker 0's point
+cudaError_t launch_fit_accumulate(mhar_ctx* ctx, FitScratch* f);
+cudaError_t launch_fit_factor(mhar_ctx* ctx, FitScratch* f, long long samples, int rank,
+                              int power_iters);
 
 // ---- allocation-free chord entry point (noalloc.cu) ---------------------------
 const char* noalloc_last_error();

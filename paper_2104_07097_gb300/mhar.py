@@ -37,7 +37,8 @@ ST_NONFINITE = 4
 # Every symbol include/mhar.h declares.
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
            "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
-           "mhar_chord_noalloc", "mhar_last_error", "mhar_strerror", "mhar_destroy")
+           "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
+           "mhar_fit_preconditioner", "mhar_last_error", "mhar_strerror", "mhar_destroy")
 
 
 class MharOpts(ctypes.Structure):
@@ -45,7 +46,8 @@ class MharOpts(ctypes.Structure):
                 ("refresh_k", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
                 ("walker0", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("graph_chunk", ctypes.c_int32), ("refresh_fp64", ctypes.c_int32),
-                ("smem_operands", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("smem_operands", ctypes.c_int32), ("emit_walkers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class MharStats(ctypes.Structure):
@@ -102,6 +104,13 @@ def load(path: str | None = None):
     lib.mhar_chord_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                        vp, vp, vp]
     lib.mhar_chord_noalloc.restype = ctypes.c_int
+    lib.mhar_set_preconditioner.argtypes = [vp, dp, dp, ctypes.c_int32]
+    lib.mhar_set_preconditioner.restype = ctypes.c_int
+    lib.mhar_get_preconditioner.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int32)]
+    lib.mhar_get_preconditioner.restype = ctypes.c_int
+    lib.mhar_fit_preconditioner.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32]
+    lib.mhar_fit_preconditioner.restype = ctypes.c_int
     lib.mhar_last_error.argtypes = [vp]
     lib.mhar_last_error.restype = ctypes.c_char_p
     lib.mhar_strerror.argtypes = [ctypes.c_int]
@@ -205,6 +214,47 @@ def mhar_time_kernels(ctx, iters: int):
     return ms
 
 
+def mhar_set_preconditioner(ctx, n: int, delta, U=None) -> None:
+    """delta None removes the preconditioner; U is n x r (r <= 32) or None."""
+    if delta is None:
+        rc = load().mhar_set_preconditioner(ctx, None, None, 0)
+    else:
+        delta = _f64(delta).reshape(n)
+        r = 0
+        if U is not None and np.size(U) > 0:
+            U = _f64(U).reshape(n, -1)
+            r = U.shape[1]
+        else:
+            U = None
+        rc = load().mhar_set_preconditioner(ctx, _dp(delta), _dp(U), r)
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+
+
+def mhar_get_preconditioner(ctx, n: int):
+    """(delta, U) or None when directions are isotropic."""
+    r = ctypes.c_int32()
+    rc = load().mhar_get_preconditioner(ctx, None, None, ctypes.byref(r))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    if r.value < 0:
+        return None
+    delta = np.zeros(n)
+    U = np.zeros((n, r.value))
+    rc = load().mhar_get_preconditioner(ctx, _dp(delta), _dp(U) if r.value > 0 else None,
+                                        ctypes.byref(r))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return delta, U
+
+
+def mhar_fit_preconditioner(ctx, warmup: int, snapshots: int, rank: int, power_iters: int) -> None:
+    rc = load().mhar_fit_preconditioner(ctx, int(warmup), int(snapshots), int(rank),
+                                        int(power_iters))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+
+
 def mhar_chord_noalloc(A_ptr, b_ptr, m: int, n: int, X_ptr, D_ptr, z: int, lmin_ptr, lmax_ptr,
                        stream=None) -> int:
     """Allocation-free chord of every walker; all array arguments are device
@@ -226,7 +276,7 @@ class Sampler:
     def __init__(self, A, b, x0, z: int, AE=None, bE=None, precision: str | int = "fp64",
                  seed: int = 0, refresh_k: int = 64, walker0: int = 0, stream=None,
                  graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False,
-                 smem_operands: bool = False):
+                 smem_operands: bool = False, emit_walkers: int = 0):
         o = mhar_default_opts()
         o.seed = int(seed)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -236,17 +286,20 @@ class Sampler:
         o.out_on_device = 1 if out_on_device else 0
         o.refresh_fp64 = 1 if refresh_fp64 else 0
         o.smem_operands = 1 if smem_operands else 0
+        o.emit_walkers = int(emit_walkers)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         A = _f64(A)
         self.m, self.n = A.shape
         self.z = int(z) if z > 0 else max(self.m, self.n) + 1
         self.out_on_device = out_on_device
+        self.emit_walkers = int(emit_walkers) if emit_walkers > 0 else self.z
         self._ctx = mhar_create(A, b, AE, bE, x0, self.z, o)
 
     def run(self, steps: int, thin: int = 0, out=None):
         """Advances `steps` iterations; with thin > 0 returns (or fills) the
-        floor(steps/thin) x z x n samples.  `out` may be a numpy array (host)
+        floor(steps/thin) x W x n samples (W = emit_walkers, default z).
+        `out` may be a numpy array (host)
         or, for out_on_device samplers, a CUDA tensor / raw device pointer."""
         nsamp = steps // thin if thin > 0 else 0
         ptr = None
@@ -254,9 +307,10 @@ class Sampler:
             if out is None:
                 if self.out_on_device:
                     raise ValueError("out_on_device sampler needs a device `out`")
-                out = np.zeros((nsamp, self.z, self.n))
+                out = np.zeros((nsamp, self.emit_walkers, self.n))
             if isinstance(out, np.ndarray):
-                if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < nsamp * self.z * self.n:
+                if (out.dtype != np.float64 or not out.flags.c_contiguous
+                        or out.size < nsamp * self.emit_walkers * self.n):
                     raise ValueError("out must be a C-contiguous float64 array of the sample shape")
                 ptr = ctypes.c_void_p(out.ctypes.data)
             elif hasattr(out, "data_ptr"):
@@ -282,6 +336,18 @@ class Sampler:
 
     def stats(self) -> MharStats:
         return mhar_get_stats(self._ctx)
+
+    def set_preconditioner(self, delta, U=None) -> None:
+        """Directions d = P (delta * h + U g); delta None restores isotropic ones."""
+        mhar_set_preconditioner(self._ctx, self.n, delta, U)
+
+    def preconditioner(self):
+        return mhar_get_preconditioner(self._ctx, self.n)
+
+    def fit_preconditioner(self, warmup: int, snapshots: int = 10, rank: int = 32,
+                           power_iters: int = 4) -> None:
+        """Learns (delta, U) from `warmup` iterations of the chain and freezes it."""
+        mhar_fit_preconditioner(self._ctx, warmup, snapshots, min(rank, self.n), power_iters)
 
     def time_kernels(self, iters: int):
         """Average device ms of (directions, chord+update, refresh)."""
