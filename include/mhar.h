@@ -60,8 +60,10 @@ extern "C" {
  * MHAR_MIXED_RECOMPUTE: the paper's own formulation (Lemma 4.2) on the tensor
  *   cores: every iteration one fused kernel forms A X and A D from FP16 pairs
  *   (three products each, FP32 accumulation), the slack b - A X, the ratios
- *   and the chord.  No slack is stored, so there is nothing to refresh and no
- *   drift; refresh_k is ignored. */
+ *   and the chord, moves the walkers, and prepares the next iteration's
+ *   operands (and, without equalities or preconditioner, its directions).
+ *   No slack is stored, so there is nothing to refresh and no drift;
+ *   refresh_k is ignored. */
 #define MHAR_FP64             0
 #define MHAR_FP32             1
 #define MHAR_MIXED_F16X3      2
@@ -170,9 +172,12 @@ int mhar_get_stats(const mhar_ctx* ctx, mhar_stats* stats);
  * with CUDA events; times the direction kernels alone the same way (they are
  * idempotent for a fixed iteration counter); then times one slack refresh
  * (mixed mode).  Writes average device milliseconds:
- *   ms[0] direction draw (+ projection when mE > 0)   (Section 4.3)
- *   ms[1] the rest of one iteration: the fused tensor-core kernel in mixed
- *         mode, the chord and update kernels otherwise   (Sections 4.4-4.5)
+ *   ms[0] direction draw (+ projection when mE > 0)   (Section 4.3); 0 in
+ *         MHAR_MIXED_RECOMPUTE mode without equalities or preconditioner,
+ *         where the chord kernel draws the next directions itself
+ *   ms[1] the rest of one iteration: the fused tensor-core kernel in the
+ *         tensor-core modes, the chord and update kernels otherwise
+ *         (Sections 4.4-4.5)
  *   ms[2] one slack refresh (mixed mode; 0 otherwise)
  * The timed iterations are real: the chain and its counters advance. */
 int mhar_time_kernels(mhar_ctx* ctx, int iters, double* ms);

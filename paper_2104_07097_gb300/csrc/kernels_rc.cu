@@ -11,8 +11,8 @@
 //   s_i = b_i - p_i           (in units of the row's power-of-two scale)
 //   lambda_max = min{ s_i / g_i : g_i > 0 },  lambda_min = max{ s_i / g_i : g_i < 0 }
 //   theta = lambda_min + u (lambda_max - lambda_min)
-// The move X += D diag(theta) is applied by the next iteration's walker
-// preparation kernel (which also re-splits X), or by a flush before X is read.
+// The move X += D diag(theta) is made at the end of the same kernel, which
+// also re-splits X and draws the next directions (walker_tail.cuh).
 // Nothing of size m x z is stored: no slack array, no ratio matrix, no
 // drift and no refresh.  Per walker-step the tensor cores do 12 m n flops.
 //
@@ -40,6 +40,7 @@
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
 #include "tc_common.cuh"
+#include "walker_tail.cuh"
 
 namespace mhar {
 namespace {
@@ -70,6 +71,8 @@ struct RcParams {
   int j;
   uint32_t walker0;
   int z, kdim, k_chunks, tiles_per_cta, m_tiles;
+  int fused;                // 1: move, re-split and draw in the kernel (walker_tail.cuh)
+  WalkerTail wt;
 };
 
 struct RcTail {
@@ -85,6 +88,8 @@ struct RcTail {
   float part_hi[4][kWalkers];
   float recv_lo[kMaxCluster][kWalkers];   // partial chords pushed by every CTA of the cluster
   float recv_hi[kMaxCluster][kWalkers];
+  float theta_s[kWalkers];
+  unsigned int red[kWalkers];
 };
 
 constexpr size_t kSmemRc = 1024 + static_cast<size_t>(kWSlots) * kWBytes +
@@ -289,10 +294,12 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     if (cg == 0) {
       const float L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
       const float H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
-      // Push this CTA's partial chord into slot `rank` of the cluster's rank 0,
-      // which combines them.
-      st_dsmem_f32(&tail->recv_lo[rank][wl], 0, L);
-      st_dsmem_f32(&tail->recv_hi[rank][wl], 0, H);
+      // Push this CTA's partial chord into slot `rank` of every CTA of the
+      // cluster: each then knows the strip's chords without a second barrier.
+      for (uint32_t r = 0; r < csize; ++r) {
+        st_dsmem_f32(&tail->recv_lo[rank][wl], r, L);
+        st_dsmem_f32(&tail->recv_hi[rank][wl], r, H);
+      }
     }
     if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
@@ -306,7 +313,7 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
                  : "memory");
   }
 
-  if (rank == 0 && warp >= 2 && ((warp - 2) >> 2) == 0) {
+  if ((rank == 0 || p.fused) && warp >= 2 && ((warp - 2) >> 2) == 0) {
     const int q = warp & 3;
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
@@ -315,6 +322,7 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       L = fmaxf(L, tail->recv_lo[r][wl]);
       H = fminf(H, tail->recv_hi[r][wl]);
     }
+    if (p.fused && k >= p.z) tail->theta_s[wl] = 0.0f;
     if (k < p.z) {
       float t = 0.0f;
       int flag = 0;
@@ -330,15 +338,27 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
         t = static_cast<float>(static_cast<double>(L) +
                                u * (static_cast<double>(H) - static_cast<double>(L)));
       }
-      p.lmin[k] = L;
-      p.lmax[k] = H;
-      p.theta[k] = t;
-      p.pend[k] = t;
-      if (flag) {
-        atomicOr(p.status, flag);
-        atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+      if (p.fused) tail->theta_s[wl] = t;
+      if (rank == 0) {
+        p.lmin[k] = L;
+        p.lmax[k] = H;
+        p.theta[k] = t;
+        if (!p.fused) p.pend[k] = t;
+        if (flag) {
+          atomicOr(p.status, flag);
+          atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+        }
       }
     }
+  }
+  if (p.fused && warp >= 2) {
+    named_bar<kEpiWarps * 32>();
+    const int per = (kWalkers + static_cast<int>(csize) - 1) / static_cast<int>(csize);
+    const int w_begin = static_cast<int>(rank) * per;
+    const int w_count = max(0, min(per, kWalkers - w_begin));
+    walker_tail<kEpiWarps * 32>(p.wt, p.seed, *p.step_ptr + static_cast<uint64_t>(p.j) + 1ull,
+                                p.walker0, strip, p.z, w_begin, w_count, tail->theta_s, tail->red,
+                                static_cast<int>(threadIdx.x) - 64);
   }
 }
 
@@ -408,6 +428,8 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   p.k_chunks = c->k_pad / kTcKChunk;
   p.tiles_per_cta = s.tiles_per_cta;
   p.m_tiles = plan->m_tiles;
+  p.fused = c->fused_tail ? 1 : 0;
+  p.wt = make_walker_tail(c, 0);
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(s.C, plan->strips, 1);

@@ -33,6 +33,7 @@
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
 #include "tc_common.cuh"
+#include "walker_tail.cuh"
 
 namespace mhar {
 namespace {
@@ -66,6 +67,8 @@ struct TsParams {
   int j;
   uint32_t walker0;
   int z, z_ld, kdim, k_chunks, k_pad, tiles_per_cta, m_tiles;
+  int fused;                // 1: move, re-split and draw in the kernel (walker_tail.cuh)
+  WalkerTail wt;
 };
 
 struct TsTail {
@@ -79,6 +82,8 @@ struct TsTail {
   float part_hi[4][kWalkers];
   float recv_lo[kMaxCluster][kWalkers];
   float recv_hi[kMaxCluster][kWalkers];
+  float theta_s[kWalkers];
+  unsigned int red[kWalkers];
 };
 
 constexpr size_t kSmemTs = 1024 + static_cast<size_t>(kSlots) * kSlotBytes + sizeof(TsTail);
@@ -296,8 +301,12 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     if (cg == 0) {
       const float L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
       const float H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
-      st_dsmem(&tail->recv_lo[rank][wl], 0, L);
-      st_dsmem(&tail->recv_hi[rank][wl], 0, H);
+      // Every CTA of the cluster gets every partial: each then knows the
+      // strip's chords and theta without a second barrier.
+      for (uint32_t r = 0; r < gridDim.x; ++r) {
+        st_dsmem(&tail->recv_lo[rank][wl], r, L);
+        st_dsmem(&tail->recv_hi[rank][wl], r, H);
+      }
     }
     if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
@@ -311,7 +320,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
                  : "memory");
   }
 
-  if (rank == 0 && warp >= 2 && ((warp - 2) >> 2) == 0) {
+  if ((rank == 0 || p.fused) && warp >= 2 && ((warp - 2) >> 2) == 0) {
     const int q = warp & 3;
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
@@ -320,6 +329,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       L = fmaxf(L, tail->recv_lo[r][wl]);
       H = fminf(H, tail->recv_hi[r][wl]);
     }
+    if (p.fused && k >= p.z) tail->theta_s[wl] = 0.0f;
     if (k < p.z) {
       float t = 0.0f;
       int flag = 0;
@@ -335,15 +345,27 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
         t = static_cast<float>(static_cast<double>(L) +
                                u * (static_cast<double>(H) - static_cast<double>(L)));
       }
-      p.lmin[k] = L;
-      p.lmax[k] = H;
-      p.theta[k] = t;
-      p.pend[k] = t;
-      if (flag) {
-        atomicOr(p.status, flag);
-        atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+      if (p.fused) tail->theta_s[wl] = t;
+      if (rank == 0) {
+        p.lmin[k] = L;
+        p.lmax[k] = H;
+        p.theta[k] = t;
+        if (!p.fused) p.pend[k] = t;
+        if (flag) {
+          atomicOr(p.status, flag);
+          atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+        }
       }
     }
+  }
+  if (p.fused && warp >= 2) {
+    named_bar<kEpiWarps * 32>();
+    const int per = (kWalkers + static_cast<int>(gridDim.x) - 1) / static_cast<int>(gridDim.x);
+    const int w_begin = static_cast<int>(rank) * per;
+    const int w_count = max(0, min(per, kWalkers - w_begin));
+    walker_tail<kEpiWarps * 32>(p.wt, p.seed, *p.step_ptr + static_cast<uint64_t>(p.j) + 1ull,
+                                p.walker0, strip, p.z, w_begin, w_count, tail->theta_s, tail->red,
+                                static_cast<int>(threadIdx.x) - 64);
   }
 }
 
@@ -417,6 +439,8 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   p.k_pad = c->k_pad;
   p.tiles_per_cta = s.tiles_per_cta;
   p.m_tiles = s.m_tiles;
+  p.fused = c->fused_tail ? 1 : 0;
+  p.wt = make_walker_tail(c, 1);
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(s.C, plan->strips, 1);

@@ -137,7 +137,14 @@ __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const 
   }
 }
 
+// Recompute mode with the fused tail and nothing between the draw and the
+// chord: the chord kernel draws the next directions itself.
+bool tail_draws(const mhar_ctx* c) {
+  return recompute(c) && c->fused_tail && c->mE == 0 && c->pc_rank < 0;
+}
+
 int kernels_per_iteration(const mhar_ctx* c) {
+  if (tail_draws(c)) return 1;
   return 1 + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
 }
 
@@ -148,7 +155,12 @@ int emit_count(const mhar_ctx* c) {
 // Direction draw of one iteration (Section 4.3); in recompute mode the same
 // launch first applies the previous iteration's moves and re-splits X.
 cudaError_t enqueue_directions(mhar_ctx* c, int j) {
-  cudaError_t e = recompute(c) ? mhar::launch_prep_walkers(c, j, 7) : mhar::launch_directions(c, j);
+  if (tail_draws(c)) return cudaSuccess;  // drawn by the previous chord kernel
+  cudaError_t e;
+  if (recompute(c))
+    e = mhar::launch_prep_walkers(c, j, c->fused_tail ? 4 : 7);
+  else
+    e = mhar::launch_directions(c, j);
   // Preconditioned draw d = delta .* h + U g; the tensor-core modes split it
   // into the FP16 pair here unless the projection still has to run.
   if (e == cudaSuccess && c->pc_rank >= 0)
@@ -165,12 +177,24 @@ cudaError_t enqueue_chord(mhar_ctx* c, int j) {
   return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
 }
 
-// Recompute mode keeps each walker's last move pending until the next
-// iteration; anything that reads X applies it first.
+// Recompute mode without the fused tail keeps each walker's last move
+// pending until the next iteration; anything that reads X applies it first.
 int flush_pending(mhar_ctx* c) {
-  if (!recompute(c)) return MHAR_OK;
+  if (!recompute(c) || c->fused_tail) return MHAR_OK;
   MHAR_CUDA(mhar::launch_prep_walkers(c, 0, 1), "flush kernel");
   ++c->launches;
+  return MHAR_OK;
+}
+
+// Recompute mode with the fused tail: each chord kernel leaves the FP16
+// operands of the next iteration in place.  After the host changed the state
+// (creation, set_state, a new preconditioner) one preparation launch rebuilds
+// them: the split of X, and the directions when the chord kernel draws them.
+int ensure_operands(mhar_ctx* c) {
+  if (!recompute(c) || !c->fused_tail || c->operands_fresh) return MHAR_OK;
+  MHAR_CUDA(mhar::launch_prep_walkers(c, 0, tail_draws(c) ? 6 : 2), "operand preparation");
+  ++c->launches;
+  c->operands_fresh = true;
   return MHAR_OK;
 }
 
@@ -200,6 +224,8 @@ int capture(mhar_ctx* c, int count, cudaGraphExec_t* out) {
 }
 
 int advance(mhar_ctx* c, int64_t count) {
+  int frc = ensure_operands(c);
+  if (frc) return frc;
   if (c->opts.graph_chunk <= 0) {
     while (count > 0) {
       const int now = count > (1 << 20) ? (1 << 20) : static_cast<int>(count);
@@ -275,6 +301,7 @@ void drop_graphs(mhar_ctx* c) {
 // recomputes the slack from the points.
 int adopt_preconditioner(mhar_ctx* c, int rank) {
   c->pc_rank = rank;
+  c->operands_fresh = false;
   drop_graphs(c);
   if (mixed(c)) {
     MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
@@ -518,6 +545,8 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
     if ((rc = mhar::tc_plan_create(c))) return rc;
     if (recompute(c)) {
+      c->fused_tail = true;
+      c->operands_fresh = false;
       c->use_ts = mhar::ts_eligible(c) && c->opts.smem_operands == 0;
       if ((rc = c->use_ts ? mhar::ts_prepare(c) : mhar::rc_prepare(c))) return rc;
     }
@@ -656,6 +685,7 @@ int mhar_set_state(mhar_ctx* c, const double* X, uint64_t step) {
   if (recompute(c))
     MHAR_CUDA(cudaMemsetAsync(c->d.pend, 0, sizeof(float) * ((c->z + 127) / 128 * 128), c->stream),
               "clear pending moves");
+  c->operands_fresh = false;
   MHAR_CUDA(cudaMemcpyAsync(c->d.step, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream),
             "copy step");
   c->step = step;
@@ -866,6 +896,8 @@ extern "C" {
 
 int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   if (!c || !ms || iters < 1 || iters > 4096) return MHAR_E_ARG;
+  int orc = ensure_operands(c);
+  if (orc) return orc;
   // (1) `iters` real iterations, replayed back to back from one graph.
   auto full = [&]() -> cudaError_t {
     for (int it = 0; it < iters; ++it) {
@@ -891,9 +923,11 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
   c->launches += static_cast<int64_t>(iters) * kernels_per_iteration(c) + 1;
   c->step += static_cast<uint64_t>(iters);
-  e = time_graph(c, dirs, &t_dir);
-  if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
-  c->launches += static_cast<int64_t>(iters) * (1 + (c->mE > 0 ? 1 : 0));
+  if (!tail_draws(c)) {  // otherwise the draw is part of the chord kernel
+    e = time_graph(c, dirs, &t_dir);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
+    c->launches += static_cast<int64_t>(iters) * (kernels_per_iteration(c) - 1);
+  }
   if (stored(c)) {
     auto ref = [&]() -> cudaError_t {
       cudaError_t e2 = cudaSuccess;

@@ -95,6 +95,12 @@ struct mhar_ctx {
   int64_t launches_one = 0;    // kernel nodes in g_one
   bool use_ts = false;         // recompute mode: TMEM-operand kernel (n <= 128)
   int pc_rank = -1;            // -1: isotropic directions; else rank of U (0..32)
+  // Recompute mode: the chord kernel itself moves the walkers, re-splits the
+  // points and (with no projection / preconditioner) draws the next
+  // directions; `operands_fresh` says whether the FP16 operands of the next
+  // iteration are in place (false after any change of state from the host).
+  bool fused_tail = false;
+  bool operands_fresh = false;
   double last_drift = 0.0;
   double max_violation = 0.0;
   double eq_residual = 0.0;

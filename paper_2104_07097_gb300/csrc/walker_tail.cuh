@@ -1,0 +1,201 @@
+// walker_tail.cuh -- the end of a recompute-mode iteration, run inside the
+// chord kernel once theta is known.
+//
+// After the cluster barrier every CTA of a walker strip's cluster holds the
+// strip's 128 chords and theta (computed identically in each CTA), and each
+// CTA takes a contiguous share of the 128 walkers to
+//  (1) move the point, x += theta (d - A_E^T c')  (Section 4.5; c' is the
+//      exact null-space correction of the rounded direction, when m_E > 0),
+//      in double-float arithmetic;
+//  (2) split the moved point into the FP16 operand pair of the next
+//      iteration: x_i / (sigma_i 2^e), 2^e the per-walker power of two with
+//      max_i |x_i| / sigma_i 2^-e in [0.5, 1);
+//  (3) when neither a projection nor a preconditioner follows, draw the next
+//      iteration's direction (Section 4.3, Philox stream 0) straight into its
+//      FP16 pair.
+// The arithmetic is element for element that of prep_walkers_kernel, so a run
+// with the fused tail equals a run with separate preparation launches.
+// Threads take (walker, 8-coordinate chunk) items with the walker fastest, so
+// a warp moves whole chunks of 32 consecutive walkers.
+#pragma once
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+#include "tc_common.cuh"
+
+namespace mhar {
+
+struct WalkerTail {
+  float* Xhi;            // z x n_ld
+  float* Xlo;
+  __half* Dh;            // operand layout (op_off)
+  __half* Dl;
+  __half* Xh;
+  __half* Xl;
+  float* wscale;         // z_ld
+  const float* sigma;    // n_ld
+  const float* AE32;     // mE x n_ld or null
+  const float* corr;     // z x mE or null
+  int mE, n, n_ld, k_pad, z_ld, inter, draw;
+};
+
+// The tail's arguments for a context (`inter`: interleaved operand layout).
+inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter) {
+  WalkerTail t;
+  t.Xhi = c->d.Xhi;
+  t.Xlo = c->d.Xlo;
+  t.Dh = c->d.Dh;
+  t.Dl = c->d.Dl;
+  t.Xh = c->d.Xh;
+  t.Xl = c->d.Xl;
+  t.wscale = c->d.wscale;
+  t.sigma = c->d.sigma;
+  t.AE32 = c->d.AE32;
+  t.corr = c->d.corr;
+  t.mE = c->mE;
+  t.n = c->n;
+  t.n_ld = c->n_ld;
+  t.k_pad = c->k_pad;
+  t.z_ld = (c->z + tc::kWalkers - 1) / tc::kWalkers * tc::kWalkers;
+  t.inter = inter;
+  t.draw = (c->mE == 0 && c->pc_rank < 0) ? 1 : 0;
+  return t;
+}
+
+namespace tail_detail {
+
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void st8(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void ld8h(const __half* p, float* v) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[2 * e] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] & 0xffffu)));
+    v[2 * e + 1] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] >> 16)));
+  }
+}
+// Splits 8 values into FP16 hi / lo halves and stores both 16-byte chunks.
+__device__ __forceinline__ void split_store8(const float* v, __half* hi_dst, __half* lo_dst) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __half h0 = __float2half_rn(v[2 * e]);
+    const __half h1 = __float2half_rn(v[2 * e + 1]);
+    const __half l0 = __float2half_rn(v[2 * e] - __half2float(h0));
+    const __half l1 = __float2half_rn(v[2 * e + 1] - __half2float(h1));
+    h[e] = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+    l[e] = static_cast<uint32_t>(__half_as_ushort(l0)) | (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
+  }
+  *reinterpret_cast<uint4*>(hi_dst) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_dst) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+}  // namespace tail_detail
+
+// Run by kThreads threads (tid = 0..kThreads-1) that share named barrier 1.
+// theta_s: the strip's 128 theta values (shared memory); red: w_count words of
+// shared scratch.  next_step: the iteration the drawn directions belong to.
+template <int kThreads>
+__device__ void walker_tail(const WalkerTail& t, uint64_t seed, uint64_t next_step,
+                            uint32_t walker0, int strip, int z, int w_begin, int w_count,
+                            const float* theta_s, unsigned int* red, int tid) {
+  using namespace tail_detail;
+  const int chunks = (t.n + 7) >> 3;
+  const int items = w_count * chunks;
+  for (int w = tid; w < w_count; w += kThreads) red[w] = 0u;
+  tc::named_bar<kThreads>();
+
+  // (1) move, and the walker's largest scaled coordinate.
+  for (int it = tid; it < items; it += kThreads) {
+    const int c = it / w_count, wo = it - c * w_count;
+    const int k = strip * tc::kWalkers + w_begin + wo;
+    if (k >= z) continue;
+    const int i0 = 8 * c;
+    const size_t xr = static_cast<size_t>(k) * t.n_ld + i0;
+    const float th = theta_s[w_begin + wo];
+    float hi[8];
+    ld8(t.Xhi + xr, hi);
+    if (th != 0.0f) {
+      float lo[8], dh[8], dl[8];
+      ld8(t.Xlo + xr, lo);
+      const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+      ld8h(t.Dh + o, dh);
+      ld8h(t.Dl + o, dl);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = i0 + e;
+        if (i >= t.n) continue;
+        const float d = (dh[e] + dl[e]) * t.sigma[i];
+        df_axpy(hi[e], lo[e], th, d);
+        if (t.corr != nullptr) {
+          float dlt = 0.0f;
+          for (int q = 0; q < t.mE; ++q)
+            dlt = fmaf(t.AE32[static_cast<size_t>(q) * t.n_ld + i],
+                       t.corr[static_cast<size_t>(k) * t.mE + q], dlt);
+          lo[e] = fmaf(-th, dlt, lo[e]);
+        }
+      }
+      st8(t.Xhi + xr, hi);
+      st8(t.Xlo + xr, lo);
+    }
+    float mx = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]) / t.sigma[i0 + e]);
+    atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
+  }
+  tc::named_bar<kThreads>();
+
+  // (2) FP16 pair of the scaled point; (3) the next direction.
+  for (int it = tid; it < items; it += kThreads) {
+    const int c = it / w_count, wo = it - c * w_count;
+    const int k = strip * tc::kWalkers + w_begin + wo;
+    if (k >= z) continue;
+    const int i0 = 8 * c;
+    const size_t xr = static_cast<size_t>(k) * t.n_ld + i0;
+    const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+    const float mx = __uint_as_float(red[wo]);
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
+    const float inv = ldexpf(1.0f, -ex);
+    if (c == 0) t.wscale[k] = ldexpf(1.0f, ex);
+    float hi[8], lo[8], v[8];
+    ld8(t.Xhi + xr, hi);
+    ld8(t.Xlo + xr, lo);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = i0 + e;
+      v[e] = i < t.n ? (hi[e] + lo[e]) * inv / t.sigma[i] : 0.0f;
+    }
+    split_store8(v, t.Xh + o, t.Xl + o);
+    if (t.draw) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (i0 + 4 * h < t.n) {
+          const U4 w = philox_block(seed, next_step, walker0 + static_cast<uint32_t>(k),
+                                    static_cast<uint32_t>(2 * c + h), kStreamDirection);
+          box_muller_f32(w.x, w.y, v[4 * h], v[4 * h + 1]);
+          box_muller_f32(w.z, w.w, v[4 * h + 2], v[4 * h + 3]);
+        } else {
+          v[4 * h] = v[4 * h + 1] = v[4 * h + 2] = v[4 * h + 3] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e >= t.n) v[e] = 0.0f;
+      split_store8(v, t.Dh + o, t.Dl + o);
+    }
+  }
+}
+
+}  // namespace mhar

@@ -86,5 +86,8 @@ def test_time_kernels_reports_device_times(rand100, prec):
         ms = s.time_kernels(32)
         X, step = s.state()
     assert step == 32
-    assert 0 < ms[0] < 1.0 and 0 < ms[1] < 5.0 and 0 <= ms[2] < 5.0
+    # In the recompute mode the chord kernel draws the next directions itself,
+    # so the separate direction time is 0.
+    assert (0 < ms[0] < 1.0 if prec == "mixed" else ms[0] == 0.0)
+    assert 0 < ms[1] < 5.0 and 0 <= ms[2] < 5.0
     assert (X @ p.A.T - p.b).max() <= 1e-6
