@@ -12,7 +12,8 @@
 //   lambda_max = min{ s_i / g_i : g_i > 0 },  lambda_min = max{ s_i / g_i : g_i < 0 }
 //   theta = lambda_min + u (lambda_max - lambda_min)
 // The move X += D diag(theta) is made at the end of the same kernel, which
-// also re-splits X and draws the next directions (walker_tail.cuh).
+// also re-splits X; the next directions are drawn early in the kernel into
+// the other of two direction pairs (walker_tail.cuh).
 // Nothing of size m x z is stored: no slack array, no ratio matrix, no
 // drift and no refresh.  Per walker-step the tensor cores do 12 m n flops.
 //
@@ -59,7 +60,6 @@ constexpr int kMaxCluster = 8;
 struct RcParams {
   const float* bS;          // m_pad: b_i / row_scale_i (FP32)
   const float* wscale;      // z_ld: X[k,:] = wscale[k] (Xh + Xl)[k,:]
-  float* pend;              // z_ld: the move theta each walker still has to make
   double* lmin;
   double* lmax;
   double* theta;
@@ -71,8 +71,7 @@ struct RcParams {
   int j;
   uint32_t walker0;
   int z, kdim, k_chunks, tiles_per_cta, m_tiles;
-  int fused;                // 1: move, re-split and draw in the kernel (walker_tail.cuh)
-  WalkerTail wt;
+  WalkerTail wt;            // walker-side work (walker_tail.cuh)
 };
 
 struct RcTail {
@@ -108,6 +107,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __global__ void __launch_bounds__(kThreadsRc, 1)
 recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
+                    const __grid_constant__ CUtensorMap tm_dh2, const __grid_constant__ CUtensorMap tm_dl2,
                     const __grid_constant__ CUtensorMap tm_xh, const __grid_constant__ CUtensorMap tm_xl,
                     const RcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -118,6 +118,14 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   RcTail* tail = reinterpret_cast<RcTail*>(aslot + kASlots * kABytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  TailItem tail_item;  // the epilogue threads' first tail item
+  tail_item.valid = 0;
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
+  const int csz_i = static_cast<int>(gridDim.x);
+  const int share = (kWalkers + csz_i - 1) / csz_i;   // walkers of this CTA's walker-side work
+  const int w_begin = static_cast<int>(blockIdx.x) * share;
+  const int w_count = max(0, min(share, kWalkers - w_begin));
   const uint32_t rank = blockIdx.x;
   const uint32_t csize = gridDim.x;
   const int strip = blockIdx.y;
@@ -159,8 +167,8 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
             if (w_it >= kWSlots) mbar_wait(&tail->w_empty[s], ((w_it / kWSlots) - 1) & 1, timed_out, p.err);
             uint8_t* dst = wslot + s * kWBytes;
             mbar_expect_tx(&tail->w_full[s], kWBytes);
-            tma_load_2d(dst, &tm_dh, &tail->w_full[s], x, yw);
-            tma_load_2d(dst + kOperandBytes, &tm_dl, &tail->w_full[s], x, yw);
+            tma_load_2d(dst, cur ? &tm_dh2 : &tm_dh, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + kOperandBytes, cur ? &tm_dl2 : &tm_dl, &tail->w_full[s], x, yw);
             tma_load_2d(dst + 2 * kOperandBytes, &tm_xh, &tail->w_full[s], x, yw);
             tma_load_2d(dst + 3 * kOperandBytes, &tm_xl, &tail->w_full[s], x, yw);
             ++w_it;
@@ -243,6 +251,11 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     __syncwarp();
   } else {
     // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
+    // First, while the first row tiles are on their way: iteration s+1's
+    // directions into the other pair (walker_tail.cuh, step 0).
+    if (p.wt.draw)
+      walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
+                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;
@@ -305,15 +318,21 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
 
   // Every push is visible after this barrier; no remote access follows it.
+  // Between its arrive and its wait the epilogue loads its first tail item
+  // (the loads do not depend on theta), so their latency overlaps the barrier.
   tc_fence_before();
-  cluster_sync_all();
+  cluster_arrive();
+  if (warp >= 2)
+    walker_tail_prefetch<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
+                                         static_cast<int>(threadIdx.x) - 64, tail_item);
+  cluster_wait();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
   }
 
-  if ((rank == 0 || p.fused) && warp >= 2 && ((warp - 2) >> 2) == 0) {
+  if (warp >= 2 && ((warp - 2) >> 2) == 0) {
     const int q = warp & 3;
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
@@ -322,7 +341,7 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       L = fmaxf(L, tail->recv_lo[r][wl]);
       H = fminf(H, tail->recv_hi[r][wl]);
     }
-    if (p.fused && k >= p.z) tail->theta_s[wl] = 0.0f;
+    if (k >= p.z) tail->theta_s[wl] = 0.0f;
     if (k < p.z) {
       float t = 0.0f;
       int flag = 0;
@@ -331,19 +350,17 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       } else if (L > H) {
         flag = MHAR_ST_STALL;
       } else {
-        const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
         const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
                                   kStreamChord);
         const double u = open_unit_f64(w.x);
         t = static_cast<float>(static_cast<double>(L) +
                                u * (static_cast<double>(H) - static_cast<double>(L)));
       }
-      if (p.fused) tail->theta_s[wl] = t;
+      tail->theta_s[wl] = t;
       if (rank == 0) {
         p.lmin[k] = L;
         p.lmax[k] = H;
         p.theta[k] = t;
-        if (!p.fused) p.pend[k] = t;
         if (flag) {
           atomicOr(p.status, flag);
           atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
@@ -351,14 +368,10 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       }
     }
   }
-  if (p.fused && warp >= 2) {
+  if (warp >= 2) {
     named_bar<kEpiWarps * 32>();
-    const int per = (kWalkers + static_cast<int>(csize) - 1) / static_cast<int>(csize);
-    const int w_begin = static_cast<int>(rank) * per;
-    const int w_count = max(0, min(per, kWalkers - w_begin));
-    walker_tail<kEpiWarps * 32>(p.wt, p.seed, *p.step_ptr + static_cast<uint64_t>(p.j) + 1ull,
-                                p.walker0, strip, p.z, w_begin, w_count, tail->theta_s, tail->red,
-                                static_cast<int>(threadIdx.x) - 64);
+    walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count, tail->theta_s,
+                                tail->red, static_cast<int>(threadIdx.x) - 64, tail_item);
   }
 }
 
@@ -412,7 +425,6 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   RcParams p;
   p.bS = c->d.bS;
   p.wscale = c->d.wscale;
-  p.pend = c->d.pend;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;
   p.theta = c->d.theta;
@@ -428,7 +440,6 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   p.k_chunks = c->k_pad / kTcKChunk;
   p.tiles_per_cta = s.tiles_per_cta;
   p.m_tiles = plan->m_tiles;
-  p.fused = c->fused_tail ? 1 : 0;
   p.wt = make_walker_tail(c, 0);
 
   cudaLaunchConfig_t cfg = {};
@@ -444,7 +455,7 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, plan->ah, plan->al, plan->dh, plan->dl,
-                            plan->xh, plan->xl, p);
+                            plan->dh2, plan->dl2, plan->xh, plan->xl, p);
 }
 
 }  // namespace mhar

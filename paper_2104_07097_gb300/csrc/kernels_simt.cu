@@ -99,7 +99,12 @@ template <typename T>
 __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
                                   const double* __restrict__ AE64, const double* __restrict__ L,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
-                                  float* corr, int z_ld, int inter, const float* sigma) {
+                                  float* corr, int z_ld, int inter, const float* sigma,
+                                  const uint64_t* step_ptr, int j, __half* Dh1, __half* Dl1) {
+  if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
+    Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
+    Dl = Dl1;
+  }
   __shared__ double cbuf[kThreads / 32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
@@ -170,8 +175,12 @@ __global__ void __launch_bounds__(kPcThreads)
 precondition_kernel(uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0, int z,
                     int n, int n_ld, int rank, const T* __restrict__ delta,
                     const T* __restrict__ U, T* D, int split, int k_pad, int z_ld, int inter,
-                    const float* sigma, __half* Dh, __half* Dl) {
+                    const float* sigma, __half* Dh, __half* Dl, __half* Dh1, __half* Dl1) {
   __shared__ T g[kPcWalkers][kMaxPcRank + 1];
+  if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
+    Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
+    Dl = Dl1;
+  }
   const int k0 = blockIdx.y * kPcWalkers;
   for (int t = threadIdx.x; t < kPcWalkers * (kMaxPcRank + 1); t += kPcThreads)
     g[t / (kMaxPcRank + 1)][t % (kMaxPcRank + 1)] = T(0);
@@ -368,16 +377,16 @@ __global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr,
   }
 }
 
-// Recompute mode, per iteration and walker:
-//  (1) apply the walker's pending move x += theta (d - A_E^T c') left by the
-//      last chord kernel (Section 4.5), and clear it;
-//  (2) split the point into the FP16 pair of the tensor-core operand, as
+// Recompute mode: the walkers' operands for iteration s = step + j, built
+// from the host-visible state (after creation, set_state or a new
+// preconditioner; afterwards each chord kernel leaves them in place):
+//  (2) split each point into the FP16 pair of the tensor-core operand, as
 //      x_i / (sigma_i 2^e) with 2^e a power of two such that
 //      max_i |x_i| / sigma_i 2^-e lies in [0.5, 1);
-//  (3) draw the next iteration's directions (Section 4.3): into the FP16 pair
+//  (3) draw iteration s's directions (Section 4.3): into FP16 pair s % 2
 //      directly when neither a projection nor a preconditioner follows, else
 //      into the FP32 scratch those kernels read.
-// `flags`: bit 0 apply, bit 1 split, bit 2 draw.
+// `flags`: bit 1 split, bit 2 draw.
 // Layout: 32 walkers per block, one per lane; each warp takes 8-coordinate
 // chunks (warp, warp + warps, ...).  A thread reads and writes whole chunks:
 // 32 B of each FP32 row and 16 B of each FP16 operand, so in the interleaved
@@ -414,9 +423,9 @@ __device__ __forceinline__ void st8h(__half* p, const __half* h) {
 
 __global__ void __launch_bounds__(kPrepMaxWarps * 32)
 prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
-                    int z, int z_ld, int n, int n_ld, int k_pad, int mE, float* pend, float* Xhi,
-                    float* Xlo, __half* Dh, __half* Dl, float* D32, const float* AE32,
-                    const float* corr, __half* Xh, __half* Xl, float* wscale, int inter,
+                    int z, int z_ld, int n, int n_ld, int k_pad, const float* Xhi,
+                    const float* Xlo, __half* Dh0, __half* Dl0, __half* Dh1, __half* Dl1,
+                    float* D32, __half* Xh, __half* Xl, float* wscale, int inter,
                     const float* sigma, int draw32) {
   __shared__ float red[kPrepMaxWarps][kPrepWalkers];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -425,74 +434,51 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
   const bool live = k < z;
   const int chunks = (n + 7) >> 3;
   const size_t xr = static_cast<size_t>(k) * n_ld;
+  const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+  __half* Dh = (Dh1 != nullptr && (step & 1ull)) ? Dh1 : Dh0;
+  __half* Dl = (Dl1 != nullptr && (step & 1ull)) ? Dl1 : Dl0;
   auto opo = [&](int i) { return op_off(k, i, k_pad, z_ld, inter); };
-  const float t = (live && (flags & 1)) ? pend[k] : 0.0f;
 
-  // (1) pending move, and the walker's largest scaled coordinate.
-  float mx = 0.0f;
-  if (live && (t != 0.0f || (flags & 2))) {
-    for (int c = warp; c < chunks; c += nwarps) {
-      const int i0 = 8 * c;
-      float hi[8], lo[8];
-      ld8(Xhi + xr + i0, hi);
-      if (t != 0.0f) {
-        float dh[8], dl[8];
+  // (2) the walker's largest scaled coordinate, then its FP16 pair.
+  if (flags & 2) {
+    float mx = 0.0f;
+    if (live)
+      for (int c = warp; c < chunks; c += nwarps) {
+        float hi[8];
+        ld8(Xhi + xr + 8 * c, hi);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (8 * c + e < n) mx = fmaxf(mx, fabsf(hi[e]) / sigma[8 * c + e]);
+      }
+    red[warp][lane] = mx;
+    __syncthreads();
+    if (live) {
+      for (int w = 0; w < nwarps; ++w) mx = fmaxf(mx, red[w][lane]);
+      int ex = 0;
+      if (mx > 0.0f) frexpf(mx, &ex);
+      const float inv = ldexpf(1.0f, -ex);
+      if (warp == 0) wscale[k] = ldexpf(1.0f, ex);
+      for (int c = warp; c < chunks; c += nwarps) {
+        const int i0 = 8 * c;
+        float hi[8], lo[8];
+        ld8(Xhi + xr + i0, hi);
         ld8(Xlo + xr + i0, lo);
-        ld8h(Dh + opo(i0), dh);
-        ld8h(Dl + opo(i0), dl);
+        __half h8[8], l8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int i = i0 + e;
-          if (i >= n) continue;
-          const float d = (dh[e] + dl[e]) * sigma[i];
-          df_axpy(hi[e], lo[e], t, d);
-          if (corr != nullptr) {
-            float dlt = 0.0f;
-            for (int q = 0; q < mE; ++q)
-              dlt = fmaf(AE32[static_cast<size_t>(q) * n_ld + i], corr[static_cast<size_t>(k) * mE + q], dlt);
-            lo[e] = fmaf(-t, dlt, lo[e]);
-          }
+          const float v = i < n ? (hi[e] + lo[e]) * inv / sigma[i] : 0.0f;
+          h8[e] = __float2half_rn(v);
+          l8[e] = __float2half_rn(v - __half2float(h8[e]));
         }
-        st8(Xhi + xr + i0, hi);
-        st8(Xlo + xr + i0, lo);
+        st8h(Xh + opo(i0), h8);
+        st8h(Xl + opo(i0), l8);
       }
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (i0 + e < n) mx = fmaxf(mx, fabsf(hi[e]) / sigma[i0 + e]);
-    }
-  }
-  if (flags & 2) red[warp][lane] = mx;
-  __syncthreads();  // every warp has read pend[k] and its old direction chunks
-  if (live && t != 0.0f && warp == 0) pend[k] = 0.0f;
-
-  // (2) FP16 pair of the scaled point.
-  if ((flags & 2) && live) {
-    for (int w = 0; w < nwarps; ++w) mx = fmaxf(mx, red[w][lane]);
-    int ex = 0;
-    if (mx > 0.0f) frexpf(mx, &ex);
-    const float inv = ldexpf(1.0f, -ex);
-    if (warp == 0) wscale[k] = ldexpf(1.0f, ex);
-    for (int c = warp; c < chunks; c += nwarps) {
-      const int i0 = 8 * c;
-      float hi[8], lo[8];
-      ld8(Xhi + xr + i0, hi);
-      ld8(Xlo + xr + i0, lo);
-      __half h8[8], l8[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = i0 + e;
-        const float v = i < n ? (hi[e] + lo[e]) * inv / sigma[i] : 0.0f;
-        h8[e] = __float2half_rn(v);
-        l8[e] = __float2half_rn(v - __half2float(h8[e]));
-      }
-      st8h(Xh + opo(i0), h8);
-      st8h(Xl + opo(i0), l8);
     }
   }
 
-  // (3) next directions: quads 2c and 2c + 1 of the chunk.
+  // (3) directions: quads 2c and 2c + 1 of each chunk.
   if ((flags & 4) && live) {
-    const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
     for (int c = warp; c < chunks; c += nwarps) {
       const int i0 = 8 * c;
       float v[8];
@@ -755,18 +741,19 @@ cudaError_t launch_directions(mhar_ctx* c, int j) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_projection(mhar_ctx* c) {
+cudaError_t launch_projection(mhar_ctx* c, int j) {
   const int grid = blocks_for(c->z, kThreads / 32);
   if (c->opts.precision == MHAR_FP64) {
     projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr, 0, 0, nullptr);
+        nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
-        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0, c->d.sigma);
+        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0, c->d.sigma,
+        c->d.step, j, c->d.Dh2, c->d.Dl2);
   }
   return cudaGetLastError();
 }
@@ -777,12 +764,13 @@ cudaError_t launch_precondition(mhar_ctx* c, int j, int split) {
   if (c->opts.precision == MHAR_FP64) {
     precondition_kernel<double><<<grid, kPcThreads, 0, c->stream>>>(
         c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
-        c->d.pc_delta64, c->d.pc_U64, c->d.D64, 0, c->k_pad, z_ld, 0, nullptr, nullptr, nullptr);
+        c->d.pc_delta64, c->d.pc_U64, c->d.D64, 0, c->k_pad, z_ld, 0, nullptr, nullptr, nullptr,
+        nullptr, nullptr);
   } else {
     precondition_kernel<float><<<grid, kPcThreads, 0, c->stream>>>(
         c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
         c->d.pc_delta32, c->d.pc_U32, c->d.D32, split, c->k_pad, z_ld, c->use_ts ? 1 : 0,
-        c->d.sigma, c->d.Dh, c->d.Dl);
+        c->d.sigma, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2);
   }
   return cudaGetLastError();
 }
@@ -816,9 +804,8 @@ cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
   const int warps = chunks < kPrepMaxWarps ? chunks : kPrepMaxWarps;
   prep_walkers_kernel<<<blocks_for(c->z, kPrepWalkers), warps * 32, 0, c->stream>>>(
       flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
-      c->mE, c->d.pend, c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.D32, c->d.AE32, c->d.corr,
-      c->d.Xh, c->d.Xl, c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma,
-      (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0);
+      c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2, c->d.D32, c->d.Xh, c->d.Xl,
+      c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma, (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -511,6 +511,8 @@ int tc_plan_create(mhar_ctx* c) {
   if (!make_map(&plan->ah, c->d.Ah, c->k_pad, c->m_pad) ||
       !make_map(&plan->al, c->d.Al, c->k_pad, c->m_pad) ||
       !make_map(&plan->dh, c->d.Dh, c->k_pad, z_ld) || !make_map(&plan->dl, c->d.Dl, c->k_pad, z_ld) ||
+      (c->d.Dh2 && (!make_map(&plan->dh2, c->d.Dh2, c->k_pad, z_ld) ||
+                    !make_map(&plan->dl2, c->d.Dl2, c->k_pad, z_ld))) ||
       !make_map(&plan->xh, c->d.Xh, c->k_pad, z_ld) || !make_map(&plan->xl, c->d.Xl, c->k_pad, z_ld)) {
     delete plan;
     snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed");

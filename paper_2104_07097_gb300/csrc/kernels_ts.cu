@@ -22,8 +22,8 @@
 // other warps and the TMA writes slow it; with A in tensor memory it needs
 // half.
 // The cluster layout (C CTAs along the rows, 128 walkers per CTA), the pushed
-// partial chords, the pending-move convention and the bounded waits are those
-// of kernels_rc.cu.
+// partial chords, the walker-side work (walker_tail.cuh) and the bounded
+// waits are those of kernels_rc.cu.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -51,11 +51,8 @@ constexpr uint32_t kOpCol = 256;                     // first TMEM column of the
 struct TsParams {
   const float* bS;          // m_pad: b_i / row_scale_i
   const float* wscale;      // z_ld
-  const __half* Dh;         // z_ld x k_pad (operands copied into TMEM at start)
-  const __half* Dl;
-  const __half* Xh;
+  const __half* Xh;         // z_ld x k_pad (operands copied into TMEM at start)
   const __half* Xl;
-  float* pend;
   double* lmin;
   double* lmax;
   double* theta;
@@ -67,8 +64,7 @@ struct TsParams {
   int j;
   uint32_t walker0;
   int z, z_ld, kdim, k_chunks, k_pad, tiles_per_cta, m_tiles;
-  int fused;                // 1: move, re-split and draw in the kernel (walker_tail.cuh)
-  WalkerTail wt;
+  WalkerTail wt;            // walker-side work (walker_tail.cuh)
 };
 
 struct TsTail {
@@ -107,6 +103,14 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   TsTail* tail = reinterpret_cast<TsTail*>(base + kSlots * kSlotBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  TailItem tail_item;  // the epilogue threads' first tail item
+  tail_item.valid = 0;
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
+  const int csz_i = static_cast<int>(gridDim.x);
+  const int share = (kWalkers + csz_i - 1) / csz_i;   // walkers of this CTA's walker-side work
+  const int w_begin = static_cast<int>(blockIdx.x) * share;
+  const int w_count = max(0, min(share, kWalkers - w_begin));
   const uint32_t rank = blockIdx.x;
   const int strip = blockIdx.y;
   const int tile0 = static_cast<int>(rank) * p.tiles_per_cta;
@@ -144,7 +148,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int q = warp & 3;
     const int op = e >> 2;
     const int k = strip * kWalkers + q * 32 + lane;
-    const __half* src = op == 0 ? p.Dh : op == 1 ? p.Dl : op == 2 ? p.Xh : p.Xl;
+    const __half* src = op == 0 ? p.wt.Dh[cur] : op == 1 ? p.wt.Dl[cur] : op == 2 ? p.Xh : p.Xl;
     // Operands are interleaved by 8-element chunks: chunk c of walker k is the
     // 16 bytes at (c z_ld + k) 16, so each load below is one contiguous
     // 512-byte line for the warp.
@@ -249,6 +253,11 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     __syncwarp();
   } else {
     // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
+    // First, while the first row tiles are on their way: iteration s+1's
+    // directions into the other pair (walker_tail.cuh, step 0).
+    if (p.wt.draw)
+      walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
+                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;              // 32-column group of each 128-column tile
@@ -312,15 +321,21 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
 
   // Every push is visible after this barrier; no remote access follows it.
+  // Between its arrive and its wait the epilogue loads its first tail item
+  // (the loads do not depend on theta), so their latency overlaps the barrier.
   tc_fence_before();
-  cluster_sync_all();
+  cluster_arrive();
+  if (warp >= 2)
+    walker_tail_prefetch<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
+                                         static_cast<int>(threadIdx.x) - 64, tail_item);
+  cluster_wait();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
   }
 
-  if ((rank == 0 || p.fused) && warp >= 2 && ((warp - 2) >> 2) == 0) {
+  if (warp >= 2 && ((warp - 2) >> 2) == 0) {
     const int q = warp & 3;
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
@@ -329,7 +344,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       L = fmaxf(L, tail->recv_lo[r][wl]);
       H = fminf(H, tail->recv_hi[r][wl]);
     }
-    if (p.fused && k >= p.z) tail->theta_s[wl] = 0.0f;
+    if (k >= p.z) tail->theta_s[wl] = 0.0f;
     if (k < p.z) {
       float t = 0.0f;
       int flag = 0;
@@ -338,19 +353,17 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       } else if (L > H) {
         flag = MHAR_ST_STALL;
       } else {
-        const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
         const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
                                   kStreamChord);
         const double u = open_unit_f64(w.x);
         t = static_cast<float>(static_cast<double>(L) +
                                u * (static_cast<double>(H) - static_cast<double>(L)));
       }
-      if (p.fused) tail->theta_s[wl] = t;
+      tail->theta_s[wl] = t;
       if (rank == 0) {
         p.lmin[k] = L;
         p.lmax[k] = H;
         p.theta[k] = t;
-        if (!p.fused) p.pend[k] = t;
         if (flag) {
           atomicOr(p.status, flag);
           atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
@@ -358,14 +371,10 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       }
     }
   }
-  if (p.fused && warp >= 2) {
+  if (warp >= 2) {
     named_bar<kEpiWarps * 32>();
-    const int per = (kWalkers + static_cast<int>(gridDim.x) - 1) / static_cast<int>(gridDim.x);
-    const int w_begin = static_cast<int>(rank) * per;
-    const int w_count = max(0, min(per, kWalkers - w_begin));
-    walker_tail<kEpiWarps * 32>(p.wt, p.seed, *p.step_ptr + static_cast<uint64_t>(p.j) + 1ull,
-                                p.walker0, strip, p.z, w_begin, w_count, tail->theta_s, tail->red,
-                                static_cast<int>(threadIdx.x) - 64);
+    walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count, tail->theta_s,
+                                tail->red, static_cast<int>(threadIdx.x) - 64, tail_item);
   }
 }
 
@@ -417,11 +426,8 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   TsParams p;
   p.bS = c->d.bS;
   p.wscale = c->d.wscale;
-  p.Dh = c->d.Dh;
-  p.Dl = c->d.Dl;
   p.Xh = c->d.Xh;
   p.Xl = c->d.Xl;
-  p.pend = c->d.pend;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;
   p.theta = c->d.theta;
@@ -439,7 +445,6 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   p.k_pad = c->k_pad;
   p.tiles_per_cta = s.tiles_per_cta;
   p.m_tiles = s.m_tiles;
-  p.fused = c->fused_tail ? 1 : 0;
   p.wt = make_walker_tail(c, 1);
 
   cudaLaunchConfig_t cfg = {};

@@ -81,7 +81,7 @@ bool recompute(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_RECOM
 void free_all(mhar_ctx* c) {
   mhar::DeviceBuffers& d = c->d;
   void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.AE64, d.AE32, d.bE64, d.Lchol, d.Ah, d.Al,
-                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale, d.pend,
+                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale, d.Dh2, d.Dl2,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
                   d.emit, d.check, d.pc_delta64, d.pc_U64, d.pc_delta32, d.pc_U32, d.sigma};
   for (void* p : ptrs)
@@ -137,10 +137,10 @@ __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const 
   }
 }
 
-// Recompute mode with the fused tail and nothing between the draw and the
-// chord: the chord kernel draws the next directions itself.
+// Recompute mode with nothing between the draw and the chord: the chord
+// kernel draws the next directions itself.
 bool tail_draws(const mhar_ctx* c) {
-  return recompute(c) && c->fused_tail && c->mE == 0 && c->pc_rank < 0;
+  return recompute(c) && c->mE == 0 && c->pc_rank < 0;
 }
 
 int kernels_per_iteration(const mhar_ctx* c) {
@@ -156,16 +156,12 @@ int emit_count(const mhar_ctx* c) {
 // launch first applies the previous iteration's moves and re-splits X.
 cudaError_t enqueue_directions(mhar_ctx* c, int j) {
   if (tail_draws(c)) return cudaSuccess;  // drawn by the previous chord kernel
-  cudaError_t e;
-  if (recompute(c))
-    e = mhar::launch_prep_walkers(c, j, c->fused_tail ? 4 : 7);
-  else
-    e = mhar::launch_directions(c, j);
+  cudaError_t e = recompute(c) ? mhar::launch_prep_walkers(c, j, 4) : mhar::launch_directions(c, j);
   // Preconditioned draw d = delta .* h + U g; the tensor-core modes split it
   // into the FP16 pair here unless the projection still has to run.
   if (e == cudaSuccess && c->pc_rank >= 0)
     e = mhar::launch_precondition(c, j, (mixed(c) && c->mE == 0) ? 1 : 0);
-  if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c);
+  if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c, j);
   return e;
 }
 
@@ -177,21 +173,13 @@ cudaError_t enqueue_chord(mhar_ctx* c, int j) {
   return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
 }
 
-// Recompute mode without the fused tail keeps each walker's last move
-// pending until the next iteration; anything that reads X applies it first.
-int flush_pending(mhar_ctx* c) {
-  if (!recompute(c) || c->fused_tail) return MHAR_OK;
-  MHAR_CUDA(mhar::launch_prep_walkers(c, 0, 1), "flush kernel");
-  ++c->launches;
-  return MHAR_OK;
-}
-
-// Recompute mode with the fused tail: each chord kernel leaves the FP16
-// operands of the next iteration in place.  After the host changed the state
-// (creation, set_state, a new preconditioner) one preparation launch rebuilds
-// them: the split of X, and the directions when the chord kernel draws them.
+// Recompute mode: each chord kernel moves its walkers and leaves the FP16
+// operands of the next iteration in place, so X is always current.  After the
+// host changed the state (creation, set_state, a new preconditioner) one
+// preparation launch rebuilds the operands: the split of X, and the
+// directions when the chord kernel draws them.
 int ensure_operands(mhar_ctx* c) {
-  if (!recompute(c) || !c->fused_tail || c->operands_fresh) return MHAR_OK;
+  if (!recompute(c) || c->operands_fresh) return MHAR_OK;
   MHAR_CUDA(mhar::launch_prep_walkers(c, 0, tail_draws(c) ? 6 : 2), "operand preparation");
   ++c->launches;
   c->operands_fresh = true;
@@ -274,8 +262,6 @@ int refresh(mhar_ctx* c) {
 }
 
 int emit_to(mhar_ctx* c, double* out, bool out_device, int walkers) {
-  int rc = flush_pending(c);
-  if (rc) return rc;
   ++c->launches;
   if (out_device) {
     MHAR_CUDA(mhar::launch_emit(c, out, walkers), "emit kernel");
@@ -509,7 +495,8 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
         (rc = dmalloc(c, &d.wscale, z_ld)))
       return rc;
     if (stored(c) && (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld))) return rc;
-    if (recompute(c) && (rc = dmalloc(c, &d.pend, z_ld))) return rc;
+    if (recompute(c) && ((rc = dmalloc(c, &d.Dh2, dsz)) || (rc = dmalloc(c, &d.Dl2, dsz))))
+      return rc;
     if ((rc = dmalloc(c, &d.sigma, c->n_ld)) || (rc = set_unit_sigma(c))) return rc;
   }
 
@@ -545,7 +532,6 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     MHAR_CUDA(mhar::launch_prepare_tc_operands(c), "operand preparation kernel");
     if ((rc = mhar::tc_plan_create(c))) return rc;
     if (recompute(c)) {
-      c->fused_tail = true;
       c->operands_fresh = false;
       c->use_ts = mhar::ts_eligible(c) && c->opts.smem_operands == 0;
       if ((rc = c->use_ts ? mhar::ts_prepare(c) : mhar::rc_prepare(c))) return rc;
@@ -682,9 +668,6 @@ int mhar_set_state(mhar_ctx* c, const double* X, uint64_t step) {
   MHAR_CUDA(cudaMemcpyAsync(c->d.emit, X, sizeof(double) * zn, cudaMemcpyHostToDevice, c->stream),
             "copy X");
   MHAR_CUDA(mhar::launch_set_points(c, c->d.emit), "set points kernel");
-  if (recompute(c))
-    MHAR_CUDA(cudaMemsetAsync(c->d.pend, 0, sizeof(float) * ((c->z + 127) / 128 * 128), c->stream),
-              "clear pending moves");
   c->operands_fresh = false;
   MHAR_CUDA(cudaMemcpyAsync(c->d.step, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream),
             "copy step");
@@ -710,8 +693,7 @@ int mhar_get_chord(const mhar_ctx* cc, double* lmin, double* lmax, double* theta
 
 int mhar_set_preconditioner(mhar_ctx* c, const double* delta, const double* U, int32_t rank) {
   if (!c) return MHAR_E_ARG;
-  int rc = flush_pending(c);
-  if (rc) return rc;
+  int rc = MHAR_OK;
   if (!delta) {
     if (c->pc_rank < 0) return MHAR_OK;
     if ((rc = set_unit_sigma(c))) return rc;
@@ -809,7 +791,6 @@ int mhar_fit_preconditioner(mhar_ctx* c, int64_t warmup, int32_t snapshots, int3
   const int64_t first = warmup - (snapshots - 1) * gap;
   for (int s = 0; s < snapshots && rc == MHAR_OK; ++s) {
     rc = mhar_run(c, s == 0 ? first : gap, 0, nullptr);
-    if (rc == MHAR_OK) rc = flush_pending(c);
     if (rc != MHAR_OK) break;
     cudaError_t e = cudaSuccess;
     if (s == 0) e = mhar::launch_fit_shift(c, &f);
@@ -909,8 +890,6 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   };
   // (2) the direction kernels alone, `iters` times for the current iteration
   // (idempotent: they rewrite the same directions).
-  // (In recompute mode the first of these also applies the last pending
-  // moves; the rest find none.)
   auto dirs = [&]() -> cudaError_t {
     for (int it = 0; it < iters; ++it) {
       cudaError_t e = enqueue_directions(c, 0);
@@ -950,8 +929,6 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
 int mhar_check(mhar_ctx* c, mhar_stats* s) {
   if (!c) return MHAR_E_ARG;
   const unsigned long long init[2] = {host_key(-INFINITY), host_key(0.0)};
-  int frc = flush_pending(c);
-  if (frc) return frc;
   MHAR_CUDA(cudaMemcpyAsync(c->d.check, init, sizeof(init), cudaMemcpyHostToDevice, c->stream),
             "check init");
   MHAR_CUDA(mhar::launch_check(c), "check kernel");

@@ -39,13 +39,16 @@ struct DeviceBuffers {
   float* D32 = nullptr;    // z x n_ld          (FP32 mode; mixed: pre-projection scratch)
   __half* Dh = nullptr;    // z x k_pad         (mixed)
   __half* Dl = nullptr;    // z x k_pad         (mixed)
+  // Recompute mode: a second pair, so that iteration s reads the directions
+  // from pair s % 2 while the next directions go into the other one.
+  __half* Dh2 = nullptr;
+  __half* Dl2 = nullptr;
   float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack / row_scale, blocked:
                            //  element (i, k) at ((i / 4) z_ld + k) 4 + i % 4)
   float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix)
   __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
   __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
   float* wscale = nullptr; // z_ld              (mixed: power-of-two scale of each walker)
-  float* pend = nullptr;   // z_ld              (recompute: move theta not yet applied to X)
 
   // Chord bookkeeping.
   unsigned long long* key_lo = nullptr;  // z: ordered key of lambda_min (atomic max)
@@ -99,7 +102,6 @@ struct mhar_ctx {
   // points and (with no projection / preconditioner) draws the next
   // directions; `operands_fresh` says whether the FP16 operands of the next
   // iteration are in place (false after any change of state from the host).
-  bool fused_tail = false;
   bool operands_fresh = false;
   double last_drift = 0.0;
   double max_violation = 0.0;
@@ -114,11 +116,11 @@ namespace mhar {
 // Every launcher enqueues on ctx->stream and returns cudaGetLastError().
 // `j` is the iteration offset added to the device counter *d.step.
 cudaError_t launch_directions(mhar_ctx* ctx, int j);
-cudaError_t launch_projection(mhar_ctx* ctx);
+cudaError_t launch_projection(mhar_ctx* ctx, int j);
 cudaError_t launch_chord_simt(mhar_ctx* ctx);
 cudaError_t launch_update_simt(mhar_ctx* ctx, int j);
 cudaError_t launch_advance(mhar_ctx* ctx, int steps);
-// Recompute mode: flags bit 0 apply pending moves, bit 1 split X, bit 2 draw D.
+// Recompute mode: flags bit 1 split X, bit 2 draw D (for iteration step + j).
 cudaError_t launch_prep_walkers(mhar_ctx* ctx, int j, int flags);
 cudaError_t launch_emit(mhar_ctx* ctx, double* out_device, int walkers);  // walkers 0..walkers-1
 cudaError_t launch_check(mhar_ctx* ctx);

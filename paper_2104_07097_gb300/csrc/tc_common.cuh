@@ -155,6 +155,14 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// The two halves of cluster_sync_all, for work that fits between them.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                    : "memory");
@@ -191,6 +199,7 @@ __device__ __forceinline__ void named_bar() {
 // Tensor maps and launch shape of one context, shared by both modes.
 struct TcPlan {
   CUtensorMap ah, al, dh, dl, xh, xl;
+  CUtensorMap dh2, dl2;  // recompute mode: the second direction pair
   CUtensorMap ah64, al64;   // A pair with 64-row boxes (TMEM-operand kernel)
   int C = 1;
   int tiles_per_cta = 1;

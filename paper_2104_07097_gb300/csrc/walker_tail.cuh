@@ -1,20 +1,22 @@
-// walker_tail.cuh -- the end of a recompute-mode iteration, run inside the
-// chord kernel once theta is known.
+// walker_tail.cuh -- the walker-side work of a recompute-mode iteration, run
+// inside the chord kernel of iteration s.
 //
-// After the cluster barrier every CTA of a walker strip's cluster holds the
-// strip's 128 chords and theta (computed identically in each CTA), and each
-// CTA takes a contiguous share of the 128 walkers to
+// Every CTA of a walker strip's cluster takes a contiguous share of the
+// strip's 128 walkers.
+// Early, while the first row tiles are still on their way, when neither a
+// projection nor a preconditioner follows the draw:
+//  (0) draw iteration s+1's directions (Section 4.3, Philox stream 0) into
+//      FP16 pair (s+1) % 2 -- the kernel reads pair s % 2, so no one reads
+//      the pair being written.
+// After the cluster barrier, when every CTA holds the strip's 128 chords and
+// theta (computed identically in each CTA):
 //  (1) move the point, x += theta (d - A_E^T c')  (Section 4.5; c' is the
 //      exact null-space correction of the rounded direction, when m_E > 0),
 //      in double-float arithmetic;
 //  (2) split the moved point into the FP16 operand pair of the next
 //      iteration: x_i / (sigma_i 2^e), 2^e the per-walker power of two with
-//      max_i |x_i| / sigma_i 2^-e in [0.5, 1);
-//  (3) when neither a projection nor a preconditioner follows, draw the next
-//      iteration's direction (Section 4.3, Philox stream 0) straight into its
-//      FP16 pair.
-// The arithmetic is element for element that of prep_walkers_kernel, so a run
-// with the fused tail equals a run with separate preparation launches.
+//      max_i |x_i| / sigma_i 2^-e in [0.5, 1).
+// The arithmetic is element for element that of prep_walkers_kernel.
 // Threads take (walker, 8-coordinate chunk) items with the walker fastest, so
 // a warp moves whole chunks of 32 consecutive walkers.
 #pragma once
@@ -30,8 +32,8 @@ namespace mhar {
 struct WalkerTail {
   float* Xhi;            // z x n_ld
   float* Xlo;
-  __half* Dh;            // operand layout (op_off)
-  __half* Dl;
+  __half* Dh[2];         // direction pairs s % 2 (operand layout, op_off)
+  __half* Dl[2];
   __half* Xh;
   __half* Xl;
   float* wscale;         // z_ld
@@ -39,6 +41,7 @@ struct WalkerTail {
   const float* AE32;     // mE x n_ld or null
   const float* corr;     // z x mE or null
   int mE, n, n_ld, k_pad, z_ld, inter, draw;
+  int unit_sigma;        // 1: every sigma_i is 1 (no preconditioner), skip them
 };
 
 // The tail's arguments for a context (`inter`: interleaved operand layout).
@@ -46,8 +49,10 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter) {
   WalkerTail t;
   t.Xhi = c->d.Xhi;
   t.Xlo = c->d.Xlo;
-  t.Dh = c->d.Dh;
-  t.Dl = c->d.Dl;
+  t.Dh[0] = c->d.Dh;
+  t.Dl[0] = c->d.Dl;
+  t.Dh[1] = c->d.Dh2 ? c->d.Dh2 : c->d.Dh;
+  t.Dl[1] = c->d.Dl2 ? c->d.Dl2 : c->d.Dl;
   t.Xh = c->d.Xh;
   t.Xl = c->d.Xl;
   t.wscale = c->d.wscale;
@@ -61,6 +66,7 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter) {
   t.z_ld = (c->z + tc::kWalkers - 1) / tc::kWalkers * tc::kWalkers;
   t.inter = inter;
   t.draw = (c->mE == 0 && c->pc_rank < 0) ? 1 : 0;
+  t.unit_sigma = c->pc_rank < 0 ? 1 : 0;
   return t;
 }
 
@@ -102,13 +108,82 @@ __device__ __forceinline__ void split_store8(const float* v, __half* hi_dst, __h
 
 }  // namespace tail_detail
 
-// Run by kThreads threads (tid = 0..kThreads-1) that share named barrier 1.
-// theta_s: the strip's 128 theta values (shared memory); red: w_count words of
-// shared scratch.  next_step: the iteration the drawn directions belong to.
+// A thread's first item, loaded before theta is known (the loads do not
+// depend on it), so that their latency hides behind the cluster barrier.
+struct TailItem {
+  float hi[8], lo[8], d[8];
+  int valid;
+};
+
+// Item `tid` of the strip's share: x hi / lo and d = sigma (d_hi + d_lo).
 template <int kThreads>
-__device__ void walker_tail(const WalkerTail& t, uint64_t seed, uint64_t next_step,
-                            uint32_t walker0, int strip, int z, int w_begin, int w_count,
-                            const float* theta_s, unsigned int* red, int tid) {
+__device__ __forceinline__ void walker_tail_prefetch(const WalkerTail& t, int cur, int strip,
+                                                     int z, int w_begin, int w_count, int tid,
+                                                     TailItem& r) {
+  using namespace tail_detail;
+  const int chunks = (t.n + 7) >> 3;
+  r.valid = 0;
+  if (w_count <= 0 || tid >= w_count * chunks) return;
+  const int c = tid / w_count, wo = tid - c * w_count;
+  const int k = strip * tc::kWalkers + w_begin + wo;
+  if (k >= z) return;
+  const int i0 = 8 * c;
+  const size_t xr = static_cast<size_t>(k) * t.n_ld + i0;
+  const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+  float dh[8], dl[8];
+  ld8(t.Xhi + xr, r.hi);
+  ld8(t.Xlo + xr, r.lo);
+  ld8h(t.Dh[cur] + o, dh);
+  ld8h(t.Dl[cur] + o, dl);
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    r.d[e] = i0 + e < t.n ? (t.unit_sigma ? dh[e] + dl[e] : (dh[e] + dl[e]) * t.sigma[i0 + e]) : 0.0f;
+  r.valid = 1;
+}
+
+// (0): run by kThreads threads (tid = 0..kThreads-1); `next_step` = s + 1.
+template <int kThreads>
+__device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, uint64_t next_step,
+                                 uint32_t walker0, int strip, int z, int w_begin, int w_count,
+                                 int tid) {
+  using namespace tail_detail;
+  const int chunks = (t.n + 7) >> 3;
+  const int items = w_count * chunks;
+  __half* Dh = t.Dh[cur ^ 1];
+  __half* Dl = t.Dl[cur ^ 1];
+  for (int it = tid; it < items; it += kThreads) {
+    const int c = it / w_count, wo = it - c * w_count;
+    const int k = strip * tc::kWalkers + w_begin + wo;
+    if (k >= z) continue;
+    const int i0 = 8 * c;
+    const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+    float v[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (i0 + 4 * h < t.n) {
+        const U4 w = philox_block(seed, next_step, walker0 + static_cast<uint32_t>(k),
+                                  static_cast<uint32_t>(2 * c + h), kStreamDirection);
+        box_muller_f32(w.x, w.y, v[4 * h], v[4 * h + 1]);
+        box_muller_f32(w.z, w.w, v[4 * h + 2], v[4 * h + 3]);
+      } else {
+        v[4 * h] = v[4 * h + 1] = v[4 * h + 2] = v[4 * h + 3] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (i0 + e >= t.n) v[e] = 0.0f;
+    split_store8(v, Dh + o, Dl + o);
+  }
+}
+
+// (1) and (2): run by kThreads threads (tid = 0..kThreads-1) that share named
+// barrier 1.  theta_s: the strip's 128 theta values (shared memory); red:
+// w_count words of shared scratch; `cur` = s % 2.  `first`: item tid,
+// prefetched; items tid + kThreads, ... are loaded here.
+template <int kThreads>
+__device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int w_begin,
+                            int w_count, const float* theta_s, unsigned int* red, int tid,
+                            TailItem& first) {
   using namespace tail_detail;
   const int chunks = (t.n + 7) >> 3;
   const int items = w_count * chunks;
@@ -123,20 +198,30 @@ __device__ void walker_tail(const WalkerTail& t, uint64_t seed, uint64_t next_st
     const int i0 = 8 * c;
     const size_t xr = static_cast<size_t>(k) * t.n_ld + i0;
     const float th = theta_s[w_begin + wo];
-    float hi[8];
-    ld8(t.Xhi + xr, hi);
-    if (th != 0.0f) {
-      float lo[8], dh[8], dl[8];
+    const bool cached = it == tid && first.valid;
+    float hi[8], lo[8], d[8];
+    if (cached) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) { hi[e] = first.hi[e]; lo[e] = first.lo[e]; d[e] = first.d[e]; }
+    } else {
+      ld8(t.Xhi + xr, hi);
       ld8(t.Xlo + xr, lo);
-      const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
-      ld8h(t.Dh + o, dh);
-      ld8h(t.Dl + o, dl);
+      if (th != 0.0f) {
+        float dh[8], dl[8];
+        const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+        ld8h(t.Dh[cur] + o, dh);
+        ld8h(t.Dl[cur] + o, dl);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          d[e] = i0 + e < t.n ? (t.unit_sigma ? dh[e] + dl[e] : (dh[e] + dl[e]) * t.sigma[i0 + e]) : 0.0f;
+      }
+    }
+    if (th != 0.0f) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int i = i0 + e;
         if (i >= t.n) continue;
-        const float d = (dh[e] + dl[e]) * t.sigma[i];
-        df_axpy(hi[e], lo[e], th, d);
+        df_axpy(hi[e], lo[e], th, d[e]);
         if (t.corr != nullptr) {
           float dlt = 0.0f;
           for (int q = 0; q < t.mE; ++q)
@@ -148,15 +233,25 @@ __device__ void walker_tail(const WalkerTail& t, uint64_t seed, uint64_t next_st
       st8(t.Xhi + xr, hi);
       st8(t.Xlo + xr, lo);
     }
-    float mx = 0.0f;
+    if (cached) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]) / t.sigma[i0 + e]);
+      for (int e = 0; e < 8; ++e) { first.hi[e] = hi[e]; first.lo[e] = lo[e]; }
+    }
+    float mx = 0.0f;
+    if (t.unit_sigma) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]));
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]) / t.sigma[i0 + e]);
+    }
     atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
   }
   tc::named_bar<kThreads>();
 
-  // (2) FP16 pair of the scaled point; (3) the next direction.
+  // (2) FP16 pair of the scaled point.
   for (int it = tid; it < items; it += kThreads) {
     const int c = it / w_count, wo = it - c * w_count;
     const int k = strip * tc::kWalkers + w_begin + wo;
@@ -170,31 +265,24 @@ __device__ void walker_tail(const WalkerTail& t, uint64_t seed, uint64_t next_st
     const float inv = ldexpf(1.0f, -ex);
     if (c == 0) t.wscale[k] = ldexpf(1.0f, ex);
     float hi[8], lo[8], v[8];
-    ld8(t.Xhi + xr, hi);
-    ld8(t.Xlo + xr, lo);
+    if (it == tid && first.valid) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int i = i0 + e;
-      v[e] = i < t.n ? (hi[e] + lo[e]) * inv / t.sigma[i] : 0.0f;
+      for (int e = 0; e < 8; ++e) { hi[e] = first.hi[e]; lo[e] = first.lo[e]; }
+    } else {
+      ld8(t.Xhi + xr, hi);
+      ld8(t.Xlo + xr, lo);
+    }
+    if (t.unit_sigma) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = i0 + e < t.n ? (hi[e] + lo[e]) * inv : 0.0f;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = i0 + e;
+        v[e] = i < t.n ? (hi[e] + lo[e]) * inv / t.sigma[i] : 0.0f;
+      }
     }
     split_store8(v, t.Xh + o, t.Xl + o);
-    if (t.draw) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (i0 + 4 * h < t.n) {
-          const U4 w = philox_block(seed, next_step, walker0 + static_cast<uint32_t>(k),
-                                    static_cast<uint32_t>(2 * c + h), kStreamDirection);
-          box_muller_f32(w.x, w.y, v[4 * h], v[4 * h + 1]);
-          box_muller_f32(w.z, w.w, v[4 * h + 2], v[4 * h + 3]);
-        } else {
-          v[4 * h] = v[4 * h + 1] = v[4 * h + 2] = v[4 * h + 3] = 0.0f;
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (i0 + e >= t.n) v[e] = 0.0f;
-      split_store8(v, t.Dh + o, t.Dl + o);
-    }
   }
 }
 
