@@ -120,8 +120,6 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   TailItem tail_item;  // the epilogue threads' first tail item
   tail_item.valid = 0;
-  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
-  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
   const int csz_i = static_cast<int>(gridDim.x);
   const int share = (kWalkers + csz_i - 1) / csz_i;   // walkers of this CTA's walker-side work
   const int w_begin = static_cast<int>(blockIdx.x) * share;
@@ -153,6 +151,12 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   tc_fence_after();
   const uint32_t tmem = tail->tmem_base;
   volatile int* timed_out = &tail->timed_out;
+  // Launched as a programmatic dependent of the previous iteration's kernel:
+  // the set-up above overlaps its end; nothing it wrote is read before this.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
 
   if (warp == 0) {
     // ---- TMA producer --------------------------------------------------------
@@ -447,13 +451,17 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   cfg.blockDim = dim3(kThreadsRc, 1, 1);
   cfg.dynamicSmemBytes = kSmemRc;
   cfg.stream = c->stream;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = s.C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // Programmatic dependent launch: the grid may be scheduled while the
+  // previous kernel finishes; it waits (griddepcontrol.wait) before reading.
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, plan->ah, plan->al, plan->dh, plan->dl,
                             plan->dh2, plan->dl2, plan->xh, plan->xl, p);
 }

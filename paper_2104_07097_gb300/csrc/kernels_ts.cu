@@ -105,8 +105,6 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   TailItem tail_item;  // the epilogue threads' first tail item
   tail_item.valid = 0;
-  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
-  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
   const int csz_i = static_cast<int>(gridDim.x);
   const int share = (kWalkers + csz_i - 1) / csz_i;   // walkers of this CTA's walker-side work
   const int w_begin = static_cast<int>(blockIdx.x) * share;
@@ -140,6 +138,12 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   tc_fence_after();
   const uint32_t tmem = tail->tmem_base;
   volatile int* timed_out = &tail->timed_out;
+  // Launched as a programmatic dependent of the previous iteration's kernel:
+  // the set-up above overlaps its end; nothing it wrote is read before this.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+  const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
 
   // ---- walker operands into tensor memory: warp (quarter q, operand op) ------
   // writes its 32 walkers' row of operand op, 2 FP16 per 32-bit column.
@@ -452,13 +456,17 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   cfg.blockDim = dim3(kThreadsTs, 1, 1);
   cfg.dynamicSmemBytes = kSmemTs;
   cfg.stream = c->stream;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = s.C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // Programmatic dependent launch: the grid may be scheduled while the
+  // previous kernel finishes; it waits (griddepcontrol.wait) before reading.
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, recompute_ts_kernel, plan->ah64, plan->al64, p);
 }
 
