@@ -259,6 +259,56 @@ int mhar_get_preconditioner(const mhar_ctx* ctx, double* delta, double* U, int32
 int mhar_fit_preconditioner(mhar_ctx* ctx, int64_t warmup, int32_t snapshots, int32_t rank,
                             int32_t power_iters);
 
+/* ---- batches of polytopes ------------------------------------------------- */
+/* Many independent problems advanced together, one kernel launch per
+ * iteration for all of them (the paper runs one polytope at a time; its
+ * padding study, Section 6.2, is about filling the GPU with walkers, which a
+ * batch does with problems).  Every problem is a full MHAR_MIXED_RECOMPUTE
+ * sampler of its own (Algorithm 2, Lemma 4.2 on the tensor cores) with z
+ * walkers, no equalities, and Philox key opts.seed + p for problem p, so
+ * problem p's walk is the one a single context with that seed would take.
+ * The launch covers every (problem, strip of 128 walkers) unit, largest
+ * first, each on a cluster of C CTAs along its rows; mhar_batch_tune picks C. */
+typedef struct {
+  const double* A;   /* m x n, row-major (copied)                 */
+  const double* b;   /* m                                         */
+  int32_t m, n;
+  const double* x0;  /* n, strictly inside A x <= b                */
+} mhar_problem;
+
+typedef struct mhar_batch mhar_batch;
+
+/* Creates the batch: `count` problems, z walkers each.  opts as for
+ * mhar_create (precision is forced to MHAR_MIXED_RECOMPUTE; stream,
+ * out_on_device and emit_walkers apply to every problem).  Errors as
+ * mhar_create, for the first problem that fails. */
+int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
+                      const mhar_opts* opts, mhar_batch** out);
+
+/* Autotuner: times `iters` (1..1024) real iterations of the batch for every
+ * cluster size C in {1, 2, 4, 8} (up to the largest problem's row tiles) and
+ * keeps the fastest; *cluster (may be NULL) receives it.  The timed
+ * iterations advance every walk.  Results do not depend on C. */
+int mhar_batch_tune(mhar_batch* batch, int32_t iters, int32_t* cluster);
+
+/* Advances every problem `steps` iterations; out[p] receives problem p's
+ * floor(steps / thin) samples, laid out as for mhar_run (out[p] may be NULL
+ * to skip a problem).  Returns the first problem's failure code (unbounded,
+ * non-finite) after the whole call. */
+int mhar_batch_run(mhar_batch* batch, int64_t steps, int64_t thin, double* const* out);
+
+/* Problem p's points (z x n, host FP64) and iteration counter. */
+int mhar_batch_get_state(const mhar_batch* batch, int32_t problem, double* X, uint64_t* step);
+
+/* mhar_check for problem p (kernel_launches adds the batch's own launches). */
+int mhar_batch_check(mhar_batch* batch, int32_t problem, mhar_stats* stats);
+
+/* Description of the batch's last error (never NULL). */
+const char* mhar_batch_last_error(const mhar_batch* batch);
+
+/* Frees the batch and every problem's device memory; NULL is ignored. */
+void mhar_batch_destroy(mhar_batch* batch);
+
 /* Human-readable description of the last error on ctx (never NULL); with
  * ctx == NULL, the last mhar_chord_noalloc failure on this host thread. */
 const char* mhar_last_error(const mhar_ctx* ctx);

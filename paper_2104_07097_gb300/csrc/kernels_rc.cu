@@ -36,7 +36,10 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
@@ -104,12 +107,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreadsRc, 1)
-recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
-                    const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
-                    const __grid_constant__ CUtensorMap tm_dh2, const __grid_constant__ CUtensorMap tm_dl2,
-                    const __grid_constant__ CUtensorMap tm_xh, const __grid_constant__ CUtensorMap tm_xl,
-                    const RcParams p) {
+// Tensor maps of one problem: A pair, both direction pairs, point pair.
+struct RcMaps {
+  CUtensorMap ah, al, dh, dl, dh2, dl2, xh, xl;
+};
+
+// One cluster's work for one walker strip of one problem (`strip`), iteration
+// step + j.  The maps may live in kernel parameters or in global memory.
+__device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int strip, int j) {
+  const CUtensorMap& tm_ah = mp.ah;
+  const CUtensorMap& tm_al = mp.al;
+  const CUtensorMap& tm_dh = mp.dh;
+  const CUtensorMap& tm_dl = mp.dl;
+  const CUtensorMap& tm_dh2 = mp.dh2;
+  const CUtensorMap& tm_dl2 = mp.dl2;
+  const CUtensorMap& tm_xh = mp.xh;
+  const CUtensorMap& tm_xl = mp.xl;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -126,7 +139,6 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   const int w_count = max(0, min(share, kWalkers - w_begin));
   const uint32_t rank = blockIdx.x;
   const uint32_t csize = gridDim.x;
-  const int strip = blockIdx.y;
   const int tile0 = static_cast<int>(rank) * p.tiles_per_cta;
   int ntiles = p.m_tiles - tile0;
   ntiles = ntiles < 0 ? 0 : (ntiles > p.tiles_per_cta ? p.tiles_per_cta : ntiles);
@@ -155,7 +167,7 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   // the set-up above overlaps its end; nothing it wrote is read before this.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(p.j);
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(j);
   const int cur = static_cast<int>(step & 1ull);  // this iteration's direction pair
 
   if (warp == 0) {
@@ -379,6 +391,27 @@ recompute_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
 }
 
+
+__global__ void __launch_bounds__(kThreadsRc, 1)
+recompute_tc_kernel(const __grid_constant__ RcMaps maps, const __grid_constant__ RcParams p) {
+  rc_body(maps, p, static_cast<int>(blockIdx.y), p.j);
+}
+
+// Batched form: one launch for many problems.  blockIdx.y indexes a unit, a
+// (problem, walker strip) pair, whose maps and parameters are in global
+// memory; every unit's cluster is gridDim.x CTAs along its rows.
+struct alignas(128) BatchUnit {
+  RcMaps maps;
+  RcParams p;
+  int strip;
+};
+
+__global__ void __launch_bounds__(kThreadsRc, 1)
+recompute_batch_kernel(const BatchUnit* __restrict__ units, int j) {
+  const BatchUnit& u = units[blockIdx.y];
+  rc_body(u.maps, u.p, u.strip, j);
+}
+
 struct RcShape {
   int C = 1;
   int tiles_per_cta = 1;
@@ -423,9 +456,10 @@ int rc_prepare(mhar_ctx* c) {
   return MHAR_OK;
 }
 
-cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
+namespace {
+
+RcParams rc_params(const mhar_ctx* c, int j, int tiles_per_cta) {
   const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
-  const RcShape s = rc_shape(c, plan);
   RcParams p;
   p.bS = c->d.bS;
   p.wscale = c->d.wscale;
@@ -442,18 +476,33 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   p.z = c->z;
   p.kdim = c->kdim;
   p.k_chunks = c->k_pad / kTcKChunk;
-  p.tiles_per_cta = s.tiles_per_cta;
+  p.tiles_per_cta = tiles_per_cta;
   p.m_tiles = plan->m_tiles;
   p.wt = make_walker_tail(c, 0);
+  return p;
+}
 
+RcMaps rc_maps(const TcPlan* plan) {
+  RcMaps maps;
+  maps.ah = plan->ah;
+  maps.al = plan->al;
+  maps.dh = plan->dh;
+  maps.dl = plan->dl;
+  maps.dh2 = plan->dh2;
+  maps.dl2 = plan->dl2;
+  maps.xh = plan->xh;
+  maps.xl = plan->xl;
+  return maps;
+}
+
+cudaLaunchConfig_t rc_config(int C, int rows, cudaStream_t stream, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(s.C, plan->strips, 1);
+  cfg.gridDim = dim3(C, rows, 1);
   cfg.blockDim = dim3(kThreadsRc, 1, 1);
   cfg.dynamicSmemBytes = kSmemRc;
-  cfg.stream = c->stream;
-  cudaLaunchAttribute attr[2];
+  cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = s.C;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   // Programmatic dependent launch: the grid may be scheduled while the
@@ -462,8 +511,74 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, plan->ah, plan->al, plan->dh, plan->dl,
-                            plan->dh2, plan->dl2, plan->xh, plan->xl, p);
+  return cfg;
+}
+
+}  // namespace
+
+cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  const RcShape s = rc_shape(c, plan);
+  const RcParams p = rc_params(c, j, s.tiles_per_cta);
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = rc_config(s.C, plan->strips, c->stream, attr);
+  return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, rc_maps(plan), p);
+}
+
+// ---- batches ------------------------------------------------------------------
+int batch_table_build(mhar_ctx* const* ctx, int count, int C, void** table, int* units,
+                      char* err, size_t err_len) {
+  *table = nullptr;
+  *units = 0;
+  cudaError_t e = cudaFuncSetAttribute(recompute_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemRc));
+  if (e != cudaSuccess) {
+    snprintf(err, err_len, "batch kernel attributes: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    return MHAR_E_CUDA;
+  }
+  std::vector<BatchUnit> host;
+  for (int q = 0; q < count; ++q) {
+    const mhar_ctx* c = ctx[q];
+    const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+    const int tpc = (plan->m_tiles + C - 1) / C;
+    for (int st = 0; st < plan->strips; ++st) {
+      BatchUnit u;
+      std::memset(&u, 0, sizeof(u));
+      u.maps = rc_maps(plan);
+      u.p = rc_params(c, 0, tpc);
+      u.strip = st;
+      host.push_back(u);
+    }
+  }
+  // Largest units first: CTAs start in grid order, so the long ones do not
+  // end up alone at the end of the launch.
+  std::stable_sort(host.begin(), host.end(), [](const BatchUnit& a, const BatchUnit& b) {
+    return static_cast<long long>(a.p.m_tiles) * a.p.k_chunks >
+           static_cast<long long>(b.p.m_tiles) * b.p.k_chunks;
+  });
+  void* d = nullptr;
+  e = cudaMalloc(&d, sizeof(BatchUnit) * host.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d, host.data(), sizeof(BatchUnit) * host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (d) cudaFree(d);
+    snprintf(err, err_len, "batch table: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    return MHAR_E_CUDA;
+  }
+  *table = d;
+  *units = static_cast<int>(host.size());
+  return MHAR_OK;
+}
+
+cudaError_t launch_recompute_batch(const void* table, int units, int C, int j,
+                                   cudaStream_t stream) {
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = rc_config(C, units, stream, attr);
+  return cudaLaunchKernelEx(&cfg, recompute_batch_kernel,
+                            static_cast<const BatchUnit*>(table), j);
 }
 
 }  // namespace mhar

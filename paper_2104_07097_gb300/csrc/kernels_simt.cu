@@ -403,15 +403,6 @@ __device__ __forceinline__ void st8(float* p, const float* v) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
 }
-__device__ __forceinline__ void ld8h(const __half* p, float* v) {
-  const uint4 u = *reinterpret_cast<const uint4*>(p);
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    v[2 * e] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] & 0xffffu)));
-    v[2 * e + 1] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] >> 16)));
-  }
-}
 __device__ __forceinline__ uint32_t pack2h(__half a, __half b) {
   return static_cast<uint32_t>(__half_as_ushort(a)) |
          (static_cast<uint32_t>(__half_as_ushort(b)) << 16);
@@ -513,6 +504,11 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
 }
 
 __global__ void advance_kernel(uint64_t* step_ptr, int steps) { *step_ptr += steps; }
+
+__global__ void advance_many_kernel(uint64_t* const* steps, int count, int by) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) *steps[i] += static_cast<uint64_t>(by);
+}
 
 __global__ void emit_kernel(int mode, int z, int n, int n_ld, const double* X64, const float* Xhi,
                             const float* Xlo, double* out) {
@@ -806,6 +802,11 @@ cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
       flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
       c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2, c->d.D32, c->d.Xh, c->d.Xl,
       c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma, (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_many(uint64_t* const* steps, int count, int by, cudaStream_t stream) {
+  advance_many_kernel<<<blocks_for(count, kThreads), kThreads, 0, stream>>>(steps, count, by);
   return cudaGetLastError();
 }
 

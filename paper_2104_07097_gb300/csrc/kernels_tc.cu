@@ -552,4 +552,7 @@ cudaError_t launch_refresh_tc(mhar_ctx* c) {
   return launch_walker_tc(c, kModeRefresh, 0);
 }
 
+int tc_plan_strips(const mhar_ctx* c) { return static_cast<const TcPlan*>(c->tc)->strips; }
+int tc_plan_m_tiles(const mhar_ctx* c) { return static_cast<const TcPlan*>(c->tc)->m_tiles; }
+
 }  // namespace mhar

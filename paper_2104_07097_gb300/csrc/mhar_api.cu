@@ -942,3 +942,292 @@ int mhar_check(mhar_ctx* c, mhar_stats* s) {
 }
 
 }  // extern "C"
+
+// ---- batches of problems ----------------------------------------------------------
+struct mhar_batch {
+  std::vector<mhar_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int z = 0;
+  int C = 1;
+  void* table = nullptr;
+  int units = 0;
+  uint64_t** steps = nullptr;   // device array of every problem's step counter
+  cudaGraphExec_t g_chunk = nullptr;
+  cudaGraphExec_t g_one = nullptr;
+  int graph_len = 16;
+  int64_t launches = 0;
+  int64_t walker_steps = 0;
+  mhar_opts opts{};
+  char err[512] = {0};
+};
+
+namespace {
+
+void batch_err(mhar_batch* b, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->err, sizeof(b->err), fmt, ap);
+  va_end(ap);
+}
+
+int batch_cuda(mhar_batch* b, cudaError_t e, const char* what) {
+  batch_err(b, "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return MHAR_E_CUDA;
+}
+
+void batch_drop_graphs(mhar_batch* b) {
+  if (b->g_chunk) cudaGraphExecDestroy(b->g_chunk);
+  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  b->g_chunk = b->g_one = nullptr;
+}
+
+int batch_set_shape(mhar_batch* b, int C) {
+  batch_drop_graphs(b);
+  if (b->table) cudaFree(b->table);
+  b->table = nullptr;
+  int rc = mhar::batch_table_build(b->ctx.data(), static_cast<int>(b->ctx.size()), C, &b->table,
+                                   &b->units, b->err, sizeof(b->err));
+  if (rc == MHAR_OK) b->C = C;
+  return rc;
+}
+
+cudaError_t batch_enqueue(mhar_batch* b, int count) {
+  for (int j = 0; j < count; ++j) {
+    cudaError_t e = mhar::launch_recompute_batch(b->table, b->units, b->C, j, b->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return mhar::launch_advance_many(b->steps, static_cast<int>(b->ctx.size()), count, b->stream);
+}
+
+int batch_capture(mhar_batch* b, int count, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return batch_cuda(b, e, "begin capture");
+  cudaError_t eb = batch_enqueue(b, count);
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (eb != cudaSuccess) e = eb;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e == cudaSuccess ? MHAR_OK : batch_cuda(b, e, "batch graph");
+}
+
+int batch_advance(mhar_batch* b, int64_t count) {
+  for (mhar_ctx* c : b->ctx) {
+    int rc = ensure_operands(c);
+    if (rc) {
+      batch_err(b, "%s", c->err);
+      return rc;
+    }
+  }
+  if (!b->g_one) {
+    int rc = batch_capture(b, 1, &b->g_one);
+    if (rc == MHAR_OK) rc = batch_capture(b, b->graph_len, &b->g_chunk);
+    if (rc) return rc;
+  }
+  const int64_t n = count;
+  while (count >= b->graph_len) {
+    cudaError_t e = cudaGraphLaunch(b->g_chunk, b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
+    count -= b->graph_len;
+    b->launches += b->graph_len + 1;
+  }
+  while (count-- > 0) {
+    cudaError_t e = cudaGraphLaunch(b->g_one, b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
+    b->launches += 2;
+  }
+  for (mhar_ctx* c : b->ctx) c->step += static_cast<uint64_t>(n);
+  b->walker_steps += n * b->z * static_cast<int64_t>(b->ctx.size());
+  return MHAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
+                      const mhar_opts* opts, mhar_batch** out) {
+  if (!out) return MHAR_E_ARG;
+  *out = nullptr;
+  if (!problems || count < 1 || z < 1) return MHAR_E_ARG;
+  mhar_batch* b = new (std::nothrow) mhar_batch();
+  if (!b) return MHAR_E_ARG;
+  if (opts) b->opts = *opts; else mhar_default_opts(&b->opts);
+  b->z = z;
+  int rc = MHAR_OK;
+  if (b->opts.stream) {
+    b->stream = static_cast<cudaStream_t>(b->opts.stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = batch_cuda(b, e, "stream create");
+    b->own_stream = true;
+  }
+  for (int q = 0; q < count && rc == MHAR_OK; ++q) {
+    const mhar_problem& pr = problems[q];
+    mhar_opts o = b->opts;
+    o.seed = b->opts.seed + static_cast<uint64_t>(q);
+    o.precision = MHAR_MIXED_RECOMPUTE;
+    o.smem_operands = 1;
+    o.stream = b->stream;
+    o.graph_chunk = 0;
+    mhar_ctx* c = nullptr;
+    rc = mhar_create(pr.A, pr.b, pr.m, pr.n, nullptr, nullptr, 0, pr.x0, z, &o, &c);
+    if (rc != MHAR_OK) {
+      batch_err(b, "problem %d: %s", q, mhar_strerror(rc));
+      break;
+    }
+    b->ctx.push_back(c);
+  }
+  if (rc == MHAR_OK) {
+    std::vector<uint64_t*> steps;
+    for (mhar_ctx* c : b->ctx) steps.push_back(c->d.step);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->steps), sizeof(uint64_t*) * steps.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->steps, steps.data(), sizeof(uint64_t*) * steps.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = batch_cuda(b, e, "step table");
+  }
+  if (rc == MHAR_OK) {
+    // Default shape: one CTA per unit when the units alone fill the GPU.
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->device);
+    int strips = 0;
+    for (mhar_ctx* c : b->ctx) strips += mhar::tc_plan_strips(c);
+    int C = 1;
+    while (C < 8 && strips * C * 2 <= sms) C *= 2;
+    rc = batch_set_shape(b, C);
+  }
+  if (rc != MHAR_OK) {
+    fprintf(stderr, "mhar_batch_create: %s (%s)\n", b->err, mhar_strerror(rc));
+    mhar_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return MHAR_OK;
+}
+
+int mhar_batch_tune(mhar_batch* b, int32_t iters, int32_t* cluster) {
+  if (!b || iters < 1 || iters > 1024) return MHAR_E_ARG;
+  int max_tiles = 1;
+  for (mhar_ctx* c : b->ctx)
+    max_tiles = std::max(max_tiles, mhar::tc_plan_m_tiles(c));
+  int best_C = b->C;
+  float best = INFINITY;
+  for (int C = 1; C <= 8; C *= 2) {
+    if (C > max_tiles) break;
+    int rc = batch_set_shape(b, C);
+    if (rc) return rc;
+    rc = batch_advance(b, 1);  // warm-up and graph capture
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    if (e == cudaSuccess) {
+      rc = batch_advance(b, iters);
+      if (rc) return rc;
+      e = cudaEventRecord(e1, b->stream);
+    }
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return batch_cuda(b, e, "tuning");
+    if (ms < best) {
+      best = ms;
+      best_C = C;
+    }
+  }
+  int rc = batch_set_shape(b, best_C);
+  if (rc) return rc;
+  if (cluster) *cluster = best_C;
+  return MHAR_OK;
+}
+
+int mhar_batch_run(mhar_batch* b, int64_t steps, int64_t thin, double* const* out) {
+  if (!b || steps < 0 || thin < 0) return MHAR_E_ARG;
+  const int64_t nsamp = thin > 0 ? steps / thin : 0;
+  if (nsamp > 0 && !out) {
+    batch_err(b, "out is NULL but samples are due");
+    return MHAR_E_ARG;
+  }
+  for (mhar_ctx* c : b->ctx) {
+    cudaError_t e = cudaMemsetAsync(c->d.status, 0, 2 * sizeof(int), b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "status reset");
+  }
+  int64_t done = 0, emitted = 0;
+  while (done < steps) {
+    int64_t adv = steps - done;
+    if (thin > 0) adv = std::min<int64_t>(adv, thin - (done % thin));
+    int rc = batch_advance(b, adv);
+    if (rc) return rc;
+    done += adv;
+    if (thin > 0 && done % thin == 0 && emitted < nsamp) {
+      for (size_t q = 0; q < b->ctx.size(); ++q) {
+        mhar_ctx* c = b->ctx[q];
+        if (!out[q]) continue;
+        rc = emit_to(c, out[q] + static_cast<size_t>(emitted) * emit_count(c) * c->n,
+                     c->opts.out_on_device != 0, emit_count(c));
+        if (rc) {
+          batch_err(b, "problem %zu: %s", q, c->err);
+          return rc;
+        }
+      }
+      ++emitted;
+    }
+  }
+  int worst = MHAR_OK;
+  for (size_t q = 0; q < b->ctx.size(); ++q) {
+    mhar_ctx* c = b->ctx[q];
+    int st[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, c->d.status, sizeof(st), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "status copy");
+    c->status_bits |= st[0];
+    if (st[1]) {
+      batch_err(b, "problem %zu: tensor-core pipeline wait timed out", q);
+      return MHAR_E_CUDA;
+    }
+    if ((st[0] & MHAR_ST_NONFINITE) && worst == MHAR_OK) {
+      batch_err(b, "problem %zu: non-finite slack or direction met", q);
+      worst = MHAR_E_NONFINITE;
+    }
+    if ((st[0] & MHAR_ST_UNBOUNDED) && worst == MHAR_OK) {
+      batch_err(b, "problem %zu: a chord open on one side (unbounded body)", q);
+      worst = MHAR_E_UNBOUNDED;
+    }
+  }
+  return worst;
+}
+
+int mhar_batch_get_state(const mhar_batch* b, int32_t problem, double* X, uint64_t* step) {
+  if (!b || problem < 0 || problem >= static_cast<int>(b->ctx.size())) return MHAR_E_ARG;
+  return mhar_get_state(b->ctx[problem], X, step);
+}
+
+int mhar_batch_check(mhar_batch* b, int32_t problem, mhar_stats* stats) {
+  if (!b || problem < 0 || problem >= static_cast<int>(b->ctx.size())) return MHAR_E_ARG;
+  int rc = mhar_check(b->ctx[problem], stats);
+  if (rc == MHAR_OK && stats) stats->kernel_launches += b->launches;  // the batch's own launches
+  return rc;
+}
+
+const char* mhar_batch_last_error(const mhar_batch* b) {
+  if (!b) return "null batch";
+  return b->err[0] ? b->err : "no error";
+}
+
+void mhar_batch_destroy(mhar_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graphs(b);
+  if (b->table) cudaFree(b->table);
+  if (b->steps) cudaFree(b->steps);
+  for (mhar_ctx* c : b->ctx) mhar_destroy(c);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -152,6 +152,8 @@ const char* noalloc_last_error();
 
 // ---- tensor-core path (kernels_tc.cu) ---------------------------------------
 int tc_plan_create(mhar_ctx* ctx);            // 0 or MHAR_E_*
+int tc_plan_strips(const mhar_ctx* ctx);      // walker strips of 128
+int tc_plan_m_tiles(const mhar_ctx* ctx);     // row tiles of 128
 void tc_plan_destroy(mhar_ctx* ctx);
 cudaError_t launch_chord_tc(mhar_ctx* ctx, int j);
 cudaError_t launch_refresh_tc(mhar_ctx* ctx);       // X split + S = b - A X (2 launches)
@@ -160,6 +162,15 @@ cudaError_t launch_split_points(mhar_ctx* ctx);     // X -> FP16 pair + per-walk
 // ---- recompute-slack tensor-core path (kernels_rc.cu) ------------------------
 int rc_prepare(mhar_ctx* ctx);                      // 0 or MHAR_E_*
 cudaError_t launch_recompute_tc(mhar_ctx* ctx, int j);
+
+// Batches (one launch per iteration for many problems, recompute mode with
+// shared-memory operands): a device table of (problem, walker strip) units
+// for clusters of C CTAs, largest units first.
+int batch_table_build(mhar_ctx* const* ctx, int count, int C, void** table, int* units,
+                      char* err, size_t err_len);
+cudaError_t launch_recompute_batch(const void* table, int units, int C, int j,
+                                   cudaStream_t stream);
+cudaError_t launch_advance_many(uint64_t* const* steps, int count, int by, cudaStream_t stream);
 
 // ---- recompute-slack, walker operands in tensor memory (kernels_ts.cu) -------
 bool ts_eligible(const mhar_ctx* ctx);              // n <= 128

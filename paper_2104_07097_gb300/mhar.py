@@ -38,7 +38,9 @@ ST_NONFINITE = 4
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
            "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
            "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
-           "mhar_fit_preconditioner", "mhar_last_error", "mhar_strerror", "mhar_destroy")
+           "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_run",
+           "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
+           "mhar_batch_destroy", "mhar_last_error", "mhar_strerror", "mhar_destroy")
 
 
 class MharOpts(ctypes.Structure):
@@ -56,6 +58,12 @@ class MharStats(ctypes.Structure):
                 ("status_bits", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_drift", ctypes.c_double), ("max_violation", ctypes.c_double),
                 ("eq_residual", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class MharProblem(ctypes.Structure):
+    _fields_ = [("A", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("x0", ctypes.POINTER(ctypes.c_double))]
 
 
 class MharError(RuntimeError):
@@ -111,6 +119,21 @@ def load(path: str | None = None):
     lib.mhar_fit_preconditioner.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32]
     lib.mhar_fit_preconditioner.restype = ctypes.c_int
+    lib.mhar_batch_create.argtypes = [ctypes.POINTER(MharProblem), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(MharOpts), ctypes.POINTER(vp)]
+    lib.mhar_batch_create.restype = ctypes.c_int
+    lib.mhar_batch_tune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.mhar_batch_tune.restype = ctypes.c_int
+    lib.mhar_batch_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(vp)]
+    lib.mhar_batch_run.restype = ctypes.c_int
+    lib.mhar_batch_get_state.argtypes = [vp, ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mhar_batch_get_state.restype = ctypes.c_int
+    lib.mhar_batch_check.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(MharStats)]
+    lib.mhar_batch_check.restype = ctypes.c_int
+    lib.mhar_batch_last_error.argtypes = [vp]
+    lib.mhar_batch_last_error.restype = ctypes.c_char_p
+    lib.mhar_batch_destroy.argtypes = [vp]
+    lib.mhar_batch_destroy.restype = None
     lib.mhar_last_error.argtypes = [vp]
     lib.mhar_last_error.restype = ctypes.c_char_p
     lib.mhar_strerror.argtypes = [ctypes.c_int]
@@ -357,6 +380,107 @@ class Sampler:
         if getattr(self, "_ctx", None):
             mhar_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many polytopes advanced together, one launch per iteration
+    (``mhar_batch_*``).  ``problems``: list of (A, b, x0); problem p uses
+    Philox key seed + p; every problem has z walkers; recompute tensor-core mode."""
+
+    def __init__(self, problems, z: int, seed: int = 0, stream=None, out_on_device: bool = False,
+                 emit_walkers: int = 0):
+        o = mhar_default_opts()
+        o.seed = int(seed)
+        o.precision = MIXED_RECOMPUTE
+        o.out_on_device = 1 if out_on_device else 0
+        o.emit_walkers = int(emit_walkers)
+        if stream is not None:
+            o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        self._keep = []
+        arr = (MharProblem * len(problems))()
+        self.shapes = []
+        for q, (A, b, x0) in enumerate(problems):
+            A, b, x0 = _f64(A), _f64(b), _f64(x0)
+            self._keep += [A, b, x0]
+            m, n = A.shape
+            arr[q] = MharProblem(_dp(A), _dp(b), m, n, _dp(x0))
+            self.shapes.append((m, n))
+        self.z = int(z)
+        self.emit_walkers = int(emit_walkers) if emit_walkers > 0 else self.z
+        self.out_on_device = out_on_device
+        ctx = ctypes.c_void_p()
+        rc = load().mhar_batch_create(arr, len(problems), self.z, ctypes.byref(o), ctypes.byref(ctx))
+        if rc != OK:
+            raise MharError(rc, f"mhar_batch_create failed: {mhar_strerror(rc)}")
+        self._b = ctx
+
+    def _err(self, rc):
+        raise MharError(rc, load().mhar_batch_last_error(self._b).decode())
+
+    def tune(self, iters: int = 8) -> int:
+        c = ctypes.c_int32()
+        rc = load().mhar_batch_tune(self._b, int(iters), ctypes.byref(c))
+        if rc != OK:
+            self._err(rc)
+        return int(c.value)
+
+    def run(self, steps: int, thin: int = 0, outs=None):
+        """Advances every problem; with thin > 0 returns (or fills) one
+        floor(steps/thin) x W x n array per problem (host numpy, or device
+        tensors / pointers for out_on_device batches)."""
+        nsamp = steps // thin if thin > 0 else 0
+        ptrs = (ctypes.c_void_p * len(self.shapes))()
+        if nsamp > 0:
+            if outs is None:
+                if self.out_on_device:
+                    raise ValueError("out_on_device batch needs device outputs")
+                outs = [np.zeros((nsamp, self.emit_walkers, n)) for (_, n) in self.shapes]
+            for q, o in enumerate(outs):
+                if o is None:
+                    ptrs[q] = None
+                elif isinstance(o, np.ndarray):
+                    ptrs[q] = o.ctypes.data
+                elif hasattr(o, "data_ptr"):
+                    ptrs[q] = o.data_ptr()
+                else:
+                    ptrs[q] = int(o)
+        rc = load().mhar_batch_run(self._b, int(steps), int(thin), ptrs if nsamp > 0 else None)
+        if rc != OK:
+            self._err(rc)
+        return outs
+
+    def state(self, q: int):
+        m, n = self.shapes[q]
+        X = np.zeros((self.z, n))
+        step = ctypes.c_uint64()
+        rc = load().mhar_batch_get_state(self._b, int(q), _dp(X), ctypes.byref(step))
+        if rc != OK:
+            self._err(rc)
+        return X, int(step.value)
+
+    def check(self, q: int) -> MharStats:
+        st = MharStats()
+        rc = load().mhar_batch_check(self._b, int(q), ctypes.byref(st))
+        if rc != OK:
+            self._err(rc)
+        return st
+
+    def close(self) -> None:
+        if getattr(self, "_b", None):
+            load().mhar_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

@@ -18,6 +18,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import math
+
 import numpy as np
 
 
@@ -73,14 +75,31 @@ def simplex(n: int) -> Polytope:
                     bE=np.ones(1), name=f"simplex{n}")
 
 
-def random_polytope(n: int, m: int, seed: int, check_bounded: bool = True) -> Polytope:
+def unbounded_probability(m: int, n: int) -> float:
+    """Wendel (1962): m iid symmetric random vectors in R^n lie in a common
+    half-space with probability 2^-(m-1) sum_{k<n} C(m-1, k); for unit
+    Gaussian rows that is the probability that {A x <= 1} is unbounded."""
+    if m <= n:
+        return 1.0
+    return float(sum(math.comb(m - 1, k) for k in range(n)) / 2 ** (m - 1))
+
+
+def random_polytope(n: int, m: int, seed: int, check_bounded="yes") -> Polytope:
     """m rows iid N(0, I_n) normalised to unit length, b = 1, x0 = 0.  Redraws
-    with the next seed until the body is bounded (only matters for m near 2n)."""
+    with the next seed until the body is bounded.  check_bounded: "yes" (one LP
+    per draw), "no", or "auto" (the LP only when Wendel's probability of an
+    unbounded draw exceeds 1e-12, i.e. for m near 2n)."""
+    if check_bounded is True:
+        check_bounded = "yes"
+    elif check_bounded is False:
+        check_bounded = "no"
     s = seed
     while True:
         rng = np.random.default_rng(s)
         A = _unit_rows(rng, m, n)
-        if not check_bounded or is_bounded(A):
+        need = check_bounded == "yes" or (check_bounded == "auto" and
+                                          unbounded_probability(m, n) > 1e-12)
+        if not need or is_bounded(A):
             return Polytope(A=A, b=np.ones(m), x0=np.zeros(n), name=f"rand{n}x{m}s{s}")
         s += 1_000_003
 
@@ -113,7 +132,7 @@ def batch(count: int, seed: int, nmin: int = 20, nmax: int = 400,
     for p in range(count):
         n = int(rng.integers(nmin, nmax + 1))
         m = int(rng.integers(mfac[0] * n, mfac[1] * n + 1))
-        out.append(random_polytope(n, m, seed=seed * 100_003 + p))
+        out.append(random_polytope(n, m, seed=seed * 100_003 + p, check_bounded="auto"))
     return out
 
 
