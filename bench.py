@@ -16,6 +16,11 @@ CUDA cores, and the same tensor-core mode), each with 500 + 5000 iterations,
 and reports min-ESS (over coordinates, from a trace of 64 walkers every 5th
 iteration, scaled to all z walkers) per second of device time.
 
+A third leg ("batched") times 256 random polytopes of different sizes (n
+uniform in 20..400, m uniform in 2n..20n, z = 512 each, 1000 iterations)
+advanced together by one kernel launch per iteration, with the cluster size
+chosen by the library's autotuner.
+
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
 """
@@ -40,6 +45,7 @@ WORKLOAD = dict(name="rand100x2000", n=100, m=2000, seed=2, z=4096, iterations=2
 METRIC = "walker-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
+BATCH_WORKLOAD = dict(name="batch256", count=256, seed=4, z=512, iterations=1000, tune_iters=8)
 ESS_WORKLOAD = dict(name="illcond500x10000", n=500, m=10000, seed=5, z=16384, warmup=500,
                     iterations=5000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
                     snapshots=5, power_iters=4)
@@ -166,6 +172,40 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def batch_leg(stream, torch, mhar, peaks) -> dict:
+    """256 random polytopes (n ~ U{20..400}, m ~ U{2n..20n}), z = 512 each, one
+    kernel launch per iteration for all of them, cluster size autotuned."""
+    B = BATCH_WORKLOAD
+    bodies = wl.batch(B["count"], seed=B["seed"])
+    z, iters = B["z"], B["iterations"]
+    t0 = time.perf_counter()
+    bt = mhar.Batch([(p.A, p.b, p.x0) for p in bodies], z, seed=0, stream=stream)
+    create_s = time.perf_counter() - t0
+    try:
+        C = bt.tune(B["tune_iters"])
+        bt.run(16)  # warm-up with the chosen shape (graph capture)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        bt.run(iters)
+        b.record(stream)
+        torch.cuda.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        worst = max(bt.check(q).max_violation for q in range(len(bodies)))
+    finally:
+        bt.close()
+    flops = 12.0 * sum(p.m * p.n for p in bodies) * z * iters
+    peak = peaks["bf16_tflops_sustained"]
+    return {"workload": f"{B['name']}: {B['count']} random polytopes, n ~ U{{20..400}}, "
+                        f"m ~ U{{2n..20n}}, z={z} each, {iters} iterations",
+            "value": B["count"] * z * iters / secs, "unit": METRIC,
+            "seconds": secs, "cluster": C, "launches_per_iteration": 1,
+            "create_seconds": create_s,
+            "roofline": {"bound": "tensor", "achieved": flops / secs / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / secs / 1e12 / peak},
+            "max_violation": worst}
+
+
 def ess_leg(stream, torch, mhar) -> dict:
     """min-ESS/s of learned-preconditioned vs plain MHAR on the ill-conditioned body."""
     from paper_2104_07097_gb300 import diagnostics
@@ -221,6 +261,7 @@ def main() -> None:
     ap.add_argument("--precision", default="mixed_rs", choices=["mixed_rs", "mixed", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ess", action="store_true", help="skip the min-ESS/s comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-polytope leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -291,7 +332,8 @@ def main() -> None:
         roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
                     "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
                     "traffic": None,
-                    "kernel": "recompute_tc_kernel" if args.precision == "mixed_rs" else "walker_tc_kernel",
+                    "kernel": ("recompute_ts_kernel" if n <= 128 else "recompute_tc_kernel")
+                              if args.precision == "mixed_rs" else "walker_tc_kernel",
                     "algorithmic": f"{2 * nprod} m n tensor flops per walker-step ({nprod} FP16 products)",
                     "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}
     else:
@@ -351,6 +393,8 @@ def main() -> None:
                 "feasibility": {"max_violation": st.max_violation, "refresh_drift": st.refresh_drift,
                                 "stalls": st.stalls},
                 "plain_fp32": plain}
+        if world == 1 and not args.no_batch and args.precision == "mixed_rs":
+            line["batched"] = batch_leg(stream, torch, mhar, peaks)
         if world == 1 and not args.no_ess:
             line["ess"] = ess_leg(stream, torch, mhar)
         if world == 1 and not args.no_cpu_baseline:
