@@ -93,7 +93,14 @@ typedef struct {
   int32_t  emit_walkers;  /* samples written by mhar_run hold walkers 0..W-1
                              only (0 = all z); e.g. a trace of a subset for
                              effective-sample-size estimates                 */
-  int32_t  reserved[4];   /* must be zero                                     */
+  int32_t  schedule;      /* recompute mode with shared-memory operands (n > 128
+                             or smem_operands): 0 (default) picks the faster
+                             of 1 = clusters of CTAs along the rows of A and
+                             2 = stream-K (every SM takes an equal share of
+                             the (walker strip, row tile) work; strips split
+                             over SMs combine their partial chords in global
+                             memory).  Results do not depend on it.          */
+  int32_t  reserved[3];   /* must be zero                                     */
 } mhar_opts;
 
 typedef struct {

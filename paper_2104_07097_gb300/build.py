@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmhar.so")
-SOURCES = ["mhar_api.cu", "kernels_simt.cu", "kernels_tc.cu", "kernels_rc.cu", "kernels_ts.cu", "noalloc.cu", "kernels_fit.cu"]
+SOURCES = ["mhar_api.cu", "kernels_simt.cu", "kernels_tc.cu", "kernels_rc.cu", "kernels_ts.cu", "noalloc.cu", "kernels_fit.cu", "kernels_sk.cu"]
 HEADERS = ["mhar_device.cuh", "mhar_internal.h", "tc_common.cuh", "walker_tail.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

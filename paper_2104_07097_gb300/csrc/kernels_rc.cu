@@ -295,25 +295,28 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
       __syncwarp();
       if (lane == 0) mbar_arrive(&tail->t_empty[b]);
       const float4* br4 = reinterpret_cast<const float4*>(p.bS + row_base + nt * kRowsTile + cg * 32);
-      float br[32];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float4 v = __ldg(br4 + i);
-        br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
-      }
+      for (int h = 0; h < 2; ++h) {
+        float br[16];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const float gg = c < 16 ? g0[c] : g1[c - 16];
-        const float pp = c < 16 ? p0[c] : p1[c - 16];
-        const float sv = fmaf(-pp, ws, br[c]);
-        const float ss = fmaxf(sv, 0.0f);
-        chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
-        // s/g improves the bound on its side iff s < bound * g (g > 0: upper
-        // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
-        const float bnd = gg > 0.0f ? hi : lo;
-        if (ss < bnd * gg) {
-          const float r = __fdividef(ss, gg);
-          if (gg > 0.0f) hi = r; else lo = r;
+        for (int i = 0; i < 4; ++i) {
+          const float4 v = __ldg(br4 + 4 * h + i);
+          br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float gg = h == 0 ? g0[c] : g1[c];
+          const float pp = h == 0 ? p0[c] : p1[c];
+          const float sv = fmaf(-pp, ws, br[c]);
+          const float ss = fmaxf(sv, 0.0f);
+          chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
+          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
+          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
+          const float bnd = gg > 0.0f ? hi : lo;
+          if (ss < bnd * gg) {
+            const float r = __fdividef(ss, gg);
+            if (gg > 0.0f) hi = r; else lo = r;
+          }
         }
       }
     }
@@ -435,6 +438,22 @@ RcShape rc_shape(const mhar_ctx* c, const TcPlan* plan) {
 }
 
 }  // namespace
+
+bool rc_prefers_stream_k(const mhar_ctx* c) {
+  const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const RcShape s = rc_shape(c, plan);
+  // Row tiles on the busiest SM: clusters run in waves of `sms` CTAs; the
+  // stream-K cut gives every SM an equal share plus about one tile of
+  // per-segment overhead.
+  const long long ctas = static_cast<long long>(plan->strips) * s.C;
+  const long long waves = (ctas + sms - 1) / sms;
+  const long long cluster_cost = waves * s.tiles_per_cta;
+  const long long total = static_cast<long long>(plan->strips) * plan->m_tiles;
+  const long long sk_cost = (total + sms - 1) / sms + 1;
+  return sk_cost * 100 < cluster_cost * 93;
+}
 
 int rc_prepare(mhar_ctx* c) {
   const TcPlan* plan = static_cast<const TcPlan*>(c->tc);

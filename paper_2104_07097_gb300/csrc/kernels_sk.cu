@@ -1,0 +1,492 @@
+// kernels_sk.cu -- the recompute-slack walker step (MHAR_MIXED_RECOMPUTE,
+// shared-memory walker operands, n > 128) with a stream-K schedule.
+//
+// Same arithmetic as kernels_rc.cu (Lemma 4.2 on the tensor cores: P = X A^T
+// and G = D A^T from FP16 pairs, three products each, FP32 accumulation;
+// s = b - p; the chord; theta; the walker-side work of walker_tail.cuh).
+// The schedule differs: when the walker strips (128 walkers each) are fewer
+// than the SMs, clusters along the rows leave SMs idle (128 strips of 79 row
+// tiles on 152 SMs keep 24 idle).  Here every SM runs one CTA, and the
+// (strip, row tile) work is cut into equal contiguous ranges, one per CTA, so
+// that a strip's rows may be split over several CTAs ("segments").  A CTA
+// whose segment covers a whole strip finishes it alone; otherwise each
+// segment writes its partial chords (lambda_min, lambda_max of its rows) to
+// global memory and bumps the strip's counter, and the CTA that completes
+// the strip combines the partials (max / min, exact, so the result does not
+// depend on the cut), draws theta and does the walker-side work for the
+// whole strip.  Next iteration's directions are drawn early by the strip's
+// segments, each for its share of the walkers.
+// The pipelines (TMA producer, MMA issuer, 16 epilogue warps, double-buffered
+// accumulators) run across segment boundaries without re-initialisation.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mhar_device.cuh"
+#include "mhar_internal.h"
+#include "tc_common.cuh"
+#include "walker_tail.cuh"
+
+namespace mhar {
+namespace {
+
+using namespace tc;
+
+constexpr int kWSlots = 2;                           // walker-operand slots (Dh, Dl, Xh, Xl chunk)
+constexpr int kASlots = 5;                           // A half-slots
+constexpr int kWBytes = 4 * kOperandBytes;
+constexpr int kABytes = kOperandBytes;
+constexpr int kEpiWarps = 16;
+constexpr int kThreadsSk = (2 + kEpiWarps) * 32;
+
+// One contiguous range of row tiles of one strip, processed by one CTA.
+struct SkSeg {
+  int strip;     // walker strip (128 walkers)
+  int t0, t1;    // row tiles [t0, t1)
+  int slot;      // index of this segment among the strip's segments
+  int nseg;      // number of segments of the strip
+};
+
+struct SkParams {
+  const float* bS;
+  const float* wscale;
+  double* lmin;
+  double* lmax;
+  double* theta;
+  int* status;
+  unsigned long long* counters;
+  int* err;
+  const uint64_t* step_ptr;
+  uint64_t seed;
+  uint32_t walker0;
+  int z, kdim, k_chunks;
+  const SkSeg* segs;        // all segments, grouped by CTA
+  const int* seg_begin;     // CTA b owns segs[seg_begin[b] .. seg_begin[b + 1])
+  float* partials;          // [strip][slot][2][128]: lambda_min, lambda_max of a segment
+  int* arrivals;            // [strip]: segments done this iteration (reset by the last)
+  int max_nseg;
+  WalkerTail wt;
+};
+
+struct SkTail {
+  uint64_t w_full[kWSlots];
+  uint64_t w_empty[kWSlots];
+  uint64_t a_full[kASlots];
+  uint64_t a_empty[kASlots];
+  uint64_t t_full[2];
+  uint64_t t_empty[2];
+  uint32_t tmem_base;
+  int timed_out;
+  int last;                       // this CTA completes the current strip
+  float part_lo[4][kWalkers];
+  float part_hi[4][kWalkers];
+  float theta_s[kWalkers];
+  unsigned int red[kWalkers];
+};
+
+constexpr size_t kSmemSk = 1024 + static_cast<size_t>(kWSlots) * kWBytes +
+                           static_cast<size_t>(kASlots) * kABytes + sizeof(SkTail);
+
+__device__ __forceinline__ void mbar_arrive_sk(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsSk, 1)
+recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+                    const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
+                    const __grid_constant__ CUtensorMap tm_dh2, const __grid_constant__ CUtensorMap tm_dl2,
+                    const __grid_constant__ CUtensorMap tm_xh, const __grid_constant__ CUtensorMap tm_xl,
+                    const __grid_constant__ SkParams p, int j) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* wslot = base;
+  uint8_t* aslot = base + kWSlots * kWBytes;
+  SkTail* tail = reinterpret_cast<SkTail*>(aslot + kASlots * kABytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
+    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    tail->timed_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_tmap(&tm_ah);
+    prefetch_tmap(&tm_al);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)), "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tail->tmem_base;
+  volatile int* timed_out = &tail->timed_out;
+  // Programmatic dependent of the previous iteration's kernel: nothing it
+  // wrote is read before this.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const uint64_t step = *p.step_ptr + static_cast<uint64_t>(j);
+  const int cur = static_cast<int>(step & 1ull);
+  const int sb = p.seg_begin[blockIdx.x], se = p.seg_begin[blockIdx.x + 1];
+
+  if (warp == 0) {
+    // ---- TMA producer: walker operand chunk and A hi / lo per (tile, k chunk) --
+    if (lane == 0) {
+      int w_it = 0, a_it = 0;
+      for (int sg = sb; sg < se; ++sg) {
+        const SkSeg seg = p.segs[sg];
+        const int yw = seg.strip * kWalkers;
+        for (int nt = seg.t0; nt < seg.t1; ++nt) {
+          for (int kc = 0; kc < p.k_chunks; ++kc) {
+            const int x = kc * kTcKChunk;
+            int s = w_it % kWSlots;
+            if (w_it >= kWSlots) mbar_wait(&tail->w_empty[s], ((w_it / kWSlots) - 1) & 1, timed_out, p.err);
+            uint8_t* dst = wslot + s * kWBytes;
+            mbar_expect_tx(&tail->w_full[s], kWBytes);
+            tma_load_2d(dst, cur ? &tm_dh2 : &tm_dh, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + kOperandBytes, cur ? &tm_dl2 : &tm_dl, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + 2 * kOperandBytes, &tm_xh, &tail->w_full[s], x, yw);
+            tma_load_2d(dst + 3 * kOperandBytes, &tm_xl, &tail->w_full[s], x, yw);
+            ++w_it;
+            const int yr = nt * kRowsTile;
+            for (int half = 0; half < 2; ++half, ++a_it) {
+              s = a_it % kASlots;
+              if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, p.err);
+              mbar_expect_tx(&tail->a_full[s], kABytes);
+              tma_load_2d(aslot + s * kABytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s], x, yr);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer: G = (Dh + Dl) A^T and P = (Xh + Xl) A^T, 3 products each --
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      int w_it = 0, a_it = 0, gt = 0;
+      for (int sg = sb; sg < se; ++sg) {
+        const SkSeg seg = p.segs[sg];
+        for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
+          const int b = gt & 1;
+          if (gt >= 2) mbar_wait(&tail->t_empty[b], ((gt >> 1) - 1) & 1, timed_out, p.err);
+          tc_fence_after();
+          const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
+          const uint32_t p_tmem = g_tmem + 128u;
+          for (int kc = 0; kc < p.k_chunks; ++kc) {
+            const int ws = w_it % kWSlots;
+            mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
+            const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
+            const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
+            const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
+            int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
+            ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
+            int as = a_it % kASlots;
+            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
+            tc_fence_after();
+            uint64_t ad = sw128_desc(smem_u32(aslot + as * kABytes));
+#pragma unroll 4
+            for (int ks = 0; ks < ks_n; ++ks) {
+              const uint64_t o = static_cast<uint64_t>(2 * ks);
+              const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+              mma_f16(g_tmem, dh + o, ad + o, idesc, acc);
+              mma_f16(g_tmem, dl + o, ad + o, idesc, 1u);
+              mma_f16(p_tmem, xh + o, ad + o, idesc, acc);
+              mma_f16(p_tmem, xl + o, ad + o, idesc, 1u);
+            }
+            mma_commit(&tail->a_empty[as]);
+            ++a_it;
+            as = a_it % kASlots;
+            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
+            tc_fence_after();
+            ad = sw128_desc(smem_u32(aslot + as * kABytes));
+#pragma unroll 4
+            for (int ks = 0; ks < ks_n; ++ks) {
+              const uint64_t o = static_cast<uint64_t>(2 * ks);
+              mma_f16(g_tmem, dh + o, ad + o, idesc, 1u);
+              mma_f16(p_tmem, xh + o, ad + o, idesc, 1u);
+            }
+            mma_commit(&tail->a_empty[as]);
+            ++a_it;
+            mma_commit(&tail->w_empty[ws]);
+            ++w_it;
+          }
+          mma_commit(&tail->t_full[b]);
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: per segment, the partial chord of its rows; the CTA that
+    // completes a strip also draws theta and does the walker-side work ----------
+    const int tid = static_cast<int>(threadIdx.x) - 64;
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;
+    const int wl = q * 32 + lane;
+    TailItem none;
+    none.valid = 0;
+    int gt = 0;
+    for (int sg = sb; sg < se; ++sg) {
+      const SkSeg seg = p.segs[sg];
+      const int strip = seg.strip;
+      // Iteration s+1's directions for this segment's share of the strip's
+      // walkers, into the other pair (while the segment's first tile loads).
+      if (p.wt.draw) {
+        const int share = (kWalkers + seg.nseg - 1) / seg.nseg;
+        const int wb = seg.slot * share;
+        walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
+                                         wb, max(0, min(share, kWalkers - wb)), tid);
+      }
+      const int k = strip * kWalkers + wl;
+      const float ws = p.wscale[k];
+      float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+      for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
+        const int b = gt & 1;
+        mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, p.err, true);
+        tc_fence_after();
+        const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+        const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);
+        float g0[16], g1[16], p0[16], p1[16];
+        tmem_ld16(gcol, g0);
+        tmem_ld16(gcol + 16, g1);
+        tmem_ld16(gcol + 128, p0);
+        tmem_ld16(gcol + 144, p1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_sk(&tail->t_empty[b]);
+        const float4* br4 = reinterpret_cast<const float4*>(p.bS + nt * kRowsTile + cg * 32);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float br[16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 v = __ldg(br4 + 4 * h + i);
+            br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float gg = h == 0 ? g0[c] : g1[c];
+            const float pp = h == 0 ? p0[c] : p1[c];
+            const float sv = fmaf(-pp, ws, br[c]);
+            const float ss = fmaxf(sv, 0.0f);
+            chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
+            // s/g improves the bound on its side iff s < bound * g (g > 0: upper
+            // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
+            const float bnd = gg > 0.0f ? hi : lo;
+            if (ss < bnd * gg) {
+              const float r = __fdividef(ss, gg);
+              if (gg > 0.0f) hi = r; else lo = r;
+            }
+          }
+        }
+      }
+      if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+      tail->part_lo[cg][wl] = lo;
+      tail->part_hi[cg][wl] = hi;
+      named_bar<kEpiWarps * 32>();
+      float L = -INFINITY, H = INFINITY;
+      if (cg == 0) {
+        L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
+        H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
+      }
+      if (seg.nseg > 1) {
+        // Publish this segment's partial chords, then count the strip's
+        // segments; the last one to arrive finishes the strip.
+        float* mine = p.partials + (static_cast<size_t>(strip) * p.max_nseg + seg.slot) * 2 * kWalkers;
+        if (cg == 0) {
+          mine[wl] = L;
+          mine[kWalkers + wl] = H;
+          __threadfence();
+        }
+        named_bar<kEpiWarps * 32>();
+        if (tid == 0) {
+          const int before = atomicAdd(&p.arrivals[strip], 1);
+          const int last = before == seg.nseg - 1;
+          if (last) p.arrivals[strip] = 0;  // every segment of the strip has counted
+          tail->last = last;
+        }
+        named_bar<kEpiWarps * 32>();
+        if (!tail->last) continue;
+        __threadfence();
+        if (cg == 0) {
+          L = -INFINITY;
+          H = INFINITY;
+          for (int g = 0; g < seg.nseg; ++g) {
+            const float* part = p.partials + (static_cast<size_t>(strip) * p.max_nseg + g) * 2 * kWalkers;
+            L = fmaxf(L, __ldcg(part + wl));
+            H = fminf(H, __ldcg(part + kWalkers + wl));
+          }
+        }
+      }
+      // theta for the strip's walkers (Section 4.5), then the moves.
+      if (cg == 0) {
+        float t = 0.0f;
+        if (k < p.z) {
+          int flag = 0;
+          if (isinf(L) || isinf(H)) {
+            flag = MHAR_ST_UNBOUNDED;
+          } else if (L > H) {
+            flag = MHAR_ST_STALL;
+          } else {
+            const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
+                                      kStreamChord);
+            const double u = open_unit_f64(w.x);
+            t = static_cast<float>(static_cast<double>(L) +
+                                   u * (static_cast<double>(H) - static_cast<double>(L)));
+          }
+          p.lmin[k] = L;
+          p.lmax[k] = H;
+          p.theta[k] = t;
+          if (flag) {
+            atomicOr(p.status, flag);
+            atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+          }
+        }
+        tail->theta_s[wl] = t;
+      }
+      named_bar<kEpiWarps * 32>();
+      walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, 0, kWalkers, tail->theta_s, tail->red,
+                                  tid, none);
+      named_bar<kEpiWarps * 32>();
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+// ---- host side -------------------------------------------------------------------
+struct SkPlan {
+  SkSeg* segs = nullptr;
+  int* seg_begin = nullptr;
+  float* partials = nullptr;
+  int* arrivals = nullptr;
+  int grid = 0;
+  int max_nseg = 1;
+};
+
+int sk_prepare(mhar_ctx* c) {
+  const int strips = tc_plan_strips(c);
+  const int m_tiles = tc_plan_m_tiles(c);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const long long T = static_cast<long long>(strips) * m_tiles;
+  const int G = static_cast<int>(std::min<long long>(sms, T));
+  std::vector<SkSeg> segs;
+  std::vector<int> begin(G + 1, 0);
+  std::vector<int> nseg(strips, 0);
+  for (int b = 0; b < G; ++b) {
+    begin[b] = static_cast<int>(segs.size());
+    long long u0 = b * T / G;
+    const long long u1 = (b + 1) * T / G;
+    while (u0 < u1) {
+      SkSeg s;
+      s.strip = static_cast<int>(u0 / m_tiles);
+      s.t0 = static_cast<int>(u0 % m_tiles);
+      s.t1 = static_cast<int>(std::min<long long>(m_tiles, s.t0 + (u1 - u0)));
+      s.slot = nseg[s.strip]++;
+      s.nseg = 0;
+      segs.push_back(s);
+      u0 += s.t1 - s.t0;
+    }
+  }
+  begin[G] = static_cast<int>(segs.size());
+  int max_nseg = 1;
+  for (SkSeg& s : segs) {
+    s.nseg = nseg[s.strip];
+    max_nseg = std::max(max_nseg, s.nseg);
+  }
+  SkPlan* plan = new SkPlan();
+  plan->grid = G;
+  plan->max_nseg = max_nseg;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&plan->segs), sizeof(SkSeg) * segs.size());
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->seg_begin), sizeof(int) * begin.size());
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&plan->partials),
+                   sizeof(float) * static_cast<size_t>(strips) * max_nseg * 2 * kWalkers);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->arrivals), sizeof(int) * strips);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->segs, segs.data(), sizeof(SkSeg) * segs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->seg_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(plan->arrivals, 0, sizeof(int) * strips);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(recompute_sk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemSk));
+  c->sk = plan;
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "stream-K schedule: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    return MHAR_E_CUDA;
+  }
+  return MHAR_OK;
+}
+
+void sk_destroy(mhar_ctx* c) {
+  SkPlan* plan = static_cast<SkPlan*>(c->sk);
+  if (!plan) return;
+  void* ptrs[] = {plan->segs, plan->seg_begin, plan->partials, plan->arrivals};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete plan;
+  c->sk = nullptr;
+}
+
+cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
+  const TcPlan* tp = static_cast<const TcPlan*>(c->tc);
+  const SkPlan* plan = static_cast<const SkPlan*>(c->sk);
+  SkParams p;
+  p.bS = c->d.bS;
+  p.wscale = c->d.wscale;
+  p.lmin = c->d.lmin;
+  p.lmax = c->d.lmax;
+  p.theta = c->d.theta;
+  p.status = c->d.status;
+  p.counters = c->d.counters;
+  p.err = c->d.status + 1;
+  p.step_ptr = c->d.step;
+  p.seed = c->opts.seed;
+  p.walker0 = c->opts.walker0;
+  p.z = c->z;
+  p.kdim = c->kdim;
+  p.k_chunks = c->k_pad / kTcKChunk;
+  p.segs = plan->segs;
+  p.seg_begin = plan->seg_begin;
+  p.partials = plan->partials;
+  p.arrivals = plan->arrivals;
+  p.max_nseg = plan->max_nseg;
+  p.wt = make_walker_tail(c, 0);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan->grid, 1, 1);
+  cfg.blockDim = dim3(kThreadsSk, 1, 1);
+  cfg.dynamicSmemBytes = kSmemSk;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, recompute_sk_kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2,
+                            tp->dl2, tp->xh, tp->xl, p, j);
+}
+
+}  // namespace mhar

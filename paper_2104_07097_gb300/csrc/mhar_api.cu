@@ -168,7 +168,10 @@ cudaError_t enqueue_directions(mhar_ctx* c, int j) {
 // The kernels of one iteration after the direction draw (Sections 4.4-4.5).
 cudaError_t enqueue_chord(mhar_ctx* c, int j) {
   if (stored(c)) return mhar::launch_chord_tc(c, j);
-  if (recompute(c)) return c->use_ts ? mhar::launch_recompute_ts(c, j) : mhar::launch_recompute_tc(c, j);
+  if (recompute(c)) {
+    if (c->use_ts) return mhar::launch_recompute_ts(c, j);
+    return c->use_sk ? mhar::launch_recompute_sk(c, j) : mhar::launch_recompute_tc(c, j);
+  }
   cudaError_t e = mhar::launch_chord_simt(c);
   return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
 }
@@ -371,6 +374,7 @@ void mhar_destroy(mhar_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->g_chunk) cudaGraphExecDestroy(c->g_chunk);
   if (c->g_one) cudaGraphExecDestroy(c->g_one);
+  if (c->sk) mhar::sk_destroy(c);
   if (c->tc) mhar::tc_plan_destroy(c);
   free_all(c);
   if (c->stream && c->stream != static_cast<cudaStream_t>(c->opts.stream))
@@ -534,7 +538,15 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     if (recompute(c)) {
       c->operands_fresh = false;
       c->use_ts = mhar::ts_eligible(c) && c->opts.smem_operands == 0;
-      if ((rc = c->use_ts ? mhar::ts_prepare(c) : mhar::rc_prepare(c))) return rc;
+      c->use_sk = !c->use_ts &&
+                  (c->opts.schedule == 2 ||
+                   (c->opts.schedule == 0 && c->k_pad / mhar::kTcKChunk > 2 &&
+                    mhar::rc_prefers_stream_k(c)));
+      if (c->use_ts)
+        rc = mhar::ts_prepare(c);
+      else
+        rc = c->use_sk ? mhar::sk_prepare(c) : mhar::rc_prepare(c);
+      if (rc) return rc;
     }
     if (stored(c) && ((rc = reset_drift(c)) || (rc = refresh(c)))) return rc;
   }
@@ -561,7 +573,7 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
     rc = MHAR_E_UNSUPPORTED;
   } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
              c->opts.refresh_k < 0 || c->opts.graph_chunk < 0 || c->opts.emit_walkers < 0 ||
-             c->opts.emit_walkers > z) {
+             c->opts.emit_walkers > z || c->opts.schedule < 0 || c->opts.schedule > 2) {
     set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d emit_walkers=%d)",
             c->opts.precision, c->opts.refresh_k, c->opts.graph_chunk, c->opts.emit_walkers);
     rc = MHAR_E_ARG;

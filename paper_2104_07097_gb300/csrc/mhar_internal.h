@@ -97,6 +97,8 @@ struct mhar_ctx {
   int64_t launches_chunk = 0;  // kernel nodes in g_chunk
   int64_t launches_one = 0;    // kernel nodes in g_one
   bool use_ts = false;         // recompute mode: TMEM-operand kernel (n <= 128)
+  bool use_sk = false;         // recompute mode: stream-K schedule (kernels_sk.cu)
+  void* sk = nullptr;          // its segment table
   int pc_rank = -1;            // -1: isotropic directions; else rank of U (0..32)
   // Recompute mode: the chord kernel itself moves the walkers, re-splits the
   // points and (with no projection / preconditioner) draws the next
@@ -171,6 +173,14 @@ int batch_table_build(mhar_ctx* const* ctx, int count, int C, void** table, int*
 cudaError_t launch_recompute_batch(const void* table, int units, int C, int j,
                                    cudaStream_t stream);
 cudaError_t launch_advance_many(uint64_t* const* steps, int count, int by, cudaStream_t stream);
+
+// Whether the stream-K schedule beats clusters along the rows for this shape.
+bool rc_prefers_stream_k(const mhar_ctx* ctx);
+
+// ---- recompute-slack, stream-K schedule (kernels_sk.cu) ------------------------
+int sk_prepare(mhar_ctx* ctx);
+void sk_destroy(mhar_ctx* ctx);
+cudaError_t launch_recompute_sk(mhar_ctx* ctx, int j);
 
 // ---- recompute-slack, walker operands in tensor memory (kernels_ts.cu) -------
 bool ts_eligible(const mhar_ctx* ctx);              // n <= 128

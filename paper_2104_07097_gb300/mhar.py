@@ -49,7 +49,7 @@ class MharOpts(ctypes.Structure):
                 ("walker0", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("graph_chunk", ctypes.c_int32), ("refresh_fp64", ctypes.c_int32),
                 ("smem_operands", ctypes.c_int32), ("emit_walkers", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class MharStats(ctypes.Structure):
@@ -299,7 +299,7 @@ class Sampler:
     def __init__(self, A, b, x0, z: int, AE=None, bE=None, precision: str | int = "fp64",
                  seed: int = 0, refresh_k: int = 64, walker0: int = 0, stream=None,
                  graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False,
-                 smem_operands: bool = False, emit_walkers: int = 0):
+                 smem_operands: bool = False, emit_walkers: int = 0, schedule: int = 0):
         o = mhar_default_opts()
         o.seed = int(seed)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -310,6 +310,7 @@ class Sampler:
         o.refresh_fp64 = 1 if refresh_fp64 else 0
         o.smem_operands = 1 if smem_operands else 0
         o.emit_walkers = int(emit_walkers)
+        o.schedule = int(schedule)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         A = _f64(A)
