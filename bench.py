@@ -41,7 +41,14 @@ sys.path.insert(0, ROOT)
 
 from paper_2104_07097_gb300 import workloads as wl  # noqa: E402
 
-WORKLOAD = dict(name="rand100x2000", n=100, m=2000, seed=2, z=4096, iterations=2000)
+WORKLOADS = {
+    "rand100x2000": dict(name="rand100x2000", kind="random", n=100, m=2000, seed=2, z=4096,
+                         iterations=2000),
+    # The ill-conditioned body of the ESS leg, as a throughput workload.
+    "illcond500x10000": dict(name="illcond500x10000", kind="illcond", n=500, m=10000, seed=5,
+                             z=16384, iterations=200),
+}
+WORKLOAD = dict(WORKLOADS["rand100x2000"])
 METRIC = "walker-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
@@ -53,6 +60,8 @@ REF_SAMPLE = dict(walkers=64, iterations=20)
 
 
 def polytope():
+    if WORKLOAD["kind"] == "illcond":
+        return wl.ill_conditioned(WORKLOAD["n"], WORKLOAD["m"], seed=WORKLOAD["seed"])
     return wl.random_polytope(WORKLOAD["n"], WORKLOAD["m"], seed=WORKLOAD["seed"])
 
 
@@ -206,7 +215,7 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
             "max_violation": worst}
 
 
-def ess_leg(stream, torch, mhar) -> dict:
+def ess_leg(stream, torch, mhar, peaks) -> dict:
     """min-ESS/s of learned-preconditioned vs plain MHAR on the ill-conditioned body."""
     from paper_2104_07097_gb300 import diagnostics
     E = ESS_WORKLOAD
@@ -214,6 +223,7 @@ def ess_leg(stream, torch, mhar) -> dict:
     z, T, W, every = E["z"], E["iterations"], E["trace_walkers"], E["trace_every"]
     out = torch.empty((T // every, W, p.n), dtype=torch.float64, device="cuda")
     arms = {}
+    kernel_roofline = None
     for name, prec, learned in (("learned_mixed_rs", "mixed_rs", True),
                                 ("plain_mixed_rs", "mixed_rs", False),
                                 ("plain_fp32", "fp32", False)):
@@ -234,6 +244,16 @@ def ess_leg(stream, torch, mhar) -> dict:
             torch.cuda.synchronize()
             secs = a.elapsed_time(b) / 1e3
             st = smp.check()
+            if name == "plain_mixed_rs":
+                kms = smp.time_kernels(16)
+                flops = 12.0 * p.m * p.n * z
+                kernel_roofline = {
+                    "bound": "tensor", "kernel": smp.kernel_name(),
+                    "ms_per_iteration": kms[1],
+                    "achieved": flops / (kms[1] * 1e-3) / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "frac": flops / (kms[1] * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
+                    "algorithmic": "12 m n tensor flops per walker-step"}
         trace = out.cpu().numpy()
         ess = diagnostics.ess_per_coordinate(trace) * (z / W)
         arms[name] = {"min_ess": float(ess.min()), "median_ess": float(np.median(ess)),
@@ -248,6 +268,7 @@ def ess_leg(stream, torch, mhar) -> dict:
                        f"snapshots, {E['power_iters']} power iterations each), then frozen; "
                        f"warm-up and fits are inside the timed region",
             "arms": arms,
+            "roofline": kernel_roofline,
             "min_ess_per_s_learned_vs_plain_fp32":
                 arms["learned_mixed_rs"]["min_ess_per_s"] / arms["plain_fp32"]["min_ess_per_s"]}
 
@@ -262,7 +283,11 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ess", action="store_true", help="skip the min-ESS/s comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-polytope leg")
+    ap.add_argument("--workload", default="rand100x2000", choices=sorted(WORKLOADS),
+                    help="the timed workload (default: the headline random polytope)")
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.impl == "reference":
         run_reference(args)
         return
@@ -332,8 +357,7 @@ def main() -> None:
         roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
                     "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
                     "traffic": None,
-                    "kernel": ("recompute_ts_kernel" if n <= 128 else "recompute_tc_kernel")
-                              if args.precision == "mixed_rs" else "walker_tc_kernel",
+                    "kernel": s.kernel_name(),
                     "algorithmic": f"{2 * nprod} m n tensor flops per walker-step ({nprod} FP16 products)",
                     "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}
     else:
@@ -396,7 +420,7 @@ def main() -> None:
         if world == 1 and not args.no_batch and args.precision == "mixed_rs":
             line["batched"] = batch_leg(stream, torch, mhar, peaks)
         if world == 1 and not args.no_ess:
-            line["ess"] = ess_leg(stream, torch, mhar)
+            line["ess"] = ess_leg(stream, torch, mhar, peaks)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)

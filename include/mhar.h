@@ -316,6 +316,10 @@ const char* mhar_batch_last_error(const mhar_batch* batch);
 /* Frees the batch and every problem's device memory; NULL is ignored. */
 void mhar_batch_destroy(mhar_batch* batch);
 
+/* Name of the kernel that runs the chord of one iteration on this context
+ * (e.g. "recompute_ts_kernel"); never NULL. */
+const char* mhar_kernel_name(const mhar_ctx* ctx);
+
 /* Human-readable description of the last error on ctx (never NULL); with
  * ctx == NULL, the last mhar_chord_noalloc failure on this host thread. */
 const char* mhar_last_error(const mhar_ctx* ctx);

@@ -364,6 +364,13 @@ const char* mhar_strerror(int code) {
   }
 }
 
+const char* mhar_kernel_name(const mhar_ctx* c) {
+  if (!c) return "none";
+  if (recompute(c)) return c->use_ts ? "recompute_ts_kernel" : (c->use_sk ? "recompute_sk_kernel" : "recompute_tc_kernel");
+  if (stored(c)) return "walker_tc_kernel";
+  return "chord_simt_kernel";
+}
+
 const char* mhar_last_error(const mhar_ctx* c) {
   if (!c) return mhar::noalloc_last_error();
   return c->err[0] ? c->err : "no error";

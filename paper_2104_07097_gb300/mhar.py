@@ -40,7 +40,8 @@ EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mh
            "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
            "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_run",
            "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
-           "mhar_batch_destroy", "mhar_last_error", "mhar_strerror", "mhar_destroy")
+           "mhar_batch_destroy", "mhar_kernel_name", "mhar_last_error", "mhar_strerror",
+           "mhar_destroy")
 
 
 class MharOpts(ctypes.Structure):
@@ -134,6 +135,8 @@ def load(path: str | None = None):
     lib.mhar_batch_last_error.restype = ctypes.c_char_p
     lib.mhar_batch_destroy.argtypes = [vp]
     lib.mhar_batch_destroy.restype = None
+    lib.mhar_kernel_name.argtypes = [vp]
+    lib.mhar_kernel_name.restype = ctypes.c_char_p
     lib.mhar_last_error.argtypes = [vp]
     lib.mhar_last_error.restype = ctypes.c_char_p
     lib.mhar_strerror.argtypes = [ctypes.c_int]
@@ -372,6 +375,10 @@ class Sampler:
                            power_iters: int = 4) -> None:
         """Learns (delta, U) from `warmup` iterations of the chain and freezes it."""
         mhar_fit_preconditioner(self._ctx, warmup, snapshots, min(rank, self.n), power_iters)
+
+    def kernel_name(self) -> str:
+        """The kernel that runs each iteration's chord on this sampler."""
+        return load().mhar_kernel_name(self._ctx).decode()
 
     def time_kernels(self, iters: int):
         """Average device ms of (directions, chord+update, refresh)."""
