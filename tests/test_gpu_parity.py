@@ -131,6 +131,20 @@ def test_graph_and_eager_identical():
     np.testing.assert_array_equal(outs[0], outs[2])
 
 
+@pytest.mark.parametrize("n", [30, 100])
+def test_recompute_launch_shapes_identical(n):
+    # One iteration per launch (eager, or graphs of 1) and several iterations
+    # per launch (graphs of 7 and 16, eager runs of up to 64 per launch)
+    # must give the same walk bit for bit.
+    p = wl.random_polytope(n, 12 * n, seed=n)
+    outs = []
+    for chunk in (0, 1, 7, 16):
+        with mhar.Sampler(p.A, p.b, p.x0, 300, precision="mixed_rs", seed=4, graph_chunk=chunk) as s:
+            outs.append(s.run(70, thin=35))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0], o)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_rs"])
 def test_continuation_and_thinning(prec):
     p = wl.random_polytope(30, 250, seed=4)
