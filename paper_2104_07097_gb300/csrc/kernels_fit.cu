@@ -61,8 +61,12 @@ cov_accumulate_kernel(int mode, int z, int n, int n_ld, int tiles, const double*
     ++ti;
   }
   const int tj = ti + t;
-  __shared__ double xa[kCovStage][kCovTile];
-  __shared__ double xb[kCovStage][kCovTile];
+  // Centred values (x - shift, formed in FP64) are staged as FP32; the
+  // products of one stage of kCovStage walkers are summed in FP32 and each
+  // stage's sum is added to an FP64 total, so FP64 work is 1 / kCovStage of
+  // the products (FP64 runs at a small fraction of the FP32 rate on GB300).
+  __shared__ float xa[kCovStage][kCovTile];
+  __shared__ float xb[kCovStage][kCovTile];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4];
 #pragma unroll
@@ -82,13 +86,18 @@ cov_accumulate_kernel(int mode, int z, int n, int n_ld, int tiles, const double*
         if (ia < n) va = point(mode, X64, Xhi, Xlo, row + ia) - shift[ia];
         if (ib < n) vb = point(mode, X64, Xhi, Xlo, row + ib) - shift[ib];
       }
-      xa[w][q] = va;
-      xb[w][q] = vb;
+      xa[w][q] = static_cast<float>(va);
+      xb[w][q] = static_cast<float>(vb);
     }
     __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[r][q] = 0.0f;
 #pragma unroll 4
     for (int w = 0; w < kCovStage; ++w) {
-      double a[4], bb[4];
+      float a[4], bb[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = xa[w][ty * 4 + r];
 #pragma unroll
@@ -96,9 +105,13 @@ cov_accumulate_kernel(int mode, int z, int n, int n_ld, int tiles, const double*
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], bb[q], acc[r][q]);
-      if (ti == tj && threadIdx.x < kCovTile) col_sum += xa[w][threadIdx.x];
+        for (int q = 0; q < 4; ++q) part[r][q] = fmaf(a[r], bb[q], part[r][q]);
+      if (ti == tj && threadIdx.x < kCovTile) col_sum += static_cast<double>(xa[w][threadIdx.x]);
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] += static_cast<double>(part[r][q]);
     __syncthreads();
   }
 #pragma unroll

@@ -80,9 +80,11 @@ struct TsTail {
   float recv_hi[kMaxCluster][kWalkers];
   float theta_s[kWalkers];
   unsigned int red[kWalkers];
+  float gs[kWalkers * kMaxPcRank];    // low-rank normals of a preconditioned draw
 };
 
 constexpr size_t kSmemTs = 1024 + static_cast<size_t>(kSlots) * kSlotBytes + sizeof(TsTail);
+static_assert(kSmemTs <= 232448, "recompute_ts_kernel exceeds the shared memory of a CTA");
 
 __device__ __forceinline__ void st_dsmem(float* local, uint32_t rank, float v) {
   uint32_t remote;
@@ -261,7 +263,8 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     // directions into the other pair (walker_tail.cuh, step 0).
     if (p.wt.draw)
       walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
-                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
+                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64,
+                                       tail->gs);
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;              // 32-column group of each 128-column tile
@@ -449,7 +452,7 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   p.k_pad = c->k_pad;
   p.tiles_per_cta = s.tiles_per_cta;
   p.m_tiles = s.m_tiles;
-  p.wt = make_walker_tail(c, 1);
+  p.wt = make_walker_tail(c, 1, true);
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(s.C, plan->strips, 1);

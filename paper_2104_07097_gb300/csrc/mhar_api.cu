@@ -138,9 +138,10 @@ __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const 
 }
 
 // Recompute mode with nothing between the draw and the chord: the chord
-// kernel draws the next directions itself.
+// kernel draws the next directions itself (preconditioned ones too in the
+// tensor-memory-operand kernel).
 bool tail_draws(const mhar_ctx* c) {
-  return recompute(c) && c->mE == 0 && c->pc_rank < 0;
+  return recompute(c) && c->mE == 0 && (c->pc_rank < 0 || c->use_ts);
 }
 
 int kernels_per_iteration(const mhar_ctx* c) {
@@ -185,6 +186,10 @@ int ensure_operands(mhar_ctx* c) {
   if (!recompute(c) || c->operands_fresh) return MHAR_OK;
   MHAR_CUDA(mhar::launch_prep_walkers(c, 0, tail_draws(c) ? 6 : 2), "operand preparation");
   ++c->launches;
+  if (tail_draws(c) && c->pc_rank >= 0) {  // preconditioned first directions
+    MHAR_CUDA(mhar::launch_precondition(c, 0, 1), "operand preparation");
+    ++c->launches;
+  }
   c->operands_fresh = true;
   return MHAR_OK;
 }

@@ -42,10 +42,16 @@ struct WalkerTail {
   const float* corr;     // z x mE or null
   int mE, n, n_ld, k_pad, z_ld, inter, draw;
   int unit_sigma;        // 1: every sigma_i is 1 (no preconditioner), skip them
+  // Preconditioned draw d = delta .* h + U g (pc_rank >= 0; only kernels that
+  // pass shared scratch for g to walker_draw_next draw it themselves).
+  const float* pc_delta; // n_ld
+  const float* pc_U;     // n_ld x 32, zero beyond the rank
+  int pc_rank;
 };
 
-// The tail's arguments for a context (`inter`: interleaved operand layout).
-inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter) {
+// The tail's arguments for a context (`inter`: interleaved operand layout;
+// `pc_draw`: the kernel can draw preconditioned directions itself).
+inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter, bool pc_draw = false) {
   WalkerTail t;
   t.Xhi = c->d.Xhi;
   t.Xlo = c->d.Xlo;
@@ -65,8 +71,11 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter) {
   t.k_pad = c->k_pad;
   t.z_ld = (c->z + tc::kWalkers - 1) / tc::kWalkers * tc::kWalkers;
   t.inter = inter;
-  t.draw = (c->mE == 0 && c->pc_rank < 0) ? 1 : 0;
+  t.draw = (c->mE == 0 && (c->pc_rank < 0 || pc_draw)) ? 1 : 0;
   t.unit_sigma = c->pc_rank < 0 ? 1 : 0;
+  t.pc_delta = c->d.pc_delta32;
+  t.pc_U = c->d.pc_U32;
+  t.pc_rank = c->pc_rank;
   return t;
 }
 
@@ -141,16 +150,39 @@ __device__ __forceinline__ void walker_tail_prefetch(const WalkerTail& t, int cu
   r.valid = 1;
 }
 
-// (0): run by kThreads threads (tid = 0..kThreads-1); `next_step` = s + 1.
+// (0): run by kThreads threads (tid = 0..kThreads-1, sharing named barrier 1
+// when preconditioned); `next_step` = s + 1.  With a preconditioner the
+// direction is d = delta .* h + U g, g the walker's rank-r normals (Philox
+// stream 2), kept in `gs` (w_count x 32 floats of shared memory); the
+// arithmetic is that of precondition_kernel (FP32, terms in column order,
+// then d / sigma split into the FP16 pair).
 template <int kThreads>
 __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, uint64_t next_step,
                                  uint32_t walker0, int strip, int z, int w_begin, int w_count,
-                                 int tid) {
+                                 int tid, float* gs = nullptr) {
   using namespace tail_detail;
   const int chunks = (t.n + 7) >> 3;
   const int items = w_count * chunks;
   __half* Dh = t.Dh[cur ^ 1];
   __half* Dl = t.Dl[cur ^ 1];
+  const bool pre = t.pc_rank >= 0 && gs != nullptr;
+  if (pre) {
+    const int quads = (t.pc_rank + 3) >> 2;
+    for (int idx = tid; idx < w_count * (kMaxPcRank / 4); idx += kThreads) {
+      const int w = idx / (kMaxPcRank / 4), q = idx - w * (kMaxPcRank / 4);
+      const int k = strip * tc::kWalkers + w_begin + w;
+      float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (q < quads && k < z) {
+        const U4 r = philox_block(seed, next_step, walker0 + static_cast<uint32_t>(k),
+                                  static_cast<uint32_t>(q), kStreamLowRank);
+        box_muller_f32(r.x, r.y, v[0], v[1]);
+        box_muller_f32(r.z, r.w, v[2], v[3]);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) gs[w * kMaxPcRank + 4 * q + e] = 4 * q + e < t.pc_rank ? v[e] : 0.0f;
+    }
+    tc::named_bar<kThreads>();
+  }
   for (int it = tid; it < items; it += kThreads) {
     const int c = it / w_count, wo = it - c * w_count;
     const int k = strip * tc::kWalkers + w_begin + wo;
@@ -172,6 +204,19 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if (i0 + e >= t.n) v[e] = 0.0f;
+    if (pre) {
+      const float* g = gs + wo * kMaxPcRank;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = i0 + e;
+        if (i >= t.n) continue;
+        const float* u = t.pc_U + static_cast<size_t>(i) * kMaxPcRank;
+        float acc = t.pc_delta[i] * v[e];
+#pragma unroll 8
+        for (int c2 = 0; c2 < kMaxPcRank; ++c2) acc = fmaf(u[c2], g[c2], acc);
+        v[e] = acc * (1.0f / t.sigma[i]);
+      }
+    }
     split_store8(v, Dh + o, Dl + o);
   }
 }
