@@ -14,7 +14,9 @@ warm-up iterations in four fit rounds, rank-32 + diagonal fit on the device,
 then 5000 frozen iterations, tensor-core recompute mode) against plain isotropic runs (FP32 on
 CUDA cores, and the same tensor-core mode), each with 500 + 5000 iterations,
 and reports min-ESS (over coordinates, from a trace of 64 walkers every 5th
-iteration, scaled to all z walkers) per second of device time.
+iteration, scaled to all z walkers) per second of device time.  "ess_moderate"
+repeats it on a smaller body (n = 40, m = 400, axes from 1e-2 to 1, z = 4096)
+whose long axes the warm-up reaches.
 
 A third leg ("batched") times 256 random polytopes of different sizes (n
 uniform in 20..400, m uniform in 2n..20n, z = 512 each, 1000 iterations)
@@ -53,7 +55,12 @@ METRIC = "walker-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
 BATCH_WORKLOAD = dict(name="batch256", count=256, seed=4, z=512, iterations=1000, tune_iters=8)
-ESS_WORKLOAD = dict(name="illcond500x10000", n=500, m=10000, seed=5, z=16384, warmup=500,
+ESS_WORKLOAD = dict(name="illcond500x10000", n=500, m=10000, seed=5, smin=1e-3, z=16384,
+                    warmup=500, iterations=5000, trace_walkers=64, trace_every=5, rank=32,
+                    fit_rounds=4, snapshots=5, power_iters=4)
+# A smaller ill-conditioned body whose long axes the 500 warm-up iterations do
+# reach, so that the learned directions' own effect on mixing shows.
+ESS_MODERATE = dict(name="illcond40x400", n=40, m=400, seed=5, smin=1e-2, z=4096, warmup=500,
                     iterations=5000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
                     snapshots=5, power_iters=4)
 REF_SAMPLE = dict(walkers=64, iterations=20)
@@ -215,11 +222,10 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
             "max_violation": worst}
 
 
-def ess_leg(stream, torch, mhar, peaks) -> dict:
-    """min-ESS/s of learned-preconditioned vs plain MHAR on the ill-conditioned body."""
+def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
+    """min-ESS/s of learned-preconditioned vs plain MHAR on an ill-conditioned body."""
     from paper_2104_07097_gb300 import diagnostics
-    E = ESS_WORKLOAD
-    p = wl.ill_conditioned(E["n"], E["m"], seed=E["seed"])
+    p = wl.ill_conditioned(E["n"], E["m"], seed=E["seed"], smin=E["smin"])
     z, T, W, every = E["z"], E["iterations"], E["trace_walkers"], E["trace_every"]
     out = torch.empty((T // every, W, p.n), dtype=torch.float64, device="cuda")
     arms = {}
@@ -260,7 +266,8 @@ def ess_leg(stream, torch, mhar, peaks) -> dict:
                       "seconds": secs, "min_ess_per_s": float(ess.min()) / secs,
                       "walker_steps_per_s": z * (E["warmup"] + T) / secs,
                       "max_violation": st.max_violation}
-    return {"workload": f"{E['name']} z={z}: {E['warmup']} warm-up + {T} iterations",
+    return {"workload": f"{E['name']} (axes scaled by s, log s ~ U[ln {E['smin']:g}, 0]) z={z}: "
+                        f"{E['warmup']} warm-up + {T} iterations",
             "trace": f"{W} walkers, every {every}th iteration; ESS scaled by z/{W}; Geyer initial "
                      f"monotone sequence",
             "learned": f"rank {E['rank']} + diagonal, fitted on the device in {E['fit_rounds']} rounds "
@@ -421,6 +428,7 @@ def main() -> None:
             line["batched"] = batch_leg(stream, torch, mhar, peaks)
         if world == 1 and not args.no_ess:
             line["ess"] = ess_leg(stream, torch, mhar, peaks)
+            line["ess_moderate"] = ess_leg(stream, torch, mhar, peaks, ESS_MODERATE)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)
