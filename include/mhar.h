@@ -236,9 +236,9 @@ int mhar_chord_noalloc(const double* A, const double* b, int m, int n,
 /* Sets the preconditioner (delta != NULL) or removes it (delta == NULL:
  * isotropic directions again).  delta: n values, finite, >= 0; U: n x rank,
  * row-major, NULL when rank == 0; 0 <= rank <= 32.  The library copies both.
- * Moves still pending from the last iteration are applied first; the next
- * mhar_run re-captures its graphs.  MHAR_E_ARG on a bad rank or pointer,
- * MHAR_E_NONFINITE on a non-finite entry. */
+ * The walkers keep their points; the next iteration's directions are redrawn
+ * with the new law, and the next mhar_run re-captures its graphs.
+ * MHAR_E_ARG on a bad rank or pointer, MHAR_E_NONFINITE on a non-finite entry. */
 int mhar_set_preconditioner(mhar_ctx* ctx, const double* delta, const double* U, int32_t rank);
 
 /* Current preconditioner: *rank = -1 when none is set (delta and U are then

@@ -447,6 +447,8 @@ bool rc_prefers_stream_k(const mhar_ctx* c) {
   // Row tiles on the busiest SM: clusters run in waves of `sms` CTAs; the
   // stream-K cut gives every SM an equal share plus about one tile of
   // per-segment overhead.
+  // A body too tall for clusters of at most 8 CTAs goes to stream-K.
+  if (s.C > kMaxCluster || s.tiles_per_cta > kMaxTiles) return true;
   const long long ctas = static_cast<long long>(plan->strips) * s.C;
   const long long waves = (ctas + sms - 1) / sms;
   const long long cluster_cost = waves * s.tiles_per_cta;

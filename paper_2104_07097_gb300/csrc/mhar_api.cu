@@ -552,8 +552,8 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       c->use_ts = mhar::ts_eligible(c) && c->opts.smem_operands == 0;
       c->use_sk = !c->use_ts &&
                   (c->opts.schedule == 2 ||
-                   (c->opts.schedule == 0 && c->k_pad / mhar::kTcKChunk > 2 &&
-                    mhar::rc_prefers_stream_k(c)));
+                   (c->opts.schedule == 0 && mhar::rc_prefers_stream_k(c) &&
+                    (c->k_pad / mhar::kTcKChunk > 2 || c->m_pad > 32768)));
       if (c->use_ts)
         rc = mhar::ts_prepare(c);
       else

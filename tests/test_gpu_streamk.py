@@ -78,3 +78,19 @@ def test_schedule_option_rejected_out_of_range():
     with pytest.raises(mhar.MharError) as e:
         mhar.Sampler(p.A, p.b, p.x0, 128, precision="mixed_rs", schedule=3)
     assert e.value.code == mhar.E_ARG
+
+
+def test_tall_body_goes_to_stream_k():
+    # m = 40000 rows exceeds clusters of 8 CTAs x 32 row tiles; the automatic
+    # schedule takes stream-K, which has no such limit.
+    p = wl.random_polytope(20, 40000, seed=3, check_bounded="auto")
+    z, steps = 128, 5
+    with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=6, smem_operands=True) as s:
+        assert s.kernel_name() == "recompute_sk_kernel"
+        got = s.run(steps, thin=1)
+    ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, thin=1, seed=6)
+    err = np.abs(got - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
+    assert err <= 1e-4, err
+    with pytest.raises(mhar.MharError) as e:
+        mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", smem_operands=True, schedule=1)
+    assert e.value.code == mhar.E_UNSUPPORTED
