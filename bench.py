@@ -222,6 +222,41 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
             "max_violation": worst}
 
 
+def configs_leg(stream, torch, mhar, peaks) -> dict:
+    """Throughput on the remaining configurations: the hypercube in FP64 and the
+    simplex with cuts (one equality) in the recompute tensor-core mode."""
+    legs = {}
+    cases = (
+        ("cube10_fp64", wl.cube(10), 100, 1000, "fp64"),
+        ("simplex1000+4000cuts_mixed_rs", wl.simplex_cuts(1000, 4000, seed=3), 8192, 1000,
+         "mixed_rs"),
+    )
+    for name, p, z, iters, prec in cases:
+        with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=0,
+                          stream=stream) as smp:
+            smp.run(20)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            smp.run(iters)
+            b.record(stream)
+            torch.cuda.synchronize()
+            secs = a.elapsed_time(b) / 1e3
+            st = smp.check()
+            leg = {"workload": f"{name}: n={p.n}, m={p.m}, m_E={p.mE}, z={z}, {iters} iterations",
+                   "value": z * iters / secs, "unit": METRIC, "seconds": secs,
+                   "kernel": smp.kernel_name(), "max_violation": st.max_violation,
+                   "eq_residual": st.eq_residual}
+            if prec == "mixed_rs":
+                flops = 12.0 * p.m * p.n * z * iters
+                leg["roofline"] = {"bound": "tensor", "achieved": flops / secs / 1e12,
+                                   "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                                   "frac": flops / secs / 1e12 / peaks["bf16_tflops_sustained"],
+                                   "note": "whole iteration incl. direction draw and projection"}
+            legs[name] = leg
+    return legs
+
+
 def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
     """min-ESS/s of learned-preconditioned vs plain MHAR on an ill-conditioned body."""
     from paper_2104_07097_gb300 import diagnostics
@@ -370,7 +405,7 @@ def main() -> None:
     else:
         bytes_ = 2.0 * m * n * z * (8 if args.precision == "fp64" else 4)
         roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": "chord_simt_kernel"}
+                    "traffic": None, "kernel": s.kernel_name()}
 
     # End to end through the public API from pinned host buffers: create
     # (H2D of A, b, x0), run, D2H of the emitted points, destroy.
@@ -426,6 +461,7 @@ def main() -> None:
                 "plain_fp32": plain}
         if world == 1 and not args.no_batch and args.precision == "mixed_rs":
             line["batched"] = batch_leg(stream, torch, mhar, peaks)
+            line["other_configs"] = configs_leg(stream, torch, mhar, peaks)
         if world == 1 and not args.no_ess:
             line["ess"] = ess_leg(stream, torch, mhar, peaks)
             line["ess_moderate"] = ess_leg(stream, torch, mhar, peaks, ESS_MODERATE)

@@ -29,28 +29,36 @@ __device__ __forceinline__ double neg_inf() { return -__longlong_as_double(0x7ff
 __device__ __forceinline__ double pos_inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 
 // ---- Section 4.3: direction entries ----------------------------------------
-// mode 0: FP64 -> D64; mode 1: FP32 -> D32; mode 2: FP32 -> FP16 hi/lo split
-// (when there is no projection) or FP32 scratch D32 (projection follows).
+// mode 0: FP64 -> D64 (one thread per Box-Muller pair: the FP64 functions are
+// slow on this GPU, so the two pairs of a quad go to two threads); mode 1:
+// FP32 -> D32; mode 2: FP32 -> FP16 hi/lo split (when there is no
+// projection) or FP32 scratch D32 (projection follows).  One thread per quad
+// in modes 1 and 2.
 __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint64_t* step_ptr,
                                   int j, uint32_t walker0, int z, int n, int n_ld, int k_pad,
                                   double* D64, float* D32, __half* Dh, __half* Dl) {
   const int quads = (n + 3) >> 2;
+  const int per_quad = mode == 0 ? 2 : 1;
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<long long>(z) * quads) return;
-  const int k = static_cast<int>(idx / quads);
-  const int q = static_cast<int>(idx - static_cast<long long>(k) * quads);
+  if (idx >= static_cast<long long>(z) * quads * per_quad) return;
+  const long long qi = idx / per_quad;
+  const int half = static_cast<int>(idx - qi * per_quad);
+  const int k = static_cast<int>(qi / quads);
+  const int q = static_cast<int>(qi - static_cast<long long>(k) * quads);
   const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
   const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k),
                             static_cast<uint32_t>(q), kStreamDirection);
   const int i0 = 4 * q;
   if (mode == 0) {
-    double v[4];
-    box_muller_f64(open_unit_f64(w.x), open_unit_f64(w.y), v[0], v[1]);
-    box_muller_f64(open_unit_f64(w.z), open_unit_f64(w.w), v[2], v[3]);
-    double* dst = D64 + static_cast<size_t>(k) * n_ld + i0;
+    double v[2];
+    if (half == 0)
+      box_muller_f64(open_unit_f64(w.x), open_unit_f64(w.y), v[0], v[1]);
+    else
+      box_muller_f64(open_unit_f64(w.z), open_unit_f64(w.w), v[0], v[1]);
+    double* dst = D64 + static_cast<size_t>(k) * n_ld + i0 + 2 * half;
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (i0 + e < n) dst[e] = v[e];
+    for (int e = 0; e < 2; ++e)
+      if (i0 + 2 * half + e < n) dst[e] = v[e];
   } else {
     float v[4];
     box_muller_f32(w.x, w.y, v[0], v[1]);
@@ -568,6 +576,104 @@ __global__ void check_kernel(int mode, int m, int n, int n_ld, int mE, const dou
 // of 64 rows x 64 walkers, K staged through shared memory), stored as the
 // tensor-core path keeps it (divided by the row scale, blocked by 4 rows),
 // and the largest change |S_old - S_new| recorded (drift).
+// Small bodies: one warp per walker, lanes over the rows.  The tile kernel
+// above keeps (m/64)(z/64) blocks busy, which for a body like the
+// 10-dimensional cube is a couple of SMs; here every walker has its own warp,
+// so the FP64 work (slow on this GPU) spreads over many SMs.  Same formulas:
+// s = b - a.x, g = a.d, slack clamped at 0, rows with g == 0 skipped.  With
+// `move` the warp also draws theta and moves its walker (update_kernel's
+// arithmetic), so one launch does Sections 4.4 and 4.5.
+constexpr int kWarpChordThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpChordThreads)
+chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ X,
+                  const T* __restrict__ D, int m, int n, int n_ld, int z,
+                  unsigned long long* key_lo, unsigned long long* key_hi, int* status,
+                  int move, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
+                  double* lmin, double* lmax, double* theta, unsigned long long* counters,
+                  double* X64, const double* D64, float* Xhi, float* Xlo, const float* D32,
+                  int mE, const float* AE32, const float* corr) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (kWarpChordThreads / 32) + warp;
+  if (k >= z) return;
+  const T* x = X + static_cast<size_t>(k) * n_ld;
+  const T* d = D + static_cast<size_t>(k) * n_ld;
+  T lo = static_cast<T>(neg_inf()), hi = static_cast<T>(pos_inf());
+  bool bad = false;
+  for (int i = lane; i < m; i += 32) {
+    const T* a = A + static_cast<size_t>(i) * n_ld;
+    T ax = T(0), ad = T(0);
+    for (int c = 0; c < n; ++c) {
+      ax += a[c] * x[c];
+      ad += a[c] * d[c];
+    }
+    T sv = b[i] - ax;
+    if (!isfinite(sv) || !isfinite(ad)) { bad = true; continue; }
+    if (sv < T(0)) sv = T(0);
+    if (ad > T(0)) {
+      const T lam = sv / ad;
+      hi = lam < hi ? lam : hi;
+    } else if (ad < T(0)) {
+      const T lam = sv / ad;
+      lo = lam > lo ? lam : lo;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T ol = __shfl_xor_sync(0xffffffffu, lo, off);
+    const T oh = __shfl_xor_sync(0xffffffffu, hi, off);
+    lo = ol > lo ? ol : lo;
+    hi = oh < hi ? oh : hi;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, MHAR_ST_NONFINITE);
+  if (!move) {
+    if (lane == 0) {
+      key_lo[k] = f64_key(static_cast<double>(lo));
+      key_hi[k] = f64_key(static_cast<double>(hi));
+    }
+    return;
+  }
+  // Section 4.5 in the same warp (the arithmetic of update_kernel): theta on
+  // the chord, x += theta d.
+  double t = 0.0;
+  if (lane == 0) {
+    const double L = static_cast<double>(lo), H = static_cast<double>(hi);
+    if (isinf(L) || isinf(H)) {
+      atomicOr(status, MHAR_ST_UNBOUNDED);
+      atomicAdd(&counters[1], 1ull);
+    } else if (L > H) {
+      atomicOr(status, MHAR_ST_STALL);
+      atomicAdd(&counters[0], 1ull);
+    } else {
+      const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+      const U4 w = philox_block(seed, step, walker0 + static_cast<uint32_t>(k), 0u, kStreamChord);
+      const double u = open_unit_f64(w.x);
+      t = L + u * (H - L);
+      if (sizeof(T) != 8) t = static_cast<double>(static_cast<float>(t));
+    }
+    lmin[k] = L;
+    lmax[k] = H;
+    theta[k] = t;
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  const size_t row = static_cast<size_t>(k) * n_ld;
+  if constexpr (sizeof(T) == 8) {
+    for (int i = lane; i < n; i += 32) X64[row + i] += t * D64[row + i];
+  } else {
+    const float tf = static_cast<float>(t);
+    for (int i = lane; i < n; i += 32) df_axpy(Xhi[row + i], Xlo[row + i], tf, D32[row + i]);
+    if (corr != nullptr && tf != 0.0f) {
+      for (int i = lane; i < n; i += 32) {
+        float dlt = 0.0f;
+        for (int e = 0; e < mE; ++e)
+          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
+        Xlo[row + i] = fmaf(-tf, dlt, Xlo[row + i]);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 refresh_simt_kernel(int m, int n_ld, int z, int z_ld, const double* __restrict__ A,
                     const double* __restrict__ b, const float* __restrict__ Xhi,
@@ -729,8 +835,15 @@ inline int blocks_for(long long count, int per_block) {
 
 cudaError_t launch_directions(mhar_ctx* c, int j) {
   const int mode = c->opts.precision == MHAR_FP64 ? 0 : (c->opts.precision == MHAR_FP32 ? 1 : 2);
-  const long long threads = static_cast<long long>(c->z) * ((c->n + 3) / 4);
-  directions_kernel<<<blocks_for(threads, kThreads), kThreads, 0, c->stream>>>(
+  const long long threads =
+      static_cast<long long>(c->z) * ((c->n + 3) / 4) * (mode == 0 ? 2 : 1);
+  // Few threads (small bodies): small blocks, so that the draws (FP64
+  // transcendental functions in FP64 mode) spread over many SMs.
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  int block = static_cast<int>((threads + sms - 1) / sms);
+  block = block < 32 ? 32 : (block > kThreads ? kThreads : (block + 31) / 32 * 32);
+  directions_kernel<<<blocks_for(threads, block), block, 0, c->stream>>>(
       mode, (c->mE == 0 && c->pc_rank < 0) ? 1 : 0, c->opts.seed, c->d.step, j, c->opts.walker0,
       c->z, c->n, c->n_ld,
       c->k_pad, c->d.D64, c->d.D32, c->d.Dh, c->d.Dl);
@@ -768,6 +881,30 @@ cudaError_t launch_precondition(mhar_ctx* c, int j, int split) {
         c->d.pc_delta32, c->d.pc_U32, c->d.D32, split, c->k_pad, z_ld, c->use_ts ? 1 : 0,
         c->d.sigma, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2);
   }
+  return cudaGetLastError();
+}
+
+bool simt_warp_path(const mhar_ctx* c) {
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  return static_cast<long long>(blocks_for(c->m, 64)) * blocks_for(c->z, 64) < sms &&
+         c->m <= 2048;
+}
+
+cudaError_t launch_chord_update_warp(mhar_ctx* c, int j) {
+  const int g = blocks_for(c->z, kWarpChordThreads / 32);
+  if (c->opts.precision == MHAR_FP64)
+    chord_warp_kernel<double><<<g, kWarpChordThreads, 0, c->stream>>>(
+        c->d.A64, c->d.b64, c->d.X64, c->d.D64, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
+        c->d.key_hi, c->d.status, 1, c->opts.seed, c->d.step, j, c->opts.walker0, c->d.lmin,
+        c->d.lmax, c->d.theta, c->d.counters, c->d.X64, c->d.D64, nullptr, nullptr, nullptr,
+        c->mE, nullptr, nullptr);
+  else
+    chord_warp_kernel<float><<<g, kWarpChordThreads, 0, c->stream>>>(
+        c->d.A32, c->d.b32, c->d.Xhi, c->d.D32, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
+        c->d.key_hi, c->d.status, 1, c->opts.seed, c->d.step, j, c->opts.walker0, c->d.lmin,
+        c->d.lmax, c->d.theta, c->d.counters, nullptr, nullptr, c->d.Xhi, c->d.Xlo, c->d.D32,
+        c->mE, c->d.AE32, c->d.corr);
   return cudaGetLastError();
 }
 

@@ -146,7 +146,8 @@ bool tail_draws(const mhar_ctx* c) {
 
 int kernels_per_iteration(const mhar_ctx* c) {
   if (tail_draws(c)) return 1;
-  return 1 + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) + (mixed(c) ? 1 : 2);
+  return 1 + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) +
+         ((mixed(c) || mhar::simt_warp_path(c)) ? 1 : 2);
 }
 
 int emit_count(const mhar_ctx* c) {
@@ -173,6 +174,7 @@ cudaError_t enqueue_chord(mhar_ctx* c, int j) {
     if (c->use_ts) return mhar::launch_recompute_ts(c, j);
     return c->use_sk ? mhar::launch_recompute_sk(c, j) : mhar::launch_recompute_tc(c, j);
   }
+  if (mhar::simt_warp_path(c)) return mhar::launch_chord_update_warp(c, j);
   cudaError_t e = mhar::launch_chord_simt(c);
   return e == cudaSuccess ? mhar::launch_update_simt(c, j) : e;
 }
@@ -373,7 +375,7 @@ const char* mhar_kernel_name(const mhar_ctx* c) {
   if (!c) return "none";
   if (recompute(c)) return c->use_ts ? "recompute_ts_kernel" : (c->use_sk ? "recompute_sk_kernel" : "recompute_tc_kernel");
   if (stored(c)) return "walker_tc_kernel";
-  return "chord_simt_kernel";
+  return mhar::simt_warp_path(c) ? "chord_warp_kernel" : "chord_simt_kernel";
 }
 
 const char* mhar_last_error(const mhar_ctx* c) {

@@ -120,6 +120,10 @@ namespace mhar {
 cudaError_t launch_directions(mhar_ctx* ctx, int j);
 cudaError_t launch_projection(mhar_ctx* ctx, int j);
 cudaError_t launch_chord_simt(mhar_ctx* ctx);
+// Small bodies in the FP64 / FP32 modes: one warp per walker does the chord,
+// theta and the move (Sections 4.4-4.5) in a single launch.
+bool simt_warp_path(const mhar_ctx* ctx);
+cudaError_t launch_chord_update_warp(mhar_ctx* ctx, int j);
 cudaError_t launch_update_simt(mhar_ctx* ctx, int j);
 cudaError_t launch_advance(mhar_ctx* ctx, int steps);
 // Recompute mode: flags bit 1 split X, bit 2 draw D (for iteration step + j).

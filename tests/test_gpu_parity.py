@@ -232,3 +232,17 @@ def test_unbounded_body_reported(prec):
         X, _ = s.state()
         np.testing.assert_array_equal(X, 0.0)
         assert s.stats().unbounded == 3 * 16
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiled_chord_path_against_oracle(prec):
+    # z = 2048 walkers and m = 1500 rows give (1500/64) x (2048/64) = 768 tiles,
+    # enough for the tiled chord kernel (smaller bodies use a warp per walker);
+    # the first 40 walkers are checked against the oracle run on them alone.
+    p = wl.random_polytope(40, 1500, seed=8)
+    z, steps = 2048, 10
+    with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=5) as s:
+        got = s.run(steps, thin=1)
+    ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (40, 1)), steps, thin=1, seed=5)
+    err = np.abs(got[:, :40] - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
+    assert err <= TOL[prec], err
