@@ -269,57 +269,37 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
     // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
     // First, while the first row tiles are on their way: iteration s+1's
     // directions into the other pair (walker_tail.cuh, step 0).
-    if (p.wt.draw)
-      walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
-                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;
+    const float* bS_rows = p.bS + row_base + cg * 32;
+    if (lane == 0 && ntiles > 0) prefetch_l1(bS_rows);
+    if (p.wt.draw)
+      walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
+                                       w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
     const float ws = p.wscale[k];
-    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    ChordAcc acc;
+    acc.init();
     for (int nt = 0; nt < ntiles; ++nt) {
       const int b = nt & 1;
+      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(bS_rows + (nt + 1) * kRowsTile);
       mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err, true);
       tc_fence_after();
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
       const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);
-      float g0[16], g1[16], p0[16], p1[16];
-      tmem_ld16(gcol, g0);
-      tmem_ld16(gcol + 16, g1);
-      tmem_ld16(gcol + 128, p0);
-      tmem_ld16(gcol + 144, p1);
+      float sv[32], gv[32];
+      tmem_ld32(gcol + 128u, sv);
+      tmem_ld32(gcol, gv);
       // The accumulators of this buffer are in registers: let the MMA reuse it.
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tail->t_empty[b]);
-      const float4* br4 = reinterpret_cast<const float4*>(p.bS + row_base + nt * kRowsTile + cg * 32);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float br[16];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 v = __ldg(br4 + 4 * h + i);
-          br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
-        }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float gg = h == 0 ? g0[c] : g1[c];
-          const float pp = h == 0 ? p0[c] : p1[c];
-          const float sv = fmaf(-pp, ws, br[c]);
-          const float ss = fmaxf(sv, 0.0f);
-          chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
-          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
-          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
-          const float bnd = gg > 0.0f ? hi : lo;
-          if (ss < bnd * gg) {
-            const float r = __fdividef(ss, gg);
-            if (gg > 0.0f) hi = r; else lo = r;
-          }
-        }
-      }
+      slack32(sv, bS_rows + nt * kRowsTile, ws, acc);
+      scan32(sv, gv, acc);
     }
+    const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
     tail->part_hi[cg][wl] = hi;
     named_bar<kEpiWarps * 32>();
@@ -333,7 +313,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
         st_dsmem_f32(&tail->recv_hi[rank][wl], r, H);
       }
     }
-    if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+    if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
 
   // Every push is visible after this barrier; no remote access follows it.

@@ -241,6 +241,8 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     for (int sg = sb; sg < se; ++sg) {
       const SkSeg seg = p.segs[sg];
       const int strip = seg.strip;
+      const float* bS_rows = p.bS + cg * 32;
+      if (lane == 0 && seg.t1 > seg.t0) prefetch_l1(bS_rows + seg.t0 * kRowsTile);
       // Iteration s+1's directions for this segment's share of the strip's
       // walkers, into the other pair (while the segment's first tile loads).
       if (p.wt.draw) {
@@ -251,48 +253,27 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       }
       const int k = strip * kWalkers + wl;
       const float ws = p.wscale[k];
-      float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+      ChordAcc acc;
+      acc.init();
       for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
         const int b = gt & 1;
+        if (lane == 0 && nt + 1 < seg.t1) prefetch_l1(bS_rows + (nt + 1) * kRowsTile);
         mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, p.err, true);
         tc_fence_after();
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
         const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);
-        float g0[16], g1[16], p0[16], p1[16];
-        tmem_ld16(gcol, g0);
-        tmem_ld16(gcol + 16, g1);
-        tmem_ld16(gcol + 128, p0);
-        tmem_ld16(gcol + 144, p1);
+        float sv[32], gv[32];
+        tmem_ld32(gcol + 128u, sv);
+        tmem_ld32(gcol, gv);
+        // The accumulators of this buffer are in registers: let the MMA reuse it.
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_sk(&tail->t_empty[b]);
-        const float4* br4 = reinterpret_cast<const float4*>(p.bS + nt * kRowsTile + cg * 32);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float br[16];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float4 v = __ldg(br4 + 4 * h + i);
-            br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
-          }
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const float gg = h == 0 ? g0[c] : g1[c];
-            const float pp = h == 0 ? p0[c] : p1[c];
-            const float sv = fmaf(-pp, ws, br[c]);
-            const float ss = fmaxf(sv, 0.0f);
-            chk = fmaf(gg, 0.0f, fmaf(pp, 0.0f, chk));
-            // s/g improves the bound on its side iff s < bound * g (g > 0: upper
-            // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
-            const float bnd = gg > 0.0f ? hi : lo;
-            if (ss < bnd * gg) {
-              const float r = __fdividef(ss, gg);
-              if (gg > 0.0f) hi = r; else lo = r;
-            }
-          }
-        }
+        slack32(sv, bS_rows + nt * kRowsTile, ws, acc);
+        scan32(sv, gv, acc);
       }
-      if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+      if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
+      const float lo = acc.lo_all(), hi = acc.hi_all();
       tail->part_lo[cg][wl] = lo;
       tail->part_hi[cg][wl] = hi;
       named_bar<kEpiWarps * 32>();

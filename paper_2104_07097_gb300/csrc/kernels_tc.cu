@@ -256,7 +256,8 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const int cg = e >> 2;        // which 32-column group of each tile
     const int wl = q * 32 + lane; // walker within the strip
     const int k = strip * kWalkers + wl;
-    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    ChordAcc acc;
+    acc.init();
     float s_cur[32], s_nxt[32];
     if (ntiles > 0) load_s32(p, s_block(p, row_base + cg * 32, k), s_cur);
     for (int nt = 0; nt < ntiles; ++nt) {
@@ -275,22 +276,17 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
           // scale, so their ratio is the paper's lambda_i unchanged.
           const float gg = g[c];
           const float ss = fmaxf(s_cur[16 * half + c], 0.0f);
-          chk = fmaf(gg, 0.0f, chk);
-          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
-          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
-          const float bnd = gg > 0.0f ? hi : lo;
-          if (ss < bnd * gg) {
-            const float r = __fdividef(ss, gg);
-            if (gg > 0.0f) hi = r; else lo = r;
-          }
+          acc.check(gg);
+          acc.add(ss, gg);
         }
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) s_cur[c] = s_nxt[c];
     }
+    const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
     tail->part_hi[cg][wl] = hi;
-    const int bad = !(chk == 0.0f);
+    const int bad = !acc.finite();
     named_bar<kEpiWarps * 32>();
     if (cg == 0) {
       tail->cta_lo[wl] = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));

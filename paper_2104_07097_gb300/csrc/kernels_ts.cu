@@ -14,9 +14,12 @@
 //   * the rows of A stream in 128-row tiles (MMA N = 128) through twelve
 //     16 KB slots (hi and lo staged separately), more than a tile ahead;
 //   * the G and P accumulators of a tile (128 + 128 columns) take the other
-//     256 TMEM columns; the epilogue copies a tile's accumulators to
-//     registers and releases them at once, so the MMAs of the next tile wait
-//     only for that copy.
+//     256 TMEM columns.  A tile's MMAs run as two passes, P first, then G,
+//     each with its own full / empty barrier pair: the epilogue copies P to
+//     registers while the G pass runs and releases it, so the next tile's P
+//     pass follows the G pass without draining the tensor pipe, and likewise
+//     for G.  The epilogue's ratio work on a tile overlaps the next tile's
+//     MMAs.
 // Measured on GB300: an MMA whose operands both come from shared memory needs
 // the SM's whole shared-memory bandwidth at full rate, so the loads of the
 // other warps and the TMA writes slow it; with A in tensor memory it needs
@@ -70,8 +73,8 @@ struct TsParams {
 struct TsTail {
   uint64_t a_full[kSlots];
   uint64_t a_empty[kSlots];
-  uint64_t t_full;
-  uint64_t t_empty;
+  uint64_t p_full, p_empty;    // P accumulator: MMAs done / copied out
+  uint64_t g_full, g_empty;    // G accumulator
   uint32_t tmem_base;
   int timed_out;
   float part_lo[4][kWalkers];
@@ -96,6 +99,45 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One 64-column K chunk of a tile's P pass (X hi, X lo times A hi; X hi
+// times A lo) with KS K steps; slot uses ih = it0 + 2 kc (A hi), ih + 1 (A lo).
+template <int KS>
+__device__ __forceinline__ void ts_p_chunk(TsTail* tail, uint8_t* base, int it0, int kc,
+                                           uint32_t p_tmem, uint32_t op_xh, uint32_t op_xl,
+                                           uint32_t idesc, volatile int* timed_out, int* err) {
+  const int ih = it0 + 2 * kc, il = ih + 1;
+  const uint32_t ac0 = static_cast<uint32_t>(kc * 32);   // 2 FP16 per column
+  mbar_wait(&tail->a_full[ih % kSlots], (ih / kSlots) & 1, timed_out, err);
+  tc_fence_after();
+  // A slot's descriptor is built once; a K step of 16 FP16 adds 2 to it (32 bytes).
+  const uint64_t bh = sw128_desc(smem_u32(base + (ih % kSlots) * kSlotBytes));
+  mma_ts_run2<KS>(p_tmem, op_xh + ac0, op_xl + ac0, bh, idesc, kc > 0 ? 1u : 0u);
+  mbar_wait(&tail->a_full[il % kSlots], (il / kSlots) & 1, timed_out, err);
+  tc_fence_after();
+  const uint64_t bl = sw128_desc(smem_u32(base + (il % kSlots) * kSlotBytes));
+  mma_ts_run1<KS>(p_tmem, op_xh + ac0, bl, idesc);
+}
+
+// The same chunk of the G pass (D hi, D lo times A hi; D hi times A lo); the
+// slots were waited for by the P pass and are released here.
+template <int KS>
+__device__ __forceinline__ void ts_g_chunk(TsTail* tail, uint8_t* base, int it0, int kc,
+                                           uint32_t g_tmem, uint32_t op_dh, uint32_t op_dl,
+                                           uint32_t idesc) {
+  const int ih = it0 + 2 * kc, il = ih + 1;
+  const uint32_t ac0 = static_cast<uint32_t>(kc * 32);
+  const uint64_t bh = sw128_desc(smem_u32(base + (ih % kSlots) * kSlotBytes));
+  mma_ts_run2<KS>(g_tmem, op_dh + ac0, op_dl + ac0, bh, idesc, kc > 0 ? 1u : 0u);
+  mma_commit(&tail->a_empty[ih % kSlots]);
+  const uint64_t bl = sw128_desc(smem_u32(base + (il % kSlots) * kSlotBytes));
+  mma_ts_run1<KS>(g_tmem, op_dh + ac0, bl, idesc);
+  mma_commit(&tail->a_empty[il % kSlots]);
+}
+
+// LAST: K steps (16 FP16 each) in the last 64-column chunk of A's rows, 1..4;
+// the other chunks have 4.  A compile-time count keeps the MMA runs free of
+// branches (the issuing thread's stream between MMAs is the limiter).
+template <int LAST>
 __global__ void __launch_bounds__(kThreadsTs, 1)
 recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const TsParams p) {
@@ -124,8 +166,10 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
-    mbar_init(&tail->t_full, 1);
-    mbar_init(&tail->t_empty, kEpiWarps);
+    mbar_init(&tail->p_full, 1);
+    mbar_init(&tail->p_empty, kEpiWarps);
+    mbar_init(&tail->g_full, 1);
+    mbar_init(&tail->g_empty, kEpiWarps);
     tail->timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -208,52 +252,27 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       constexpr uint32_t idesc = make_idesc(kWalkers, kTile);
       const uint32_t op_dh = tmem + kOpCol, op_dl = op_dh + 64u, op_xh = op_dh + 128u,
                      op_xl = op_dh + 192u;
-      int it = 0;
       const uint32_t g_tmem = tmem;
       const uint32_t p_tmem = tmem + 128u;
-      for (int nt = 0; nt < ntiles; ++nt) {
-        // The accumulators are single-buffered: wait until the epilogue has
-        // copied the previous tile out.
-        if (nt >= 1) mbar_wait(&tail->t_empty, (nt - 1) & 1, timed_out, p.err);
+      int it0 = 0;   // first slot use of the tile
+      for (int nt = 0; nt < ntiles; ++nt, it0 += 2 * p.k_chunks) {
+        // P pass: X hi, X lo times A hi; X hi times A lo.  The accumulator is
+        // free once the epilogue has copied the previous tile's P out.
+        if (nt >= 1) mbar_wait(&tail->p_empty, (nt - 1) & 1, timed_out, p.err);
         tc_fence_after();
-        for (int kc = 0; kc < p.k_chunks; ++kc) {
-          int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
-          ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
-          // A hi: D hi, D lo, X hi, X lo times it.  The slot's descriptor is
-          // built once; a K step of 16 FP16 adds 2 to it (32 bytes).
-          int s = it % kSlots;
-          mbar_wait(&tail->a_full[s], (it / kSlots) & 1, timed_out, p.err);
-          tc_fence_after();
-          uint64_t bd = sw128_desc(smem_u32(base + s * kSlotBytes));
-          const uint32_t ac0 = static_cast<uint32_t>(kc * 32);
-#pragma unroll 4
-          for (int ks = 0; ks < ks_n; ++ks) {
-            const uint32_t ac = ac0 + static_cast<uint32_t>(ks * 8);   // 2 FP16 per column
-            const uint64_t b = bd + static_cast<uint64_t>(2 * ks);
-            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            mma_f16_ts(g_tmem, op_dh + ac, b, idesc, acc);
-            mma_f16_ts(g_tmem, op_dl + ac, b, idesc, 1u);
-            mma_f16_ts(p_tmem, op_xh + ac, b, idesc, acc);
-            mma_f16_ts(p_tmem, op_xl + ac, b, idesc, 1u);
-          }
-          mma_commit(&tail->a_empty[s]);
-          ++it;
-          // A lo: D hi and X hi times it.
-          s = it % kSlots;
-          mbar_wait(&tail->a_full[s], (it / kSlots) & 1, timed_out, p.err);
-          tc_fence_after();
-          bd = sw128_desc(smem_u32(base + s * kSlotBytes));
-#pragma unroll 4
-          for (int ks = 0; ks < ks_n; ++ks) {
-            const uint32_t ac = ac0 + static_cast<uint32_t>(ks * 8);
-            const uint64_t b = bd + static_cast<uint64_t>(2 * ks);
-            mma_f16_ts(g_tmem, op_dh + ac, b, idesc, 1u);
-            mma_f16_ts(p_tmem, op_xh + ac, b, idesc, 1u);
-          }
-          mma_commit(&tail->a_empty[s]);
-          ++it;
-        }
-        mma_commit(&tail->t_full);
+        for (int kc = 0; kc + 1 < p.k_chunks; ++kc)
+          ts_p_chunk<4>(tail, base, it0, kc, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
+        ts_p_chunk<LAST>(tail, base, it0, p.k_chunks - 1, p_tmem, op_xh, op_xl, idesc, timed_out,
+                         p.err);
+        mma_commit(&tail->p_full);
+        // G pass: D hi, D lo times A hi; D hi times A lo.  Each slot is
+        // released after its last use here.
+        if (nt >= 1) mbar_wait(&tail->g_empty, (nt - 1) & 1, timed_out, p.err);
+        tc_fence_after();
+        for (int kc = 0; kc + 1 < p.k_chunks; ++kc)
+          ts_g_chunk<4>(tail, base, it0, kc, g_tmem, op_dh, op_dl, idesc);
+        ts_g_chunk<LAST>(tail, base, it0, p.k_chunks - 1, g_tmem, op_dh, op_dl, idesc);
+        mma_commit(&tail->g_full);
       }
     }
     __syncwarp();
@@ -261,56 +280,44 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     // ---- epilogue: s = b - p, ratios, per-walker partial chord ------------------
     // First, while the first row tiles are on their way: iteration s+1's
     // directions into the other pair (walker_tail.cuh, step 0).
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;              // 32-column group of each 128-column tile
+    const float* bS_rows = p.bS + row_base + cg * 32;
+    if (lane == 0 && ntiles > 0) prefetch_l1(bS_rows);
     if (p.wt.draw)
       walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
                                        w_begin, w_count, static_cast<int>(threadIdx.x) - 64,
                                        tail->gs);
-    const int e = warp - 2;
-    const int q = warp & 3;
-    const int cg = e >> 2;              // 32-column group of each 128-column tile
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
     const float ws = p.wscale[k];
-    float lo = -INFINITY, hi = INFINITY, chk = 0.0f;
+    ChordAcc acc;
+    acc.init();
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(cg * 32);
     for (int nt = 0; nt < ntiles; ++nt) {
-      mbar_wait(&tail->t_full, nt & 1, timed_out, p.err);
+      // P first (its pass ends first), then G; each accumulator is released
+      // as soon as it is in registers.
+      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(bS_rows + (nt + 1) * kTile);
+      float sv[32], gv[32];
+      mbar_wait(&tail->p_full, nt & 1, timed_out, p.err);
       tc_fence_after();
-      const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(cg * 32);
-      float g0[16], g1[16], p0[16], p1[16];
-      tmem_ld16(gcol, g0);
-      tmem_ld16(gcol + 16, g1);
-      tmem_ld16(gcol + 128, p0);
-      tmem_ld16(gcol + 144, p1);
+      tmem_ld32(gcol + 128u, sv);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) arrive(&tail->t_empty);
-      const float4* br4 = reinterpret_cast<const float4*>(p.bS + row_base + nt * kTile + cg * 32);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float br[16];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 v = __ldg(br4 + 4 * h + i);
-          br[4 * i] = v.x; br[4 * i + 1] = v.y; br[4 * i + 2] = v.z; br[4 * i + 3] = v.w;
-        }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float gg = h == 0 ? g0[c] : g1[c];
-          const float pv = h == 0 ? p0[c] : p1[c];
-          const float sv = fmaf(-pv, ws, br[c]);
-          const float ss = fmaxf(sv, 0.0f);
-          chk = fmaf(gg, 0.0f, fmaf(pv, 0.0f, chk));
-          // s/g improves the bound on its side iff s < bound * g (g > 0: upper
-          // bound lambda_max; g < 0: lower bound lambda_min); g == 0 never does.
-          const float bnd = gg > 0.0f ? hi : lo;
-          if (ss < bnd * gg) {
-            const float r = __fdividef(ss, gg);
-            if (gg > 0.0f) hi = r; else lo = r;
-          }
-        }
-      }
+      if (lane == 0) arrive(&tail->p_empty);
+      // The slacks while the G pass finishes.
+      slack32(sv, bS_rows + nt * kTile, ws, acc);
+      mbar_wait(&tail->g_full, nt & 1, timed_out, p.err);
+      tc_fence_after();
+      tmem_ld32(gcol, gv);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) arrive(&tail->g_empty);
+      scan32(sv, gv, acc);
     }
+    const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
     tail->part_hi[cg][wl] = hi;
     named_bar<kEpiWarps * 32>();
@@ -324,7 +331,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
         st_dsmem(&tail->recv_hi[rank][wl], r, H);
       }
     }
-    if (!(chk == 0.0f)) atomicOr(p.status, MHAR_ST_NONFINITE);
+    if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
 
   // Every push is visible after this barrier; no remote access follows it.
@@ -415,9 +422,12 @@ int ts_prepare(mhar_ctx* c) {
     snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed (64-row maps)");
     return MHAR_E_CUDA;
   }
-  cudaError_t e = cudaFuncSetAttribute(recompute_ts_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kSmemTs));
+  cudaError_t e = cudaSuccess;
+  for (auto* k : {recompute_ts_kernel<1>, recompute_ts_kernel<2>, recompute_ts_kernel<3>,
+                  recompute_ts_kernel<4>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kSmemTs));
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "recompute (TMEM operand) kernel attributes: %s",
              cudaGetErrorString(e));
@@ -470,7 +480,13 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, recompute_ts_kernel, plan->ah64, plan->al64, p);
+  const int last = (c->kdim - (p.k_chunks - 1) * kTcKChunk) / kTcK;   // 1..4
+  switch (last) {
+    case 1: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<1>, plan->ah64, plan->al64, p);
+    case 2: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<2>, plan->ah64, plan->al64, p);
+    case 3: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<3>, plan->ah64, plan->al64, p);
+    default: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<4>, plan->ah64, plan->al64, p);
+  }
 }
 
 }  // namespace mhar

@@ -123,6 +123,32 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uin
       "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// A run of TMEM-operand MMAs over ks = 0..KS-1 K steps of one shared-memory
+// slot, unrolled at compile time (a runtime trip count puts branches and
+// address arithmetic between the single issuing thread's MMAs, which
+// measurably starves the tensor pipe):
+//   two operands:  D += A0[ks] B[ks]; D += A1[ks] B[ks]   (ks = 0..KS-1)
+//   one operand:   D += A0[ks] B[ks]
+// A operands in tensor memory at a + 8 ks (2 FP16 per 32-bit column), B
+// descriptors at b + 2 ks (32 bytes per K step).  The very first MMA
+// overwrites D when acc_first == 0; every other one accumulates.
+template <int KS>
+__device__ __forceinline__ void mma_ts_run2(uint32_t d, uint32_t a0, uint32_t a1, uint64_t b,
+                                            uint32_t idesc, uint32_t acc_first) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint32_t ac = static_cast<uint32_t>(ks * 8);
+    mma_f16_ts(d, a0 + ac, b + static_cast<uint64_t>(2 * ks), idesc, ks > 0 ? 1u : acc_first);
+    mma_f16_ts(d, a1 + ac, b + static_cast<uint64_t>(2 * ks), idesc, 1u);
+  }
+}
+template <int KS>
+__device__ __forceinline__ void mma_ts_run1(uint32_t d, uint32_t a0, uint64_t b, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks)
+    mma_f16_ts(d, a0 + static_cast<uint32_t>(ks * 8), b + static_cast<uint64_t>(2 * ks), idesc, 1u);
+}
+
 // 32 consecutive 32-bit columns of this warp's 32 TMEM lanes from registers.
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
   asm volatile(
@@ -189,6 +215,85 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, one load.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One walker's running chord over a scan of rows (Algorithm 2's lambda_min /
+// lambda_max from the ratios s_i / g_i).  Branch-free: every row's ratio is
+// formed (one fast division) and folded into the bound on its side by a
+// select and a min / max, so the warp never diverges and the result is the
+// exact min (max) of the rounded ratios, whatever the order or split of the
+// scan -- different launch shapes give the same bits.
+struct ChordAcc {
+  float lo, hi, chk;
+
+  __device__ __forceinline__ void init() {
+    lo = -INFINITY;
+    hi = INFINITY;
+    chk = 0.0f;
+  }
+  // g > 0: upper bound lambda_max; g < 0: lower bound lambda_min; g == 0
+  // bounds neither side.  s is the clamped slack (s >= 0).
+  __device__ __forceinline__ void add(float ss, float gg) {
+    const float r = __fdividef(ss, gg);
+    hi = fminf(hi, gg > 0.0f ? r : INFINITY);
+    lo = fmaxf(lo, gg < 0.0f ? r : -INFINITY);
+  }
+  // Non-finite detector: stays 0 unless some value is Inf or NaN.
+  __device__ __forceinline__ void check(float v) { chk = fmaf(v, 0.0f, chk); }
+  __device__ __forceinline__ float lo_all() const { return lo; }
+  __device__ __forceinline__ float hi_all() const { return hi; }
+  __device__ __forceinline__ bool finite() const { return chk == 0.0f; }
+};
+
+// Brings one 128-byte line into L1 ahead of its use (the b_i / scale_i of a
+// tile's 32 rows: L1 does not keep them from one launch to the next).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Slack of one walker at 32 rows from its P = X A^T columns (in place):
+// s_i = b_i - p_i w, clamped at 0 (Lemma 4.2's s = b - A x, in the row and
+// walker scales of the FP16 operands).  bS points at the 32 rows' b_i / scale_i
+// (16-byte aligned).
+__device__ __forceinline__ void slack32(float (&v)[32], const float* bS, float ws, ChordAcc& acc) {
+  const float4* b4 = reinterpret_cast<const float4*>(bS);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 b = __ldg(b4 + i);
+    const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc.check(v[4 * i + j]);
+      v[4 * i + j] = fmaxf(fmaf(-v[4 * i + j], ws, bb[j]), 0.0f);
+    }
+  }
+}
+
+// The chord scan over 32 rows: slacks s (from slack32) against G = D A^T.
+__device__ __forceinline__ void scan32(const float (&s)[32], const float (&g)[32], ChordAcc& acc) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    acc.check(g[c]);
+    acc.add(s[c], g[c]);
+  }
 }
 
 template <int kThreads>
