@@ -114,6 +114,10 @@ struct RcMaps {
 
 // One cluster's work for one walker strip of one problem (`strip`), iteration
 // step + j.  The maps may live in kernel parameters or in global memory.
+// LAST: K steps in the operands' last 64-column chunk (1..4), a compile-time
+// constant so that the MMA runs carry no branches; 0: taken at run time (the
+// batched kernel, whose units differ in n).
+template <int LAST>
 __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int strip, int j) {
   const CUtensorMap& tm_ah = mp.ah;
   const CUtensorMap& tm_al = mp.al;
@@ -211,7 +215,8 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
         tc_fence_after();
         const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
         const uint32_t p_tmem = g_tmem + 128u;
-        for (int kc = 0; kc < p.k_chunks; ++kc) {
+        auto chunk = [&](int kc, auto ks_c) {
+          constexpr int KS = decltype(ks_c)::value;
           int ws;
           if (resident) {
             ws = kc;
@@ -225,41 +230,40 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
           const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
           const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
           const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-          int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
-          ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
           // A hi: the four products that read it; then release its slot.
           int as = a_it % kASlots;
           mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
           tc_fence_after();
-          uint64_t ad = sw128_desc(smem_u32(aslot + as * kABytes));
-#pragma unroll 4
-          for (int ks = 0; ks < ks_n; ++ks) {
-            const uint64_t o = static_cast<uint64_t>(2 * ks);
-            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            mma_f16(g_tmem, dh + o, ad + o, idesc, acc);
-            mma_f16(g_tmem, dl + o, ad + o, idesc, 1u);
-            mma_f16(p_tmem, xh + o, ad + o, idesc, acc);
-            mma_f16(p_tmem, xl + o, ad + o, idesc, 1u);
-          }
+          const int ks_n = KS > 0 ? KS : min(kTcKChunk / kTcK, (p.kdim - kc * kTcKChunk) / kTcK);
+          if constexpr (KS > 0)
+            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, sw128_desc(smem_u32(aslot + as * kABytes)),
+                          idesc, kc > 0 ? 1u : 0u);
+          else
+            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl,
+                        sw128_desc(smem_u32(aslot + as * kABytes)), idesc, kc > 0 ? 1u : 0u);
           mma_commit(&tail->a_empty[as]);
           ++a_it;
           // A lo: hi parts of the walker operands times it.
           as = a_it % kASlots;
           mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
           tc_fence_after();
-          ad = sw128_desc(smem_u32(aslot + as * kABytes));
-#pragma unroll 4
-          for (int ks = 0; ks < ks_n; ++ks) {
-            const uint64_t o = static_cast<uint64_t>(2 * ks);
-            mma_f16(g_tmem, dh + o, ad + o, idesc, 1u);
-            mma_f16(p_tmem, xh + o, ad + o, idesc, 1u);
-          }
+          if constexpr (KS > 0)
+            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)), idesc);
+          else
+            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)),
+                        idesc);
           mma_commit(&tail->a_empty[as]);
           ++a_it;
           if (!resident) {
             mma_commit(&tail->w_empty[ws]);
             ++w_it;
           }
+        };
+        if constexpr (LAST > 0) {
+          for (int kc = 0; kc + 1 < p.k_chunks; ++kc) chunk(kc, std::integral_constant<int, 4>{});
+          chunk(p.k_chunks - 1, std::integral_constant<int, LAST>{});
+        } else {
+          for (int kc = 0; kc < p.k_chunks; ++kc) chunk(kc, std::integral_constant<int, 0>{});
         }
         mma_commit(&tail->t_full[b]);
       }
@@ -375,9 +379,10 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
 }
 
 
+template <int LAST>
 __global__ void __launch_bounds__(kThreadsRc, 1)
 recompute_tc_kernel(const __grid_constant__ RcMaps maps, const __grid_constant__ RcParams p) {
-  rc_body(maps, p, static_cast<int>(blockIdx.y), p.j);
+  rc_body<LAST>(maps, p, static_cast<int>(blockIdx.y), p.j);
 }
 
 // Batched form: one launch for many problems.  blockIdx.y indexes a unit, a
@@ -392,7 +397,7 @@ struct alignas(128) BatchUnit {
 __global__ void __launch_bounds__(kThreadsRc, 1)
 recompute_batch_kernel(const BatchUnit* __restrict__ units, int j) {
   const BatchUnit& u = units[blockIdx.y];
-  rc_body(u.maps, u.p, u.strip, j);
+  rc_body<0>(u.maps, u.p, u.strip, j);
 }
 
 struct RcShape {
@@ -446,9 +451,12 @@ int rc_prepare(mhar_ctx* c) {
              kMaxCluster * kMaxTiles * kRowsTile, plan->m_tiles);
     return MHAR_E_UNSUPPORTED;
   }
-  cudaError_t e = cudaFuncSetAttribute(recompute_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kSmemRc));
+  cudaError_t e = cudaSuccess;
+  for (auto* k : {recompute_tc_kernel<1>, recompute_tc_kernel<2>, recompute_tc_kernel<3>,
+                  recompute_tc_kernel<4>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kSmemRc));
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "recompute kernel attributes: %s", cudaGetErrorString(e));
     cudaGetLastError();
@@ -523,7 +531,12 @@ cudaError_t launch_recompute_tc(mhar_ctx* c, int j) {
   const RcParams p = rc_params(c, j, s.tiles_per_cta);
   cudaLaunchAttribute attr[2];
   cudaLaunchConfig_t cfg = rc_config(s.C, plan->strips, c->stream, attr);
-  return cudaLaunchKernelEx(&cfg, recompute_tc_kernel, rc_maps(plan), p);
+  switch (last_chunk_steps(p.kdim, p.k_chunks)) {
+    case 1: return cudaLaunchKernelEx(&cfg, recompute_tc_kernel<1>, rc_maps(plan), p);
+    case 2: return cudaLaunchKernelEx(&cfg, recompute_tc_kernel<2>, rc_maps(plan), p);
+    case 3: return cudaLaunchKernelEx(&cfg, recompute_tc_kernel<3>, rc_maps(plan), p);
+    default: return cudaLaunchKernelEx(&cfg, recompute_tc_kernel<4>, rc_maps(plan), p);
+  }
 }
 
 // ---- batches ------------------------------------------------------------------

@@ -96,6 +96,8 @@ __device__ __forceinline__ void mbar_arrive_sk(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// LAST: K steps in the operands' last 64-column chunk (1..4).
+template <int LAST>
 __global__ void __launch_bounds__(kThreadsSk, 1)
 recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
@@ -184,44 +186,33 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
           tc_fence_after();
           const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
           const uint32_t p_tmem = g_tmem + 128u;
-          for (int kc = 0; kc < p.k_chunks; ++kc) {
+          // One K chunk; KS (its K steps) is a compile-time constant so that the
+          // MMA runs carry no branches.
+          auto chunk = [&](int kc, auto ks_c) {
+            constexpr int KS = decltype(ks_c)::value;
             const int ws = w_it % kWSlots;
             mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
             const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
             const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
             const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-            int ks_n = (p.kdim - kc * kTcKChunk) / kTcK;
-            ks_n = ks_n > kTcKChunk / kTcK ? kTcKChunk / kTcK : ks_n;
             int as = a_it % kASlots;
             mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
             tc_fence_after();
-            uint64_t ad = sw128_desc(smem_u32(aslot + as * kABytes));
-#pragma unroll 4
-            for (int ks = 0; ks < ks_n; ++ks) {
-              const uint64_t o = static_cast<uint64_t>(2 * ks);
-              const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-              mma_f16(g_tmem, dh + o, ad + o, idesc, acc);
-              mma_f16(g_tmem, dl + o, ad + o, idesc, 1u);
-              mma_f16(p_tmem, xh + o, ad + o, idesc, acc);
-              mma_f16(p_tmem, xl + o, ad + o, idesc, 1u);
-            }
+            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, sw128_desc(smem_u32(aslot + as * kABytes)),
+                          idesc, kc > 0 ? 1u : 0u);
             mma_commit(&tail->a_empty[as]);
             ++a_it;
             as = a_it % kASlots;
             mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
             tc_fence_after();
-            ad = sw128_desc(smem_u32(aslot + as * kABytes));
-#pragma unroll 4
-            for (int ks = 0; ks < ks_n; ++ks) {
-              const uint64_t o = static_cast<uint64_t>(2 * ks);
-              mma_f16(g_tmem, dh + o, ad + o, idesc, 1u);
-              mma_f16(p_tmem, xh + o, ad + o, idesc, 1u);
-            }
+            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)), idesc);
             mma_commit(&tail->a_empty[as]);
             ++a_it;
             mma_commit(&tail->w_empty[ws]);
             ++w_it;
-          }
+          };
+          for (int kc = 0; kc + 1 < p.k_chunks; ++kc) chunk(kc, std::integral_constant<int, 4>{});
+          chunk(p.k_chunks - 1, std::integral_constant<int, LAST>{});
           mma_commit(&tail->t_full[b]);
         }
       }
@@ -410,9 +401,11 @@ int sk_prepare(mhar_ctx* c) {
   if (e == cudaSuccess)
     e = cudaMemcpy(plan->seg_begin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(plan->arrivals, 0, sizeof(int) * strips);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(recompute_sk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemSk));
+  for (auto* k : {recompute_sk_kernel<1>, recompute_sk_kernel<2>, recompute_sk_kernel<3>,
+                  recompute_sk_kernel<4>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kSmemSk));
   c->sk = plan;
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "stream-K schedule: %s", cudaGetErrorString(e));
@@ -466,8 +459,15 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, recompute_sk_kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2,
-                            tp->dl2, tp->xh, tp->xl, p, j);
+  auto* kernel = recompute_sk_kernel<4>;
+  switch (last_chunk_steps(p.kdim, p.k_chunks)) {
+    case 1: kernel = recompute_sk_kernel<1>; break;
+    case 2: kernel = recompute_sk_kernel<2>; break;
+    case 3: kernel = recompute_sk_kernel<3>; break;
+    default: break;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2, tp->dl2, tp->xh,
+                            tp->xl, p, j);
 }
 
 }  // namespace mhar

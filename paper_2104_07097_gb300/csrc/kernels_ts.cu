@@ -480,8 +480,7 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  const int last = (c->kdim - (p.k_chunks - 1) * kTcKChunk) / kTcK;   // 1..4
-  switch (last) {
+  switch (last_chunk_steps(p.kdim, p.k_chunks)) {
     case 1: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<1>, plan->ah64, plan->al64, p);
     case 2: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<2>, plan->ah64, plan->al64, p);
     case 3: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<3>, plan->ah64, plan->al64, p);

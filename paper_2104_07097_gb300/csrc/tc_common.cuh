@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "mhar_internal.h"
 
@@ -147,6 +148,62 @@ __device__ __forceinline__ void mma_ts_run1(uint32_t d, uint32_t a0, uint64_t b,
 #pragma unroll
   for (int ks = 0; ks < KS; ++ks)
     mma_f16_ts(d, a0 + static_cast<uint32_t>(ks * 8), b + static_cast<uint64_t>(2 * ks), idesc, 1u);
+}
+
+// The same for the shared-memory-operand kernels: one K chunk's MMAs against
+// the A hi slot (G += Dh A, G += Dl A, P += Xh A, P += Xl A per K step) and
+// against the A lo slot (G += Dh A, P += Xh A); descriptors advance by 2 per
+// K step.  The first G and P MMAs of the hi run overwrite when acc_first == 0.
+template <int KS>
+__device__ __forceinline__ void mma_ss_hi(uint32_t g, uint32_t p, uint64_t dh, uint64_t dl,
+                                          uint64_t xh, uint64_t xl, uint64_t ad, uint32_t idesc,
+                                          uint32_t acc_first) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = static_cast<uint64_t>(2 * ks);
+    const uint32_t acc = ks > 0 ? 1u : acc_first;
+    mma_f16(g, dh + o, ad + o, idesc, acc);
+    mma_f16(g, dl + o, ad + o, idesc, 1u);
+    mma_f16(p, xh + o, ad + o, idesc, acc);
+    mma_f16(p, xl + o, ad + o, idesc, 1u);
+  }
+}
+template <int KS>
+__device__ __forceinline__ void mma_ss_lo(uint32_t g, uint32_t p, uint64_t dh, uint64_t xh,
+                                          uint64_t ad, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = static_cast<uint64_t>(2 * ks);
+    mma_f16(g, dh + o, ad + o, idesc, 1u);
+    mma_f16(p, xh + o, ad + o, idesc, 1u);
+  }
+}
+
+// Runtime K-step count (1..4) to the runs above, for kernels that serve
+// bodies of different n in one launch.
+__device__ __forceinline__ void mma_ss_hi_n(int ks_n, uint32_t g, uint32_t p, uint64_t dh,
+                                            uint64_t dl, uint64_t xh, uint64_t xl, uint64_t ad,
+                                            uint32_t idesc, uint32_t acc_first) {
+  switch (ks_n) {
+    case 4: mma_ss_hi<4>(g, p, dh, dl, xh, xl, ad, idesc, acc_first); break;
+    case 3: mma_ss_hi<3>(g, p, dh, dl, xh, xl, ad, idesc, acc_first); break;
+    case 2: mma_ss_hi<2>(g, p, dh, dl, xh, xl, ad, idesc, acc_first); break;
+    default: mma_ss_hi<1>(g, p, dh, dl, xh, xl, ad, idesc, acc_first); break;
+  }
+}
+__device__ __forceinline__ void mma_ss_lo_n(int ks_n, uint32_t g, uint32_t p, uint64_t dh,
+                                            uint64_t xh, uint64_t ad, uint32_t idesc) {
+  switch (ks_n) {
+    case 4: mma_ss_lo<4>(g, p, dh, xh, ad, idesc); break;
+    case 3: mma_ss_lo<3>(g, p, dh, xh, ad, idesc); break;
+    case 2: mma_ss_lo<2>(g, p, dh, xh, ad, idesc); break;
+    default: mma_ss_lo<1>(g, p, dh, xh, ad, idesc); break;
+  }
+}
+
+// K steps (16 FP16 each) in the last 64-column chunk of the operands: 1..4.
+__host__ __device__ inline int last_chunk_steps(int kdim, int k_chunks) {
+  return (kdim - (k_chunks - 1) * kTcKChunk) / kTcK;
 }
 
 // 32 consecutive 32-bit columns of this warp's 32 TMEM lanes from registers.
