@@ -108,7 +108,8 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
                                   const double* __restrict__ AE64, const double* __restrict__ L,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
                                   float* corr, int z_ld, int inter, const float* sigma,
-                                  const uint64_t* step_ptr, int j, __half* Dh1, __half* Dl1) {
+                                  const uint64_t* step_ptr, int j, __half* Dh1, __half* Dl1,
+                                  int* status) {
   if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
     Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
     Dl = Dl1;
@@ -138,6 +139,7 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
       const size_t o = op_off(k, i, k_pad, z_ld, inter);
       Dh[o] = hh;
       Dl[o] = __float2half_rn(v - __half2float(hh));
+      if (!(fabsf(v) <= kHalfMax)) atomicOr(status, MHAR_ST_NONFINITE);
     } else {
       h[i] = s;
     }
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(kPcThreads)
 precondition_kernel(uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0, int z,
                     int n, int n_ld, int rank, const T* __restrict__ delta,
                     const T* __restrict__ U, T* D, int split, int k_pad, int z_ld, int inter,
-                    const float* sigma, __half* Dh, __half* Dl, __half* Dh1, __half* Dl1) {
+                    const float* sigma, __half* Dh, __half* Dl, __half* Dh1, __half* Dl1,
+                    int* status) {
   __shared__ T g[kPcWalkers][kMaxPcRank + 1];
   if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
     Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
@@ -232,6 +235,7 @@ precondition_kernel(uint64_t seed, const uint64_t* step_ptr, int j, uint32_t wal
       const size_t o = op_off(k, i, k_pad, z_ld, inter);
       Dh[o] = h;
       Dl[o] = __float2half_rn(v - __half2float(h));
+      if (!(fabsf(v) <= kHalfMax)) atomicOr(status, MHAR_ST_NONFINITE);
     } else {
       D[static_cast<size_t>(k) * n_ld + i] = acc;
     }
@@ -425,7 +429,7 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
                     int z, int z_ld, int n, int n_ld, int k_pad, const float* Xhi,
                     const float* Xlo, __half* Dh0, __half* Dl0, __half* Dh1, __half* Dl1,
                     float* D32, __half* Xh, __half* Xl, float* wscale, int inter,
-                    const float* sigma, int draw32) {
+                    const float* sigma, int draw32, int* status) {
   __shared__ float red[kPrepMaxWarps][kPrepWalkers];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -463,13 +467,16 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
         ld8(Xhi + xr + i0, hi);
         ld8(Xlo + xr + i0, lo);
         __half h8[8], l8[8];
+        bool bad = false;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int i = i0 + e;
           const float v = i < n ? (hi[e] + lo[e]) * inv / sigma[i] : 0.0f;
           h8[e] = __float2half_rn(v);
           l8[e] = __float2half_rn(v - __half2float(h8[e]));
+          bad |= !(fabsf(v) <= kHalfMax);
         }
+        if (bad) atomicOr(status, MHAR_ST_NONFINITE);
         st8h(Xh + opo(i0), h8);
         st8h(Xl + opo(i0), l8);
       }
@@ -855,14 +862,14 @@ cudaError_t launch_projection(mhar_ctx* c, int j) {
   if (c->opts.precision == MHAR_FP64) {
     projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr);
+        nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr, c->d.status);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
         c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0, c->d.sigma,
-        c->d.step, j, c->d.Dh2, c->d.Dl2);
+        c->d.step, j, c->d.Dh2, c->d.Dl2, c->d.status);
   }
   return cudaGetLastError();
 }
@@ -874,12 +881,12 @@ cudaError_t launch_precondition(mhar_ctx* c, int j, int split) {
     precondition_kernel<double><<<grid, kPcThreads, 0, c->stream>>>(
         c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
         c->d.pc_delta64, c->d.pc_U64, c->d.D64, 0, c->k_pad, z_ld, 0, nullptr, nullptr, nullptr,
-        nullptr, nullptr);
+        nullptr, nullptr, c->d.status);
   } else {
     precondition_kernel<float><<<grid, kPcThreads, 0, c->stream>>>(
         c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->pc_rank,
         c->d.pc_delta32, c->d.pc_U32, c->d.D32, split, c->k_pad, z_ld, c->use_ts ? 1 : 0,
-        c->d.sigma, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2);
+        c->d.sigma, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2, c->d.status);
   }
   return cudaGetLastError();
 }
@@ -938,7 +945,8 @@ cudaError_t launch_prep_walkers(mhar_ctx* c, int j, int flags) {
   prep_walkers_kernel<<<blocks_for(c->z, kPrepWalkers), warps * 32, 0, c->stream>>>(
       flags, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, z_ld, c->n, c->n_ld, c->k_pad,
       c->d.Xhi, c->d.Xlo, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2, c->d.D32, c->d.Xh, c->d.Xl,
-      c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma, (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0);
+      c->d.wscale, c->use_ts ? 1 : 0, c->d.sigma, (c->mE > 0 || c->pc_rank >= 0) ? 1 : 0,
+      c->d.status);
   return cudaGetLastError();
 }
 

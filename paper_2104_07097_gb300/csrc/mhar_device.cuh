@@ -19,6 +19,9 @@ constexpr uint32_t kStreamChord = 1u;
 constexpr uint32_t kStreamLowRank = 2u;
 constexpr uint32_t kStreamFit = 3u;
 constexpr int kMaxPcRank = 32;  // columns of the low-rank factor U
+// Largest finite FP16 value: a value split into an FP16 pair must stay within
+// it (beyond it the pair would be infinite and so would the products).
+constexpr float kHalfMax = 65504.0f;
 
 struct U4 { uint32_t x, y, z, w; };
 

@@ -293,30 +293,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // One walker's running chord over a scan of rows (Algorithm 2's lambda_min /
-// lambda_max from the ratios s_i / g_i).  Branch-free: every row's ratio is
-// formed (one fast division) and folded into the bound on its side by a
-// select and a min / max, so the warp never diverges and the result is the
-// exact min (max) of the rounded ratios, whatever the order or split of the
-// scan -- different launch shapes give the same bits.
+// lambda_max from the ratios r_i = s_i / g_i, s_i >= 0).  Branch-free and
+// select-free: r_i = s_i * rcp(g_i) is formed for every row and folded in by
+// integer min over its bit pattern --
+//   lambda_max = min over r >= 0 (g > 0): the unsigned min of the bits, where
+//     every negative float (sign bit set) and NaN ranks above +Inf;
+//   lambda_min = max over r <= 0 (g < 0): the signed min of the bits, where
+//     every non-negative float ranks above -Inf and, among negative floats,
+//     a smaller magnitude gives a smaller signed integer (-0 is the least).
+// g = 0 gives r = +-Inf or NaN, which never wins; s = 0 gives r = +0 (g > 0)
+// or -0 (g < 0), a chord end at the point itself.  The result is the exact
+// min (max) of the rounded ratios whatever the order or split of the scan,
+// so different launch shapes give the same bits.
 struct ChordAcc {
-  float lo, hi, chk;
+  unsigned int hib;   // bits of lambda_max (starts at +Inf)
+  int lob;            // bits of lambda_min (starts at -Inf)
+  float chk;
 
   __device__ __forceinline__ void init() {
-    lo = -INFINITY;
-    hi = INFINITY;
+    hib = 0x7f800000u;
+    lob = static_cast<int>(0xff800000u);
     chk = 0.0f;
   }
-  // g > 0: upper bound lambda_max; g < 0: lower bound lambda_min; g == 0
-  // bounds neither side.  s is the clamped slack (s >= 0).
   __device__ __forceinline__ void add(float ss, float gg) {
-    const float r = __fdividef(ss, gg);
-    hi = fminf(hi, gg > 0.0f ? r : INFINITY);
-    lo = fmaxf(lo, gg < 0.0f ? r : -INFINITY);
+    float rg;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rg) : "f"(gg));
+    const float r = ss * rg;
+    hib = min(hib, __float_as_uint(r));
+    lob = min(lob, __float_as_int(r));
   }
   // Non-finite detector: stays 0 unless some value is Inf or NaN.
   __device__ __forceinline__ void check(float v) { chk = fmaf(v, 0.0f, chk); }
-  __device__ __forceinline__ float lo_all() const { return lo; }
-  __device__ __forceinline__ float hi_all() const { return hi; }
+  __device__ __forceinline__ float lo_all() const { return __int_as_float(lob); }
+  __device__ __forceinline__ float hi_all() const { return __uint_as_float(hib); }
   __device__ __forceinline__ bool finite() const { return chk == 0.0f; }
 };
 
@@ -338,19 +347,20 @@ __device__ __forceinline__ void slack32(float (&v)[32], const float* bS, float w
     const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      acc.check(v[4 * i + j]);
-      v[4 * i + j] = fmaxf(fmaf(-v[4 * i + j], ws, bb[j]), 0.0f);
+      const float sv = fmaf(-v[4 * i + j], ws, bb[j]);
+      acc.check(sv);
+      v[4 * i + j] = fmaxf(sv, 0.0f);
     }
   }
 }
 
 // The chord scan over 32 rows: slacks s (from slack32) against G = D A^T.
+// G needs no per-row check: its FP16 operands are finite (the direction
+// split flags any value beyond the FP16 range) and so is every sum of their
+// products.
 __device__ __forceinline__ void scan32(const float (&s)[32], const float (&g)[32], ChordAcc& acc) {
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    acc.check(g[c]);
-    acc.add(s[c], g[c]);
-  }
+  for (int c = 0; c < 32; ++c) acc.add(s[c], g[c]);
 }
 
 template <int kThreads>

@@ -47,6 +47,7 @@ struct WalkerTail {
   const float* pc_delta; // n_ld
   const float* pc_U;     // n_ld x 32, zero beyond the rank
   int pc_rank;
+  int* status;           // MHAR_ST_NONFINITE if a split value leaves the FP16 range
 };
 
 // The tail's arguments for a context (`inter`: interleaved operand layout;
@@ -76,6 +77,7 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter, bool pc_draw = 
   t.pc_delta = c->d.pc_delta32;
   t.pc_U = c->d.pc_U32;
   t.pc_rank = c->pc_rank;
+  t.status = c->d.status;
   return t;
 }
 
@@ -99,9 +101,13 @@ __device__ __forceinline__ void ld8h(const __half* p, float* v) {
     v[2 * e + 1] = __half2float(__ushort_as_half(static_cast<unsigned short>(w[e] >> 16)));
   }
 }
-// Splits 8 values into FP16 hi / lo halves and stores both 16-byte chunks.
-__device__ __forceinline__ void split_store8(const float* v, __half* hi_dst, __half* lo_dst) {
+// Splits 8 values into FP16 hi / lo halves and stores both 16-byte chunks;
+// true if a value is non-finite or beyond the FP16 range.
+__device__ __forceinline__ bool split_store8(const float* v, __half* hi_dst, __half* lo_dst) {
   uint32_t h[4], l[4];
+  bool bad = false;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) bad |= !(fabsf(v[e]) <= kHalfMax);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const __half h0 = __float2half_rn(v[2 * e]);
@@ -113,6 +119,7 @@ __device__ __forceinline__ void split_store8(const float* v, __half* hi_dst, __h
   }
   *reinterpret_cast<uint4*>(hi_dst) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(lo_dst) = make_uint4(l[0], l[1], l[2], l[3]);
+  return bad;
 }
 
 }  // namespace tail_detail
@@ -217,7 +224,7 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
         v[e] = acc * (1.0f / t.sigma[i]);
       }
     }
-    split_store8(v, Dh + o, Dl + o);
+    if (split_store8(v, Dh + o, Dl + o)) atomicOr(t.status, MHAR_ST_NONFINITE);
   }
 }
 
@@ -327,7 +334,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
         v[e] = i < t.n ? (hi[e] + lo[e]) * inv / t.sigma[i] : 0.0f;
       }
     }
-    split_store8(v, t.Xh + o, t.Xl + o);
+    if (split_store8(v, t.Xh + o, t.Xl + o)) atomicOr(t.status, MHAR_ST_NONFINITE);
   }
 }
 
