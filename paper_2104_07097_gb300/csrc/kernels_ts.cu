@@ -45,7 +45,7 @@ using namespace tc;
 
 constexpr int kTile = 128;                           // MMA N: rows of A per tile
 constexpr int kSlotBytes = kTile * kTcKChunk * 2;    // 128 x 64 FP16 = 16 KB
-constexpr int kSlots = 12;
+constexpr int kSlots = 8;                            // two tiles of A (hi, lo) ahead
 constexpr int kEpiWarps = 16;
 constexpr int kThreadsTs = (2 + kEpiWarps) * 32;
 constexpr int kMaxCluster = 8;
@@ -70,7 +70,7 @@ struct TsParams {
   WalkerTail wt;            // walker-side work (walker_tail.cuh)
 };
 
-struct TsTail {
+struct alignas(16) TsTail {
   uint64_t a_full[kSlots];
   uint64_t a_empty[kSlots];
   uint64_t p_full, p_empty;    // P accumulator: MMAs done / copied out
@@ -82,11 +82,15 @@ struct TsTail {
   float recv_lo[kMaxCluster][kWalkers];
   float recv_hi[kMaxCluster][kWalkers];
   float theta_s[kWalkers];
+  double theta_u[kWalkers];           // the chord's uniform u (Philox stream 1), drawn early
   unsigned int red[kWalkers];
   float gs[kWalkers * kMaxPcRank];    // low-rank normals of a preconditioned draw
 };
 
-constexpr size_t kSmemTs = 1024 + static_cast<size_t>(kSlots) * kSlotBytes + sizeof(TsTail);
+// The walker-side items staged at kernel start: one slot per epilogue thread.
+constexpr size_t kStageBytes = static_cast<size_t>(kEpiWarps) * 32 * kTailStageBytes;
+constexpr size_t kSmemTs =
+    1024 + static_cast<size_t>(kSlots) * kSlotBytes + sizeof(TsTail) + kStageBytes;
 static_assert(kSmemTs <= 232448, "recompute_ts_kernel exceeds the shared memory of a CTA");
 
 __device__ __forceinline__ void st_dsmem(float* local, uint32_t rank, float v) {
@@ -145,6 +149,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   TsTail* tail = reinterpret_cast<TsTail*>(base + kSlots * kSlotBytes);
+  uint8_t* stage = reinterpret_cast<uint8_t*>(tail + 1);   // 16-byte aligned
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   TailItem tail_item;  // the epilogue threads' first tail item
@@ -285,6 +290,17 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int cg = e >> 2;              // 32-column group of each 128-column tile
     const float* bS_rows = p.bS + row_base + cg * 32;
     if (lane == 0 && ntiles > 0) prefetch_l1(bS_rows);
+    // This thread's walker-side item, copied to shared memory in the background.
+    walker_tail_stage<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
+                                      static_cast<int>(threadIdx.x) - 64,
+                                      stage + (threadIdx.x - 64) * kTailStageBytes);
+    if (cg == 0) {
+      // The chord's uniform does not depend on the chord: draw it now.
+      const int kk = strip * kWalkers + q * 32 + lane;
+      const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(kk), 0u,
+                                kStreamChord);
+      tail->theta_u[q * 32 + lane] = open_unit_f64(w.x);
+    }
     if (p.wt.draw)
       walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
                                        w_begin, w_count, static_cast<int>(threadIdx.x) - 64,
@@ -335,13 +351,15 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
 
   // Every push is visible after this barrier; no remote access follows it.
-  // Between its arrive and its wait the epilogue loads its first tail item
-  // (the loads do not depend on theta), so their latency overlaps the barrier.
+  // Between its arrive and its wait the epilogue reads its first tail item
+  // back from shared memory (staged at kernel start; it does not depend on
+  // theta).
   tc_fence_before();
   cluster_arrive();
   if (warp >= 2)
-    walker_tail_prefetch<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
-                                         static_cast<int>(threadIdx.x) - 64, tail_item);
+    walker_tail_unstage<kEpiWarps * 32>(p.wt, strip, p.z, w_begin, w_count,
+                                        static_cast<int>(threadIdx.x) - 64,
+                                        stage + (threadIdx.x - 64) * kTailStageBytes, tail_item);
   cluster_wait();
   if (warp == 1) {
     tc_fence_after();
@@ -367,9 +385,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       } else if (L > H) {
         flag = MHAR_ST_STALL;
       } else {
-        const U4 w = philox_block(p.seed, step, p.walker0 + static_cast<uint32_t>(k), 0u,
-                                  kStreamChord);
-        const double u = open_unit_f64(w.x);
+        const double u = tail->theta_u[wl];
         t = static_cast<float>(static_cast<double>(L) +
                                u * (static_cast<double>(H) - static_cast<double>(L)));
       }
@@ -387,8 +403,13 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
   if (warp >= 2) {
     named_bar<kEpiWarps * 32>();
+    // The stage is free again (its items are in registers): route the moved
+    // rows through it when they fit.
+    const bool rows_fit = static_cast<size_t>(2 * w_count) * tail_row_stride(p.wt.n_ld) *
+                              sizeof(float) <= kStageBytes;
     walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count, tail->theta_s,
-                                tail->red, static_cast<int>(threadIdx.x) - 64, tail_item);
+                                tail->red, static_cast<int>(threadIdx.x) - 64, tail_item,
+                                rows_fit ? reinterpret_cast<float*>(stage) : nullptr);
   }
 }
 

@@ -157,6 +157,66 @@ __device__ __forceinline__ void walker_tail_prefetch(const WalkerTail& t, int cu
   r.valid = 1;
 }
 
+// The same item staged in shared memory instead: at kernel start each thread
+// copies its first item's x hi, x lo (8 floats each) and direction pair (8
+// FP16 each) with asynchronous 16-byte copies (cp.async, no registers held),
+// into its own kTailStageBytes slot; after the chord it reads them back with
+// no global-memory latency on the walker-side path.  112-byte slots keep the
+// 16-byte accesses of 8 consecutive threads on distinct banks.
+constexpr int kTailStageBytes = 112;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+template <int kThreads>
+__device__ __forceinline__ void walker_tail_stage(const WalkerTail& t, int cur, int strip, int z,
+                                                  int w_begin, int w_count, int tid,
+                                                  uint8_t* slot) {
+  using namespace tail_detail;
+  const int chunks = (t.n + 7) >> 3;
+  if (w_count <= 0 || tid >= w_count * chunks) return;
+  const int c = tid / w_count, wo = tid - c * w_count;
+  const int k = strip * tc::kWalkers + w_begin + wo;
+  if (k >= z) return;
+  const int i0 = 8 * c;
+  const size_t xr = static_cast<size_t>(k) * t.n_ld + i0;
+  const size_t o = op_off(k, i0, t.k_pad, t.z_ld, t.inter);
+  cp_async16(slot, t.Xhi + xr);
+  cp_async16(slot + 16, t.Xhi + xr + 4);
+  cp_async16(slot + 32, t.Xlo + xr);
+  cp_async16(slot + 48, t.Xlo + xr + 4);
+  cp_async16(slot + 64, t.Dh[cur] + o);
+  cp_async16(slot + 80, t.Dl[cur] + o);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int kThreads>
+__device__ __forceinline__ void walker_tail_unstage(const WalkerTail& t, int strip, int z,
+                                                    int w_begin, int w_count, int tid,
+                                                    const uint8_t* slot, TailItem& r) {
+  using namespace tail_detail;
+  const int chunks = (t.n + 7) >> 3;
+  r.valid = 0;
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (w_count <= 0 || tid >= w_count * chunks) return;
+  const int c = tid / w_count, wo = tid - c * w_count;
+  const int k = strip * tc::kWalkers + w_begin + wo;
+  if (k >= z) return;
+  const int i0 = 8 * c;
+  float dh[8], dl[8];
+  ld8(reinterpret_cast<const float*>(slot), r.hi);
+  ld8(reinterpret_cast<const float*>(slot + 32), r.lo);
+  ld8h(reinterpret_cast<const __half*>(slot + 64), dh);
+  ld8h(reinterpret_cast<const __half*>(slot + 80), dl);
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    r.d[e] = i0 + e < t.n ? (t.unit_sigma ? dh[e] + dl[e] : (dh[e] + dl[e]) * t.sigma[i0 + e]) : 0.0f;
+  r.valid = 1;
+}
+
 // (0): run by kThreads threads (tid = 0..kThreads-1, sharing named barrier 1
 // when preconditioned); `next_step` = s + 1.  With a preconditioner the
 // direction is d = delta .* h + U g, g the walker's rank-r normals (Philox
@@ -228,17 +288,26 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
   }
 }
 
+// Shared scratch that walker_tail can route the moved points through, so
+// that their rows go to global memory as whole coalesced lines (an item's 32
+// bytes per thread, one row per walker, would otherwise be a separate
+// transaction per thread): 2 w_count rows of tail_row_stride(n_ld) floats.
+__host__ __device__ constexpr int tail_row_stride(int n_ld) { return n_ld + 4; }
+
 // (1) and (2): run by kThreads threads (tid = 0..kThreads-1) that share named
 // barrier 1.  theta_s: the strip's 128 theta values (shared memory); red:
 // w_count words of shared scratch; `cur` = s % 2.  `first`: item tid,
-// prefetched; items tid + kThreads, ... are loaded here.
+// prefetched; items tid + kThreads, ... are loaded here.  `xrows`: null, or
+// the scratch above when every item is a first item (items <= kThreads).
 template <int kThreads>
 __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int w_begin,
                             int w_count, const float* theta_s, unsigned int* red, int tid,
-                            TailItem& first) {
+                            TailItem& first, float* xrows = nullptr) {
   using namespace tail_detail;
   const int chunks = (t.n + 7) >> 3;
   const int items = w_count * chunks;
+  const int rs = tail_row_stride(t.n_ld);
+  if (items > kThreads) xrows = nullptr;
   for (int w = tid; w < w_count; w += kThreads) red[w] = 0u;
   tc::named_bar<kThreads>();
 
@@ -282,8 +351,17 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
           lo[e] = fmaf(-th, dlt, lo[e]);
         }
       }
-      st8(t.Xhi + xr, hi);
-      st8(t.Xlo + xr, lo);
+      if (xrows != nullptr) {
+        // Into the walker's row in shared memory; stored below, coalesced.
+        st8(xrows + wo * rs + i0, hi);
+        st8(xrows + (w_count + wo) * rs + i0, lo);
+      } else {
+        st8(t.Xhi + xr, hi);
+        st8(t.Xlo + xr, lo);
+      }
+    } else if (xrows != nullptr) {
+      st8(xrows + wo * rs + i0, hi);
+      st8(xrows + (w_count + wo) * rs + i0, lo);
     }
     if (cached) {
 #pragma unroll
@@ -302,6 +380,19 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
     atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
   }
   tc::named_bar<kThreads>();
+  if (xrows != nullptr) {
+    // The moved rows, 16 bytes per thread, consecutive threads along a row.
+    const int q4 = 2 * chunks;   // float4s of a row that items cover
+    for (int f = tid; f < 2 * w_count * q4; f += kThreads) {
+      const int row = f / q4, c4 = f - row * q4;
+      const int wo = row < w_count ? row : row - w_count;
+      const int k = strip * tc::kWalkers + w_begin + wo;
+      if (k >= z) continue;
+      const float4 v = *reinterpret_cast<const float4*>(xrows + row * rs + 4 * c4);
+      float* dst = (row < w_count ? t.Xhi : t.Xlo) + static_cast<size_t>(k) * t.n_ld + 4 * c4;
+      *reinterpret_cast<float4*>(dst) = v;
+    }
+  }
 
   // (2) FP16 pair of the scaled point.
   for (int it = tid; it < items; it += kThreads) {
