@@ -138,10 +138,11 @@ __device__ __forceinline__ void ts_g_chunk(TsTail* tail, uint8_t* base, int it0,
   mma_commit(&tail->a_empty[il % kSlots]);
 }
 
-// LAST: K steps (16 FP16 each) in the last 64-column chunk of A's rows, 1..4;
-// the other chunks have 4.  A compile-time count keeps the MMA runs free of
-// branches (the issuing thread's stream between MMAs is the limiter).
-template <int LAST>
+// KCH: 64-column K chunks of A's rows (1 or 2: n <= 128); LAST: K steps (16
+// FP16 each) in the last chunk, 1..4, the other chunk having 4.  A
+// compile-time K structure makes each pass one straight run of MMAs (the
+// issuing thread's stream between MMAs is the limiter).
+template <int KCH, int LAST>
 __global__ void __launch_bounds__(kThreadsTs, 1)
 recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const TsParams p) {
@@ -237,7 +238,8 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       int it = 0;
       for (int nt = 0; nt < ntiles; ++nt) {
         const int yr = row_base + nt * kTile;
-        for (int kc = 0; kc < p.k_chunks; ++kc) {
+#pragma unroll
+        for (int kc = 0; kc < KCH; ++kc) {
           for (int half = 0; half < 2; ++half, ++it) {
             const int s = it % kSlots;
             if (it >= kSlots) mbar_wait(&tail->a_empty[s], ((it / kSlots) - 1) & 1, timed_out, p.err);
@@ -260,23 +262,21 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       const uint32_t g_tmem = tmem;
       const uint32_t p_tmem = tmem + 128u;
       int it0 = 0;   // first slot use of the tile
-      for (int nt = 0; nt < ntiles; ++nt, it0 += 2 * p.k_chunks) {
+      for (int nt = 0; nt < ntiles; ++nt, it0 += 2 * KCH) {
         // P pass: X hi, X lo times A hi; X hi times A lo.  The accumulator is
         // free once the epilogue has copied the previous tile's P out.
         if (nt >= 1) mbar_wait(&tail->p_empty, (nt - 1) & 1, timed_out, p.err);
         tc_fence_after();
-        for (int kc = 0; kc + 1 < p.k_chunks; ++kc)
-          ts_p_chunk<4>(tail, base, it0, kc, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
-        ts_p_chunk<LAST>(tail, base, it0, p.k_chunks - 1, p_tmem, op_xh, op_xl, idesc, timed_out,
-                         p.err);
+        if constexpr (KCH == 2)
+          ts_p_chunk<4>(tail, base, it0, 0, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
+        ts_p_chunk<LAST>(tail, base, it0, KCH - 1, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
         mma_commit(&tail->p_full);
         // G pass: D hi, D lo times A hi; D hi times A lo.  Each slot is
         // released after its last use here.
         if (nt >= 1) mbar_wait(&tail->g_empty, (nt - 1) & 1, timed_out, p.err);
         tc_fence_after();
-        for (int kc = 0; kc + 1 < p.k_chunks; ++kc)
-          ts_g_chunk<4>(tail, base, it0, kc, g_tmem, op_dh, op_dl, idesc);
-        ts_g_chunk<LAST>(tail, base, it0, p.k_chunks - 1, g_tmem, op_dh, op_dl, idesc);
+        if constexpr (KCH == 2) ts_g_chunk<4>(tail, base, it0, 0, g_tmem, op_dh, op_dl, idesc);
+        ts_g_chunk<LAST>(tail, base, it0, KCH - 1, g_tmem, op_dh, op_dl, idesc);
         mma_commit(&tail->g_full);
       }
     }
@@ -432,6 +432,13 @@ TsShape ts_shape(const mhar_ctx* c, const TcPlan* plan) {
   return s;
 }
 
+// Instantiations by (chunks, last-chunk K steps): index 4 (KCH - 1) + LAST - 1.
+using TsKernel = void (*)(CUtensorMap, CUtensorMap, TsParams);
+constexpr TsKernel kTsKernels[8] = {
+    recompute_ts_kernel<1, 1>, recompute_ts_kernel<1, 2>, recompute_ts_kernel<1, 3>,
+    recompute_ts_kernel<1, 4>, recompute_ts_kernel<2, 1>, recompute_ts_kernel<2, 2>,
+    recompute_ts_kernel<2, 3>, recompute_ts_kernel<2, 4>};
+
 }  // namespace
 
 bool ts_eligible(const mhar_ctx* c) { return c->k_pad <= 128; }
@@ -444,8 +451,7 @@ int ts_prepare(mhar_ctx* c) {
     return MHAR_E_CUDA;
   }
   cudaError_t e = cudaSuccess;
-  for (auto* k : {recompute_ts_kernel<1>, recompute_ts_kernel<2>, recompute_ts_kernel<3>,
-                  recompute_ts_kernel<4>})
+  for (TsKernel k : kTsKernels)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kSmemTs));
@@ -501,12 +507,8 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  switch (last_chunk_steps(p.kdim, p.k_chunks)) {
-    case 1: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<1>, plan->ah64, plan->al64, p);
-    case 2: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<2>, plan->ah64, plan->al64, p);
-    case 3: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<3>, plan->ah64, plan->al64, p);
-    default: return cudaLaunchKernelEx(&cfg, recompute_ts_kernel<4>, plan->ah64, plan->al64, p);
-  }
+  const TsKernel k = kTsKernels[4 * (p.k_chunks - 1) + last_chunk_steps(p.kdim, p.k_chunks) - 1];
+  return cudaLaunchKernelEx(&cfg, k, plan->ah64, plan->al64, p);
 }
 
 }  // namespace mhar
