@@ -52,6 +52,14 @@ WORKLOADS = {
 }
 WORKLOAD = dict(WORKLOADS["rand100x2000"])
 METRIC = "walker-steps/s"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu --set full capture of this workload (the
+# commands are in profiles/); cold-cache per launch, as ncu replays it.  An
+# entry must be dropped when its kernel changes.
+PROFILED_TRAFFIC = {
+    ("rand100x2000", "recompute_ts_kernel"): 9.556e6,
+    ("illcond500x10000", "recompute_sk_kernel"): 196.325e6 + 83.136e6,
+}
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
 BATCH_WORKLOAD = dict(name="batch256", count=256, seed=4, z=512, iterations=1000, tune_iters=8)
@@ -398,7 +406,7 @@ def main() -> None:
         peak = peaks["bf16_tflops_sustained"]
         roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
                     "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
-                    "traffic": None,
+                    "traffic": PROFILED_TRAFFIC.get((WORKLOAD["name"], s.kernel_name())),
                     "kernel": s.kernel_name(),
                     "algorithmic": f"{2 * nprod} m n tensor flops per walker-step ({nprod} FP16 products)",
                     "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}

@@ -40,7 +40,9 @@ extern "C" {
 #define MHAR_E_UNBOUNDED       -3  /* some walker met a chord open on one side
                                       (the body is unbounded, Section 2.1
                                       assumes bounded bodies)                */
-#define MHAR_E_NONFINITE       -4  /* a non-finite slack, ratio or point     */
+#define MHAR_E_NONFINITE       -4  /* a non-finite slack, ratio or point, or
+                                       (tensor-core modes) a point or direction
+                                       beyond the FP16 range of its operands  */
 #define MHAR_E_CUDA            -5  /* CUDA runtime / driver failure, or no
                                       sm_103 device                          */
 #define MHAR_E_RANK            -6  /* A_E A_E^T not positive definite        */
