@@ -307,7 +307,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
   const int chunks = (t.n + 7) >> 3;
   const int items = w_count * chunks;
   const int rs = tail_row_stride(t.n_ld);
-  if (items > kThreads) xrows = nullptr;
+  if (items > kThreads || chunks > 16) xrows = nullptr;
   for (int w = tid; w < w_count; w += kThreads) red[w] = 0u;
   tc::named_bar<kThreads>();
 
@@ -338,12 +338,15 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
       }
     }
     if (th != 0.0f) {
+      // Coordinates past n have x = 0 and d = 0, for which the update is a
+      // no-op: no per-coordinate branch.
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = i0 + e;
-        if (i >= t.n) continue;
-        df_axpy(hi[e], lo[e], th, d[e]);
-        if (t.corr != nullptr) {
+      for (int e = 0; e < 8; ++e) df_axpy(hi[e], lo[e], th, d[e]);
+      if (t.corr != nullptr) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int i = i0 + e;
+          if (i >= t.n) continue;
           float dlt = 0.0f;
           for (int q = 0; q < t.mE; ++q)
             dlt = fmaf(t.AE32[static_cast<size_t>(q) * t.n_ld + i],
@@ -370,8 +373,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
     float mx = 0.0f;
     if (t.unit_sigma) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]));
+      for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(hi[e]));   // x = 0 past n
     } else {
 #pragma unroll
       for (int e = 0; e < 8; ++e)
@@ -381,15 +383,16 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
   }
   tc::named_bar<kThreads>();
   if (xrows != nullptr) {
-    // The moved rows, 16 bytes per thread, consecutive threads along a row.
+    // The moved rows: a warp per row, 16 bytes per lane along it (xrows is
+    // only used when a row is at most 32 float4s: n <= 128).
     const int q4 = 2 * chunks;   // float4s of a row that items cover
-    for (int f = tid; f < 2 * w_count * q4; f += kThreads) {
-      const int row = f / q4, c4 = f - row * q4;
+    const int lane = tid & 31;
+    for (int row = tid >> 5; row < 2 * w_count; row += kThreads / 32) {
       const int wo = row < w_count ? row : row - w_count;
       const int k = strip * tc::kWalkers + w_begin + wo;
-      if (k >= z) continue;
-      const float4 v = *reinterpret_cast<const float4*>(xrows + row * rs + 4 * c4);
-      float* dst = (row < w_count ? t.Xhi : t.Xlo) + static_cast<size_t>(k) * t.n_ld + 4 * c4;
+      if (k >= z || lane >= q4) continue;
+      const float4 v = *reinterpret_cast<const float4*>(xrows + row * rs + 4 * lane);
+      float* dst = (row < w_count ? t.Xhi : t.Xlo) + static_cast<size_t>(k) * t.n_ld + 4 * lane;
       *reinterpret_cast<float4*>(dst) = v;
     }
   }
@@ -415,15 +418,13 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
       ld8(t.Xhi + xr, hi);
       ld8(t.Xlo + xr, lo);
     }
+    // x = 0 and sigma = 1 past n: no per-coordinate branch.
     if (t.unit_sigma) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = i0 + e < t.n ? (hi[e] + lo[e]) * inv : 0.0f;
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv;
     } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = i0 + e;
-        v[e] = i < t.n ? (hi[e] + lo[e]) * inv / t.sigma[i] : 0.0f;
-      }
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv / t.sigma[i0 + e];
     }
     if (split_store8(v, t.Xh + o, t.Xl + o)) atomicOr(t.status, MHAR_ST_NONFINITE);
   }
