@@ -275,7 +275,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
           // Both the slack and G are in units of the row's power-of-two
           // scale, so their ratio is the paper's lambda_i unchanged.
           const float gg = g[c];
-          const float ss = fmaxf(s_cur[16 * half + c], 0.0f);
+          const float ss = clamp_slack(s_cur[16 * half + c]);
           acc.check(gg);
           acc.add(ss, gg);
         }

@@ -301,8 +301,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 //   lambda_min = max over r <= 0 (g < 0): the signed min of the bits, where
 //     every non-negative float ranks above -Inf and, among negative floats,
 //     a smaller magnitude gives a smaller signed integer (-0 is the least).
-// g = 0 gives r = +-Inf or NaN, which never wins; s = 0 gives r = +0 (g > 0)
-// or -0 (g < 0), a chord end at the point itself.  The result is the exact
+// g = 0 gives r = +-Inf or NaN, which never wins; s = +0 (clamp_slack) gives
+// r = +0 (g > 0) or -0 (g < 0), a chord end at the point itself.  The result is the exact
 // min (max) of the rounded ratios whatever the order or split of the scan,
 // so different launch shapes give the same bits.
 struct ChordAcc {
@@ -335,6 +335,13 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Slack clamped at +0: an integer max over the bit pattern sends every
+// negative value, -0 included, to +0 (the chord scan's sign rule needs s to
+// be +0, never -0: s = -0 over g > 0 would read as a lambda_min).
+__device__ __forceinline__ float clamp_slack(float s) {
+  return __int_as_float(max(__float_as_int(s), 0));
+}
+
 // Slack of one walker at 32 rows from its P = X A^T columns (in place):
 // s_i = b_i - p_i w, clamped at 0 (Lemma 4.2's s = b - A x, in the row and
 // walker scales of the FP16 operands).  bS points at the 32 rows' b_i / scale_i
@@ -349,7 +356,7 @@ __device__ __forceinline__ void slack32(float (&v)[32], const float* bS, float w
     for (int j = 0; j < 4; ++j) {
       const float sv = fmaf(-v[4 * i + j], ws, bb[j]);
       acc.check(sv);
-      v[4 * i + j] = fmaxf(sv, 0.0f);
+      v[4 * i + j] = clamp_slack(sv);
     }
   }
 }

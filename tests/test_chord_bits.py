@@ -17,9 +17,15 @@ INF_BITS = np.uint32(0x7F800000)
 NEG_INF_BITS = np.int32(np.uint32(0xFF800000).view(np.int32))
 
 
+def clamp_slack(s):
+    """The kernels' clamp: integer max over the bit pattern (negatives and -0 to +0)."""
+    b = np.asarray(s, np.float32).view(np.int32)
+    return np.maximum(b, 0).astype(np.int32).view(np.float32)
+
+
 def bit_chord(s, g):
     """The kernels' reduction (a reciprocal then a product, as in FP32)."""
-    s = np.asarray(s, np.float32)
+    s = clamp_slack(s)
     g = np.asarray(g, np.float32)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         r = (s * (np.float32(1.0) / g)).astype(np.float32)
@@ -32,7 +38,7 @@ def bit_chord(s, g):
 
 def plain_chord(s, g):
     """Algorithm 2's chord from the same rounded ratios, by definition."""
-    s = np.asarray(s, np.float32)
+    s = np.maximum(np.asarray(s, np.float32), np.float32(0.0)) + np.float32(0.0)
     g = np.asarray(g, np.float32)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         r = (s * (np.float32(1.0) / g)).astype(np.float32)
@@ -53,6 +59,8 @@ def plain_chord(s, g):
     ([1.0, 5.0], [1e30, -1e30]),                   # huge g: ratio near 0
     ([3.0], [1.0]),                                # open below
     ([3.0], [-1.0]),                               # open above
+    ([-0.0, 1.0], [2.0, -1.0]),                    # s = -0 over g > 0: lambda_max = +0
+    ([-1e-7, 2.0], [-3.0, 1.0]),                   # negative slack clamps to +0
 ])
 def test_edge_cases(case):
     s, g = case
