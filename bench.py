@@ -58,7 +58,7 @@ METRIC = "walker-steps/s"
 # entry must be dropped when its kernel changes.
 PROFILED_TRAFFIC = {
     ("rand100x2000", "recompute_ts_kernel"): 9.544e6,
-    ("illcond500x10000", "recompute_sk_kernel"): 181.684e6 + 82.187e6,
+    ("illcond500x10000", "recompute_sk_kernel"): 249.624e6 + 82.901e6,
 }
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
