@@ -46,7 +46,7 @@ extern "C" {
 #define MHAR_E_CUDA            -5  /* CUDA runtime / driver failure, or no
                                       sm_103 device                          */
 #define MHAR_E_RANK            -6  /* A_E A_E^T not positive definite        */
-#define MHAR_E_UNSUPPORTED     -7  /* size or mode this build does not cover */
+#define MHAR_E_UNSUPPORTED     -7  /* size or mode the library does not cover */
 
 /* ---- arithmetic modes -------------------------------------------------- */
 /* MHAR_FP64: every step in FP64 on CUDA cores; the slack b - A x and A d are

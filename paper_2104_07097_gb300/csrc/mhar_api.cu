@@ -582,7 +582,7 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
     set_err(c, "bad pointer or size (m=%d n=%d mE=%d)", m, n, mE);
     rc = MHAR_E_ARG;
   } else if (mE > kMaxEqualities || mE >= n) {
-    set_err(c, "this build handles 0 <= mE <= %d and mE < n (got mE=%d, n=%d)", kMaxEqualities,
+    set_err(c, "the library handles 0 <= mE <= %d and mE < n (got mE=%d, n=%d)", kMaxEqualities,
             mE, n);
     rc = MHAR_E_UNSUPPORTED;
   } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
