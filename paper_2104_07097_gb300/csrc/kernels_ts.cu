@@ -11,8 +11,8 @@
 //     operand of every MMA (tcgen05.mma with A in TMEM), so shared memory
 //     only feeds the rows of A -- half the operand bytes per MMA of the
 //     shared-memory form, which is what limited that form;
-//   * the rows of A stream in 128-row tiles (MMA N = 128) through twelve
-//     16 KB slots (hi and lo staged separately), more than a tile ahead;
+//   * the rows of A stream in 128-row tiles (MMA N = 128) through eight
+//     16 KB slots (hi and lo staged separately), up to two tiles ahead;
 //   * the G and P accumulators of a tile (128 + 128 columns) take the other
 //     256 TMEM columns.  A tile's MMAs run as two passes, P first, then G,
 //     each with its own full / empty barrier pair: the epilogue copies P to
@@ -24,6 +24,11 @@
 // the SM's whole shared-memory bandwidth at full rate, so the loads of the
 // other warps and the TMA writes slow it; with A in tensor memory it needs
 // half.
+//   * the walker-side inputs of each epilogue thread (its item of x hi / lo
+//     and the direction pair) are copied into shared memory at kernel start
+//     (cp.async), so the move after the chord reads no global memory; the
+//     chord's uniform is drawn early, and the moved rows reach global memory
+//     as whole lines through the same shared-memory stage.
 // The cluster layout (C CTAs along the rows, 128 walkers per CTA), the pushed
 // partial chords, the walker-side work (walker_tail.cuh) and the bounded
 // waits are those of kernels_rc.cu.
