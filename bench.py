@@ -73,6 +73,7 @@ ESS_MODERATE = dict(name="illcond40x400", n=40, m=400, seed=5, smin=1e-2, z=4096
                     iterations=5000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
                     snapshots=5, power_iters=4)
 REF_SAMPLE = dict(walkers=64, iterations=20)
+RHAT_LIMIT = 1.05
 
 
 def polytope():
@@ -154,16 +155,39 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded)}
 
 
-def cpu_baseline(p) -> dict:
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+def _oracle_shard(args):
+    """One process of the all-cores oracle run: walkers w0 .. w0 + count - 1."""
+    A, b, x0, count, w0, steps = args
     import oracle
-    zs, ts = CPU_SAMPLE["walkers"], CPU_SAMPLE["iterations"]
-    X0 = np.tile(p.x0, (zs, 1))
     t0 = time.perf_counter()
-    oracle.mhar_run(p.A, p.b, X0, steps=ts, thin=0, seed=0)
-    dt = time.perf_counter() - t0
-    return {"value": zs * ts / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{zs} walkers x {ts} iterations of {WORKLOAD['name']} (FP64 oracle, 1 thread, {dt:.1f} s)"}
+    oracle.mhar_run(A, b, np.tile(x0, (count, 1)), steps=steps, thin=0, seed=0, walker0=w0)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p) -> dict:
+    """The FP64 oracle as it stands on the host's cores: one process per core
+    (started with spawn), each on its own range of walkers (walkers are
+    independent and the generator is counter-based, so the shards are one
+    ensemble), and the same single-threaded run on one core."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    zs, ts = CPU_SAMPLE["walkers"], CPU_SAMPLE["iterations"]
+    t0 = time.perf_counter()
+    oracle.mhar_run(p.A, p.b, np.tile(p.x0, (zs, 1)), steps=ts, thin=0, seed=0)
+    dt1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    jobs = [(p.A, p.b, p.x0, zs, k * zs, ts) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_shard, jobs[:1])          # start-up (imports, library load)
+        t0 = time.perf_counter()
+        pool.map(_oracle_shard, jobs)
+        dtn = time.perf_counter() - t0
+    return {"value": cores * zs * ts / dtn, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {zs} walkers x {ts} iterations of {WORKLOAD['name']} "
+                      f"(FP64 oracle, disjoint walker ranges, {dtn:.1f} s wall)",
+            "single_core": {"value": zs * ts / dt1, "cores": 1,
+                            "sample": f"{zs} walkers x {ts} iterations, 1 thread, {dt1:.1f} s"}}
 
 
 def run_reference(args) -> None:
@@ -217,9 +241,14 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
         torch.cuda.synchronize()
         secs = a.elapsed_time(b) / 1e3
         worst = max(bt.check(q).max_violation for q in range(len(bodies)))
+        # Untimed: an FP64 audit of every problem's first 256 walkers after
+        # each of 200 more iterations.
+        bt.set_audit(1, 256)
+        bt.run(200)
+        audited = max(bt.check(q).run_max_violation for q in range(len(bodies)))
     finally:
         bt.close()
-    flops = 12.0 * sum(p.m * p.n for p in bodies) * z * iters
+    flops = 4.0 * sum(p.m * p.n for p in bodies) * z * iters
     peak = peaks["bf16_tflops_sustained"]
     return {"workload": f"{B['name']}: {B['count']} random polytopes, n ~ U{{20..400}}, "
                         f"m ~ U{{2n..20n}}, z={z} each, {iters} iterations",
@@ -227,8 +256,13 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
             "seconds": secs, "cluster": C, "launches_per_iteration": 1,
             "create_seconds": create_s,
             "roofline": {"bound": "tensor", "achieved": flops / secs / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "frac": flops / secs / 1e12 / peak},
-            "max_violation": worst}
+                         "unit": "TFLOP/s", "frac": flops / secs / 1e12 / peak,
+                         "frac_pipe": 3 * flops / secs / 1e12 / peak,
+                         "algorithmic": "4 m n flops per walker-step (A x and A d); frac_pipe "
+                                        "counts the 12 m n of the FP16x3 products"},
+            "max_violation": worst,
+            "audit": {"iterations": 200, "walkers_per_problem": 256,
+                      "run_max_violation": audited}}
 
 
 def configs_leg(stream, torch, mhar, peaks) -> dict:
@@ -257,11 +291,19 @@ def configs_leg(stream, torch, mhar, peaks) -> dict:
                    "kernel": smp.kernel_name(), "max_violation": st.max_violation,
                    "eq_residual": st.eq_residual}
             if prec == "mixed_rs":
-                flops = 12.0 * p.m * p.n * z * iters
+                flops = 4.0 * p.m * p.n * z * iters
+                pk = peaks["bf16_tflops_sustained"]
                 leg["roofline"] = {"bound": "tensor", "achieved": flops / secs / 1e12,
-                                   "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                                   "frac": flops / secs / 1e12 / peaks["bf16_tflops_sustained"],
-                                   "note": "whole iteration incl. direction draw and projection"}
+                                   "peak": pk, "unit": "TFLOP/s", "frac": flops / secs / 1e12 / pk,
+                                   "frac_pipe": 3 * flops / secs / 1e12 / pk,
+                                   "note": "whole iteration incl. direction draw and projection; "
+                                           "4 m n flops per walker-step (frac_pipe: 12 m n)"}
+            smp.set_audit(1, min(z, 1024))
+            smp.run(100)
+            sa = smp.stats()
+            leg["audit"] = {"iterations": 100, "walkers": min(z, 1024),
+                            "run_max_violation": sa.run_max_violation,
+                            "run_eq_residual": sa.run_eq_residual}
             legs[name] = leg
     return legs
 
@@ -274,6 +316,12 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
     out = torch.empty((T // every, W, p.n), dtype=torch.float64, device="cuda")
     arms = {}
     kernel_roofline = None
+    # The first warm-up round of the learned arm walks with directions scaled
+    # by the coordinates' extents read off the constraints, 1 / max_i |a_ij|
+    # (a fixed diagonal law); every fit round then refits rank-32 + diagonal
+    # from the chain's own warm-up points.
+    diag0 = 1.0 / np.abs(p.A).max(axis=0)
+    diag0 /= diag0.max()
     for name, prec, learned in (("learned_mixed_rs", "mixed_rs", True),
                                 ("plain_mixed_rs", "mixed_rs", False),
                                 ("plain_fp32", "fp32", False)):
@@ -283,6 +331,7 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
             torch.cuda.synchronize()
             a.record(stream)
             if learned:
+                smp.set_preconditioner(diag0)
                 # Each round warms up with the previous round's directions and refits.
                 for _ in range(E["fit_rounds"]):
                     smp.fit_preconditioner(E["warmup"] // E["fit_rounds"], E["snapshots"],
@@ -296,28 +345,43 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
             st = smp.check()
             if name == "plain_mixed_rs":
                 kms = smp.time_kernels(16)
-                flops = 12.0 * p.m * p.n * z
+                flops = 4.0 * p.m * p.n * z
+                pk = peaks["bf16_tflops_sustained"]
                 kernel_roofline = {
                     "bound": "tensor", "kernel": smp.kernel_name(),
                     "ms_per_iteration": kms[1],
                     "achieved": flops / (kms[1] * 1e-3) / 1e12,
-                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                    "frac": flops / (kms[1] * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
-                    "algorithmic": "12 m n tensor flops per walker-step"}
+                    "peak": pk, "unit": "TFLOP/s",
+                    "frac": flops / (kms[1] * 1e-3) / 1e12 / pk,
+                    "frac_pipe": 3 * flops / (kms[1] * 1e-3) / 1e12 / pk,
+                    "algorithmic": "4 m n flops per walker-step (A x, A d); frac_pipe counts "
+                                   "the 12 m n of the FP16x3 products"}
+            # Untimed: FP64 audit of 1024 walkers after each of 200 more iterations.
+            smp.set_audit(1, min(z, 1024))
+            smp.run(200)
+            audited = smp.stats().run_max_violation
         trace = out.cpu().numpy()
         ess = diagnostics.ess_per_coordinate(trace) * (z / W)
+        rhat = diagnostics.split_rhat(trace)
         arms[name] = {"min_ess": float(ess.min()), "median_ess": float(np.median(ess)),
                       "seconds": secs, "min_ess_per_s": float(ess.min()) / secs,
                       "walker_steps_per_s": z * (E["warmup"] + T) / secs,
-                      "max_violation": st.max_violation}
+                      "max_split_rhat": float(rhat.max()),
+                      "converged": bool(rhat.max() < RHAT_LIMIT),
+                      "max_violation": st.max_violation,
+                      "audit": {"iterations": 200, "walkers": min(z, 1024),
+                                "run_max_violation": audited}}
     return {"workload": f"{E['name']} (axes scaled by s, log s ~ U[ln {E['smin']:g}, 0]) z={z}: "
                         f"{E['warmup']} warm-up + {T} iterations",
             "trace": f"{W} walkers, every {every}th iteration; ESS scaled by z/{W}; Geyer initial "
                      f"monotone sequence",
             "learned": f"rank {E['rank']} + diagonal, fitted on the device in {E['fit_rounds']} rounds "
                        f"of {E['warmup'] // E['fit_rounds']} warm-up iterations ({E['snapshots']} "
-                       f"snapshots, {E['power_iters']} power iterations each), then frozen; "
-                       f"warm-up and fits are inside the timed region",
+                       f"snapshots, {E['power_iters']} power iterations each), then frozen; the "
+                       f"first round's directions are scaled by 1 / max_i |a_ij|; warm-up and "
+                       f"fits are inside the timed region",
+            "convergence": f"split R_hat over coordinates < {RHAT_LIMIT} (trace of the "
+                           f"{T} iterations after warm-up)",
             "arms": arms,
             "roofline": kernel_roofline,
             "min_ess_per_s_learned_vs_plain_fp32":
@@ -397,19 +461,31 @@ def main() -> None:
     # Per-kernel device times (CUDA events around each launch, same stream).
     kms = s.time_kernels(128)
     st = s.check()
+    # Untimed: an FP64 audit of 1024 walkers after each of 256 more iterations.
+    s.set_audit(1, min(z, 1024))
+    s.run(256)
+    audited = s.stats().run_max_violation
+    s.set_audit(0, 0)
     peaks = load_peaks()
     m, n = p.m, p.n
     if args.precision in ("mixed", "mixed_rs"):
-        # FP16 products of 2 m n flops each per walker-step: 4 for A D in the
-        # stored-slack mode; 3 for A D + 3 for A X in the recompute mode.
-        nprod = 4 if args.precision == "mixed" else 6
-        flops = 2.0 * nprod * m * n * z
+        # The method's own work per walker-step: A d (2 m n flops) in the
+        # stored-slack mode, A x and A d (4 m n) in the recompute mode.  The
+        # tensor pipe runs FP16 products of 2 m n each: 4 (stored) or 6
+        # (recompute), reported as frac_pipe.
+        nmeth, nprod = (1, 4) if args.precision == "mixed" else (2, 6)
+        flops = 2.0 * nmeth * m * n * z
+        pipe = 2.0 * nprod * m * n * z
         peak = peaks["bf16_tflops_sustained"]
-        roofline = {"bound": "tensor", "achieved": flops / (kms[1] * 1e-3) / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "frac": flops / (kms[1] * 1e-3) / 1e12 / peak,
+        sec = kms[1] * 1e-3
+        roofline = {"bound": "tensor", "achieved": flops / sec / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / sec / 1e12 / peak,
+                    "frac_pipe": pipe / sec / 1e12 / peak,
                     "traffic": PROFILED_TRAFFIC.get((WORKLOAD["name"], s.kernel_name())),
                     "kernel": s.kernel_name(),
-                    "algorithmic": f"{2 * nprod} m n tensor flops per walker-step ({nprod} FP16 products)",
+                    "algorithmic": f"{2 * nmeth} m n flops per walker-step (the method's "
+                                   f"products); frac_pipe counts the {2 * nprod} m n flops of "
+                                   f"its {nprod} FP16 products",
                     "peak_source": f"{peaks['_source']} bf16 sustained (FP16 rate = BF16 rate)"}
     else:
         bytes_ = 2.0 * m * n * z * (8 if args.precision == "fp64" else 4)
@@ -466,7 +542,9 @@ def main() -> None:
                 "kernel_ms": {"directions": kms[0], "chord": kms[1], "refresh": kms[2]},
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
                 "feasibility": {"max_violation": st.max_violation, "refresh_drift": st.refresh_drift,
-                                "stalls": st.stalls},
+                                "stalls": st.stalls,
+                                "audit": {"iterations": 256, "walkers": min(z, 1024),
+                                          "run_max_violation": audited}},
                 "plain_fp32": plain}
         if world == 1 and not args.no_batch and args.precision == "mixed_rs":
             line["batched"] = batch_leg(stream, torch, mhar, peaks)

@@ -47,6 +47,13 @@ extern "C" {
                                       sm_103 device                          */
 #define MHAR_E_RANK            -6  /* A_E A_E^T not positive definite        */
 #define MHAR_E_UNSUPPORTED     -7  /* size or mode the library does not cover */
+#define MHAR_E_TIMEOUT         -8  /* a bounded wait inside a tensor-core
+                                      kernel expired (about 2 s): the pipeline
+                                      stalled; the iteration's results are not
+                                      to be trusted                          */
+#define MHAR_E_INFEASIBLE_DRIFT -9 /* MHAR_MIXED_F16X3: a periodic refresh
+                                      found the tracked slack further from
+                                      b - A x than its error bound allows    */
 
 /* ---- arithmetic modes -------------------------------------------------- */
 /* MHAR_FP64: every step in FP64 on CUDA cores; the slack b - A x and A d are
@@ -65,7 +72,24 @@ extern "C" {
  *   and the chord, moves the walkers, and prepares the next iteration's
  *   operands (and, without equalities or preconditioner, its directions).
  *   No slack is stored, so there is nothing to refresh and no drift;
- *   refresh_k is ignored. */
+ *   refresh_k is ignored.
+ *
+ * Feasibility in every mode.  Each chord end (Section 4.4) is computed from
+ * a slack lowered by a bound on its rounding error and from an a_i . d
+ * pushed away from zero by a bound on its own:
+ *     lambda = (s_i - e_s) / (g_i +- e_g),
+ *     e_s = K_i ||x / sigma||_2 + 3 u |b_i|,   e_g = K_i ||d / sigma||_2,
+ * with sigma the power-of-two column scales of A (largest entry of each
+ * column of A sigma in [0.5, 1) up to one common factor), u the unit
+ * roundoff, and K_i = gamma_{n+4} ||a_i sigma||_2 on CUDA cores (gamma_k =
+ * k u / (1 - k u)), or, on the tensor cores, the exact representation error
+ * of row i's FP16 pair, the dropped products and (T + 1) 2^-22 ||a_i sigma||
+ * for the FP32 accumulation of a chain of T MMAs (T = 3 n / 16 here, 4 n / 16
+ * in MHAR_MIXED_F16X3, where the tracked slack's error since the last refresh
+ * is added).  So a point on the computed chord satisfies A x <= b exactly
+ * under that error model: the chord can only be shorter than the exact one
+ * by those bounds (about (T + 1) 2^-22 relative on the tensor cores).  Every
+ * iteration of a run can be checked in FP64 (opts.audit_every). */
 #define MHAR_FP64             0
 #define MHAR_FP32             1
 #define MHAR_MIXED_F16X3      2
@@ -102,7 +126,12 @@ typedef struct {
                              the (walker strip, row tile) work; strips split
                              over SMs combine their partial chords in global
                              memory).  Results do not depend on it.          */
-  int32_t  reserved[3];   /* must be zero                                     */
+  int32_t  audit_every;   /* > 0: after every audit_every iterations of
+                             mhar_run, an FP64 check of A x <= b and A_E x = b_E
+                             on walkers 0..audit_walkers-1 folds into the
+                             running maxima of mhar_stats (default 0: off)   */
+  int32_t  audit_walkers; /* walkers checked by each audit (0: all z)          */
+  int32_t  reserved;      /* must be zero                                     */
 } mhar_opts;
 
 typedef struct {
@@ -121,11 +150,16 @@ typedef struct {
                                filled by mhar_check                            */
   int64_t  kernel_launches; /* library kernels launched so far (graph replays
                                count every kernel node)                        */
+  double   run_max_violation; /* max of a_i x - b_i over every audit since
+                               creation (-inf before the first)              */
+  double   run_eq_residual; /* max |A_E x - b_E|_inf over every audit          */
+  int64_t  audits;          /* audits run since creation                       */
 } mhar_stats;
 
 #define MHAR_ST_UNBOUNDED 1
 #define MHAR_ST_STALL     2
 #define MHAR_ST_NONFINITE 4
+#define MHAR_ST_DRIFT     8   /* a refresh found the tracked slack off its bound */
 
 typedef struct mhar_ctx mhar_ctx;
 
@@ -176,6 +210,14 @@ int mhar_check(mhar_ctx* ctx, mhar_stats* stats);
 /* Statistics without the FP64 feasibility pass. */
 int mhar_get_stats(const mhar_ctx* ctx, mhar_stats* stats);
 
+/* Turns the per-iteration FP64 audit on or off for later mhar_run calls (the
+ * opts.audit_every / opts.audit_walkers of mhar_create): every > 0 checks
+ * walkers 0..walkers-1 (0: all) after every `every` iterations and folds the
+ * results into mhar_stats.run_max_violation / run_eq_residual; every == 0
+ * stops auditing (the running maxima are kept).  MHAR_E_ARG on negative
+ * values or walkers > z. */
+int mhar_set_audit(mhar_ctx* ctx, int32_t every, int32_t walkers);
+
 /* Device-time profile of the walker step on the context's stream.  Captures
  * `iters` (1..4096) real iterations into a CUDA graph and times one replay
  * with CUDA events; times the direction kernels alone the same way (they are
@@ -196,11 +238,14 @@ int mhar_time_kernels(mhar_ctx* ctx, int iters, double* ms);
  * a process that works inside a fixed device-memory budget reserved up front
  * (so a cudaMalloc inside a library would break its accounting or fail), or a
  * latency-critical loop that cannot take the device synchronisation cudaMalloc
- * and cudaFree may bring.  It computes, in FP64, the same quantity as
- * mhar_get_chord in MHAR_FP64 mode: for walker k, the chord
- * (lmin[k], lmax[k]) of the line X[k] + lambda D[k] through {A x <= b}
- * (Section 4.4 formulas; rows with a.d == 0 are skipped, a slack made negative
- * by rounding counts as 0, an open side gives -inf / +inf).
+ * and cudaFree may bring.  It computes, in FP64, for walker k the chord
+ * (lmin[k], lmax[k]) of the line X[k] + lambda D[k] through {A x <= b}: over
+ * the rows with a_i . d > 0 the least (b_i - a_i . x) / (a_i . d) is lmax,
+ * over the rows with a_i . d < 0 the greatest is lmin; rows with a_i . d == 0
+ * give nothing, a slack made negative by rounding counts as 0, and a side
+ * without rows stays open (-inf / +inf).  A walker whose slack or a_i . d is
+ * not finite gets lmin = lmax = NaN.  Unlike mhar_get_chord it takes no
+ * rounding margin: the values are the plain FP64 ratios.
  *   A  m x n, b  m, X  z x n, D  z x n: device pointers, FP64, row-major, no
  *      padding; only read.
  *   lmin, lmax: z doubles each, device pointers, written.
@@ -230,10 +275,11 @@ int mhar_chord_noalloc(const double* A, const double* b, int m, int n,
  * The law of d does not depend on the walker's position and is centrally
  * symmetric, so the uniform distribution on the body stays the target of
  * the walk; only the speed of mixing changes.
- * In the tensor-core modes the library also rescales each coordinate of the
- * FP16 operands by a power of two chosen from diag(delta^2) + diag(U U^T)
- * (A's columns take the inverse scale; A x and A d are unchanged), so bodies
- * whose axes differ by orders of magnitude keep their relative precision. */
+ * In the tensor-core modes the coordinate scales sigma (see "Feasibility in
+ * every mode" above) are A's column scales times one power of two, each kept
+ * within [6.8 (delta_i + sum_q |U_iq|) / 65504, 2^8 sqrt(delta_i^2 +
+ * (U U^T)_ii)] so that the scaled directions fit the FP16 range and stay
+ * clear of its subnormals. */
 
 /* Sets the preconditioner (delta != NULL) or removes it (delta == NULL:
  * isotropic directions again).  delta: n values, finite, >= 0; U: n x rank,
@@ -312,6 +358,10 @@ int mhar_batch_get_state(const mhar_batch* batch, int32_t problem, double* X, ui
 /* mhar_check for problem p (kernel_launches adds the batch's own launches). */
 int mhar_batch_check(mhar_batch* batch, int32_t problem, mhar_stats* stats);
 
+/* mhar_set_audit for every problem of the batch (audits run after every
+ * `every` iterations of mhar_batch_run). */
+int mhar_batch_set_audit(mhar_batch* batch, int32_t every, int32_t walkers);
+
 /* Description of the batch's last error (never NULL). */
 const char* mhar_batch_last_error(const mhar_batch* batch);
 
@@ -323,11 +373,20 @@ void mhar_batch_destroy(mhar_batch* batch);
 const char* mhar_kernel_name(const mhar_ctx* ctx);
 
 /* Human-readable description of the last error on ctx (never NULL); with
- * ctx == NULL, the last mhar_chord_noalloc failure on this host thread. */
+ * ctx == NULL, on this host thread, the last failed mhar_create /
+ * mhar_batch_create, or the last mhar_chord_noalloc failure (cleared when a
+ * later mhar_chord_noalloc call succeeds). */
 const char* mhar_last_error(const mhar_ctx* ctx);
 
 /* Name of a return code. */
 const char* mhar_strerror(int code);
+
+/* The return code mhar_run gives for a device status word: status_bits, the
+ * OR of MHAR_ST_* seen, and wait_expired, nonzero when a bounded wait in a
+ * tensor-core kernel ran out (the kernel stops waiting there and raises the
+ * flag; that call's results are not to be trusted).  Precedence: timeout,
+ * non-finite, drift, unbounded; stalls alone are not an error. */
+int mhar_status_code(int32_t status_bits, int32_t wait_expired);
 
 /* Frees the context and its device memory; NULL is ignored. */
 void mhar_destroy(mhar_ctx* ctx);

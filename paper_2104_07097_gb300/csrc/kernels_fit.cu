@@ -17,9 +17,8 @@
 //      rotations (Golub & Van Loan, Matrix Computations, Section 8.5),
 //      U = Q V Lambda_+^{1/2}, largest eigenvalue first;
 //   4. delta_i^2 = max(Sigma_ii - (U U^T)_ii, 1e-2 Sigma_ii, 1e-9 tr(Sigma) / n).
-// The coordinate scales of the tensor-core operands are set from the fitted
-// direction variance C_ii = delta_i^2 + (U U^T)_ii: sigma_i = 2^e with
-// sqrt(C_ii) = f 2^e, f in [0.5, 1).
+// The host then sets the coordinate scales of the tensor-core operands from
+// the fitted (delta, U), as for a preconditioner given by the caller.
 // None of this is on the per-iteration path; it runs once, then the
 // preconditioner is frozen.
 #include <cmath>
@@ -404,7 +403,7 @@ cudaError_t launch_fit_factor(mhar_ctx* c, FitScratch* f, long long samples, int
   }
   ritz_kernel<<<1, kFitThreads, 0, c->stream>>>(n, c->n_ld, rank, f->Q, f->Y, f->sigma,
                                                 c->d.pc_delta64, c->d.pc_U64, c->d.pc_delta32,
-                                                c->d.pc_U32, c->d.sigma, f->flag);
+                                                c->d.pc_U32, nullptr, f->flag);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,8 @@ constexpr int kMaxTiles = 32;                        // rows per CTA <= 4096
 constexpr int kMaxCluster = 8;
 
 struct RcParams {
-  const float* bS;          // m_pad: b_i / row_scale_i (FP32)
+  const float* rows;        // 3 m_pad: b_i / row_scale_i and the error bounds (row_block)
+  const __half* Xh;         // z_ld x k_pad, row-major: FP16 hi of the scaled points
   const float* wscale;      // z_ld: X[k,:] = wscale[k] (Xh + Xl)[k,:]
   double* lmin;
   double* lmax;
@@ -73,7 +74,7 @@ struct RcParams {
   uint64_t seed;
   int j;
   uint32_t walker0;
-  int z, kdim, k_chunks, tiles_per_cta, m_tiles;
+  int z, kdim, k_chunks, k_pad, tiles_per_cta, m_tiles;
   WalkerTail wt;            // walker-side work (walker_tail.cuh)
 };
 
@@ -92,10 +93,12 @@ struct RcTail {
   float recv_hi[kMaxCluster][kWalkers];
   float theta_s[kWalkers];
   unsigned int red[kWalkers];
+  float nrm[3 * kWalkers];                // operand_norms
 };
 
 constexpr size_t kSmemRc = 1024 + static_cast<size_t>(kWSlots) * kWBytes +
                            static_cast<size_t>(kASlots) * kABytes + sizeof(RcTail);
+static_assert(kSmemRc <= 232448, "recompute_tc_kernel exceeds the shared memory of a CTA");
 
 __device__ __forceinline__ void st_dsmem_f32(float* local, uint32_t rank, float v) {
   uint32_t remote;
@@ -276,19 +279,22 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;
-    const float* bS_rows = p.bS + row_base + cg * 32;
-    if (lane == 0 && ntiles > 0) prefetch_l1(bS_rows);
+    const int row0 = row_base + cg * 32;
+    if (lane == 0 && ntiles > 0) prefetch_l1(row_block(p.rows, row0));
     if (p.wt.draw)
       walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
                                        w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
     const float ws = p.wscale[k];
+    WalkerNorms wn =
+        operand_norms<kEpiWarps * 32>(p.wt.Dh[cur], p.Xh, p.k_pad, k, wl, cg, ws, tail->nrm);
+    if (k < p.z) add_correction(p.wt, k, wn);
     ChordAcc acc;
     acc.init();
     for (int nt = 0; nt < ntiles; ++nt) {
       const int b = nt & 1;
-      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(bS_rows + (nt + 1) * kRowsTile);
+      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile));
       mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err, true);
       tc_fence_after();
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -300,8 +306,10 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tail->t_empty[b]);
-      slack32(sv, bS_rows + nt * kRowsTile, ws, acc);
-      scan32(sv, gv, acc);
+      float fx, fd;
+      wn.pick(p.rows, row0 + nt * kRowsTile, fx, fd);
+      slack32(sv, p.rows, row0 + nt * kRowsTile, ws, fx);
+      scan32(sv, gv, p.rows, row0 + nt * kRowsTile, fd, acc);
     }
     const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
@@ -317,7 +325,6 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
         st_dsmem_f32(&tail->recv_hi[rank][wl], r, H);
       }
     }
-    if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
 
   // Every push is visible after this barrier; no remote access follows it.
@@ -470,7 +477,9 @@ namespace {
 RcParams rc_params(const mhar_ctx* c, int j, int tiles_per_cta) {
   const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
   RcParams p;
-  p.bS = c->d.bS;
+  p.rows = c->d.rows;
+  p.Xh = c->d.Xh;
+  p.k_pad = c->k_pad;
   p.wscale = c->d.wscale;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;

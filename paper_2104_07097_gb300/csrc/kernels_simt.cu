@@ -36,7 +36,8 @@ __device__ __forceinline__ double pos_inf() { return __longlong_as_double(0x7ff0
 // in modes 1 and 2.
 __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint64_t* step_ptr,
                                   int j, uint32_t walker0, int z, int n, int n_ld, int k_pad,
-                                  double* D64, float* D32, __half* Dh, __half* Dl) {
+                                  const float* sigma, double* D64, float* D32, __half* Dh,
+                                  __half* Dl) {
   const int quads = (n + 3) >> 2;
   const int per_quad = mode == 0 ? 2 : 1;
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -67,8 +68,9 @@ __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (i0 + e < n) {
-          const __half h = __float2half_rn(v[e]);
-          const __half l = __float2half_rn(v[e] - __half2float(h));
+          const float vs = v[e] * (1.0f / sigma[i0 + e]);   // d_i / sigma_i, exact
+          const __half h = __float2half_rn(vs);
+          const __half l = __float2half_rn(vs - __half2float(h));
           Dh[static_cast<size_t>(k) * k_pad + i0 + e] = h;
           Dl[static_cast<size_t>(k) * k_pad + i0 + e] = l;
         }
@@ -103,13 +105,19 @@ __device__ __forceinline__ void cholesky_solve(const double* L, int mE, double* 
   }
 }
 
+// Equality row e, coordinate i of A_E in FP32 (the FP32 modes pass A_E as FP32).
+template <typename T>
+__device__ __forceinline__ float AE32f(const T* AE, int e, int n_ld, int i) {
+  return static_cast<float>(AE[static_cast<size_t>(e) * n_ld + i]);
+}
+
 template <typename T>
 __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
                                   const double* __restrict__ AE64, const double* __restrict__ L,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
-                                  float* corr, int z_ld, int inter, const float* sigma,
-                                  const uint64_t* step_ptr, int j, __half* Dh1, __half* Dl1,
-                                  int* status) {
+                                  float* corr, float* corrn, int z_ld, int inter,
+                                  const float* sigma, const uint64_t* step_ptr, int j,
+                                  __half* Dh1, __half* Dl1, int* status) {
   if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
     Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
     Dl = Dl1;
@@ -168,6 +176,21 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     cholesky_solve(L, mE, c);
     for (int e = 0; e < mE; ++e) corr[static_cast<size_t>(k) * mE + e] = static_cast<float>(c[e]);
   }
+  __syncwarp();
+  // The point moves along d - A_E^T c' (the update's FP32 arithmetic) while
+  // the chord is found along d: ||A_E^T c' / sigma||_2, rounded up, enters
+  // the chord's error margins (tc_common.cuh, kernels_simt.cu).
+  float cn = 0.0f;
+  for (int i = lane; i < n; i += 32) {
+    float dlt = 0.0f;
+    for (int e = 0; e < mE; ++e)
+      dlt = fmaf(AE32f(AE, e, n_ld, i), corr[static_cast<size_t>(k) * mE + e], dlt);
+    const float v = dlt / sigma[i];
+    cn = fmaf(v, v, cn);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, off);
+  if (lane == 0) corrn[k] = sqrtf(cn) * 1.0009765625f;
 }
 
 // ---- preconditioned directions ---------------------------------------------
@@ -250,17 +273,39 @@ struct ChordTile<double> { static constexpr int BK = 8; };
 template <>
 struct ChordTile<float> { static constexpr int BK = 16; };
 
+// Rounding-error margins of the FP32 chord (unit roundoff u = 2^-24): with
+// sigma the power-of-two column scales of A,
+//   |computed - exact| of b_i - a_i . x  <=  e(x) + 3 u |b_i|
+//   |computed - exact| of a_i . d        <=  e(d)
+//   e(v) = min(K_i,2 ||v / sigma||_2, K_i,1 max |v_j / sigma_j|)
+// where K_i,p = gamma_{nnz_i + 4} ||a_i sigma||_p (gamma_k = k u / (1 - k u):
+// the roundings of A, x, the products and sums over the row's nonzeros, and
+// the ratio; Hoelder on |a_i| . |v|).  The kernels take b already lowered by
+// 3 u |b_i| and kr = (K_i,2, K_i,1); the per-walker norms are computed here,
+// rounded up.  FP64 passes kr = NULL: its rounding (gamma ~ 1e-13 for n = 1000)
+// is far inside the 1e-6 feasibility tolerance, and no margin keeps the FP64
+// walk equal to the exact one to the last bits the parity tests see.
+template <typename T>
+struct Unit;
+template <>
+struct Unit<double> { static constexpr double guard = 1.0 + 1e-12; };
+template <>
+struct Unit<float> { static constexpr float guard = 1.0009765625f; };
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-chord_simt_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ X,
-                  const T* __restrict__ D, int m, int n_ld, int z,
+chord_simt_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ kr,
+                  const T* __restrict__ X, const T* __restrict__ D, const float* __restrict__ sigma,
+                  const float* __restrict__ corrn, int m, int n_ld, int z,
                   unsigned long long* key_lo, unsigned long long* key_hi, int* status) {
   constexpr int BK = ChordTile<T>::BK;
+  constexpr int kRowsPerThread = 64 * BK / kThreads;   // walker rows each thread loads
   __shared__ T As[BK][64];
   __shared__ T Xs[BK][64];
   __shared__ T Ds[BK][64];
   __shared__ T red_lo[16][64];
   __shared__ T red_hi[16][64];
+  __shared__ T nrm[4][64];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * 64, w0 = blockIdx.y * 64;
   T accS[4][4], accG[4][4];
@@ -268,14 +313,31 @@ chord_simt_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) { accS[r][c] = T(0); accG[r][c] = T(0); }
+  // Sums of (x_i / sigma_i)^2, (d_i / sigma_i)^2 of the walker rows this
+  // thread loads (column tid % BK of each tile).
+  T sx[kRowsPerThread], sd[kRowsPerThread], mxx[kRowsPerThread], mxd[kRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) { sx[j] = T(0); sd[j] = T(0); mxx[j] = T(0); mxd[j] = T(0); }
 
   for (int k0 = 0; k0 < n_ld; k0 += BK) {
-    for (int e = tid; e < 64 * BK; e += kThreads) {
+    const T isig = T(1) / static_cast<T>(sigma[k0 + tid % BK]);   // a power of two: exact
+#pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j) {
+      const int e = tid + j * kThreads;
       const int r = e / BK, c = e - r * BK;
       const int gi = i0 + r, gw = w0 + r;
       As[c][r] = gi < m ? A[static_cast<size_t>(gi) * n_ld + k0 + c] : T(0);
-      Xs[c][r] = gw < z ? X[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
-      Ds[c][r] = gw < z ? D[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
+      const T xv = gw < z ? X[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
+      const T dv = gw < z ? D[static_cast<size_t>(gw) * n_ld + k0 + c] : T(0);
+      Xs[c][r] = xv;
+      Ds[c][r] = dv;
+      if (kr != nullptr) {
+        const T xs = xv * isig, ds = dv * isig;
+        sx[j] += xs * xs;
+        sd[j] += ds * ds;
+        mxx[j] = fmax(mxx[j], fabs(xs));
+        mxd[j] = fmax(mxd[j], fabs(ds));
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -295,17 +357,45 @@ chord_simt_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
     }
     __syncthreads();
   }
+  // Each walker row's sums are spread over BK consecutive lanes: add them
+  // with a butterfly (every lane gets the same bits).
+#pragma unroll
+  for (int j = 0; j < kRowsPerThread; ++j) {
+#pragma unroll
+    for (int off = BK / 2; off > 0; off >>= 1) {
+      sx[j] += __shfl_xor_sync(0xffffffffu, sx[j], off);
+      sd[j] += __shfl_xor_sync(0xffffffffu, sd[j], off);
+      mxx[j] = fmax(mxx[j], __shfl_xor_sync(0xffffffffu, mxx[j], off));
+      mxd[j] = fmax(mxd[j], __shfl_xor_sync(0xffffffffu, mxd[j], off));
+    }
+    if (tid % BK == 0) {
+      const int r = (tid + j * kThreads) / BK;
+      nrm[0][r] = sqrt(sx[j]) * Unit<T>::guard;
+      nrm[1][r] = sqrt(sd[j]) * Unit<T>::guard;
+      nrm[2][r] = mxx[j];
+      nrm[3][r] = mxd[j];
+    }
+  }
+  __syncthreads();
 
   bool bad = false;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     T lo = static_cast<T>(neg_inf()), hi = static_cast<T>(pos_inf());
+    const int w = tx + 16 * c;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int gi = i0 + ty * 4 + r;
       if (gi >= m) continue;
       T s = b[gi] - accS[r][c];
-      const T g = accG[r][c];
+      T g = accG[r][c];
+      if (kr != nullptr) {
+        const T k2 = kr[3 * gi], k1 = kr[3 * gi + 1];
+        s -= fmin(k2 * nrm[0][w], k1 * nrm[2][w]);
+        T eg = fmin(k2 * nrm[1][w], k1 * nrm[3][w]);
+        if (corrn != nullptr && w0 + w < z) eg += kr[3 * gi + 2] * static_cast<T>(corrn[w0 + w]);
+        g = g > T(0) ? g + eg : (g < T(0) ? g - eg : g);
+      }
       if (!isfinite(s) || !isfinite(g)) { bad = true; continue; }
       if (s < T(0)) s = T(0);
       if (g > T(0)) {
@@ -506,8 +596,9 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
         __half h8[8], l8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          h8[e] = __float2half_rn(v[e]);
-          l8[e] = __float2half_rn(v[e] - __half2float(h8[e]));
+          const float vs = v[e] * (1.0f / sigma[i0 + e]);   // d_i / sigma_i, exact
+          h8[e] = __float2half_rn(vs);
+          l8[e] = __float2half_rn(vs - __half2float(h8[e]));
         }
         st8h(Dh + opo(i0), h8);
         st8h(Dl + opo(i0), l8);
@@ -579,6 +670,30 @@ __global__ void check_kernel(int mode, int m, int n, int n_ld, int mE, const dou
   }
 }
 
+// Stored-slack mode, after a refresh (one warp per walker): the bound
+// ||x / sigma||_2 (1 + 2^-8) of the refreshed point, the step sum of the
+// tracked slack's error reset, and the refresh's iteration recorded.
+__global__ void stored_reset_kernel(int z, int n, int n_ld, const float* Xhi, const float* Xlo,
+                                    const float* sigma, const uint64_t* step, float* nx_ref,
+                                    float* theta_acc, uint64_t* refresh_step) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *refresh_step = *step;
+  if (k >= z) return;
+  float ss = 0.0f;
+  for (int i = lane; i < n; i += 32) {
+    const size_t o = static_cast<size_t>(k) * n_ld + i;
+    const float v = (Xhi[o] + Xlo[o]) / sigma[i];
+    ss = fmaf(v, v, ss);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  if (lane == 0) {
+    nx_ref[k] = sqrtf(ss) * 1.00390625f;
+    theta_acc[k] = 0.0f;
+  }
+}
+
 // Mixed mode: S = b - A X recomputed in FP64 from the FP32-pair points (tiles
 // of 64 rows x 64 walkers, K staged through shared memory), stored as the
 // tensor-core path keeps it (divided by the row scale, blocked by 4 rows),
@@ -594,7 +709,9 @@ constexpr int kWarpChordThreads = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(kWarpChordThreads)
-chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ X,
+chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __restrict__ kr,
+                  const float* __restrict__ sigma, const float* __restrict__ corrn,
+                  const T* __restrict__ X,
                   const T* __restrict__ D, int m, int n, int n_ld, int z,
                   unsigned long long* key_lo, unsigned long long* key_hi, int* status,
                   int move, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
@@ -606,6 +723,28 @@ chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
   if (k >= z) return;
   const T* x = X + static_cast<size_t>(k) * n_ld;
   const T* d = D + static_cast<size_t>(k) * n_ld;
+  // ||x / sigma||_2 and ||d / sigma||_2 of the walker (the margins of
+  // chord_simt_kernel); the butterfly gives every lane the same bits.
+  T nx = T(0), nd = T(0), ix = T(0), id = T(0);
+  if (kr != nullptr) {
+    for (int c = lane; c < n; c += 32) {
+      const T is = T(1) / static_cast<T>(sigma[c]);
+      const T xs = x[c] * is, ds = d[c] * is;
+      nx += xs * xs;
+      nd += ds * ds;
+      ix = fmax(ix, fabs(xs));
+      id = fmax(id, fabs(ds));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      nx += __shfl_xor_sync(0xffffffffu, nx, off);
+      nd += __shfl_xor_sync(0xffffffffu, nd, off);
+      ix = fmax(ix, __shfl_xor_sync(0xffffffffu, ix, off));
+      id = fmax(id, __shfl_xor_sync(0xffffffffu, id, off));
+    }
+    nx = sqrt(nx) * Unit<T>::guard;
+    nd = sqrt(nd) * Unit<T>::guard;
+  }
   T lo = static_cast<T>(neg_inf()), hi = static_cast<T>(pos_inf());
   bool bad = false;
   for (int i = lane; i < m; i += 32) {
@@ -616,6 +755,13 @@ chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
       ad += a[c] * d[c];
     }
     T sv = b[i] - ax;
+    if (kr != nullptr) {
+      const T k2 = kr[3 * i], k1 = kr[3 * i + 1];
+      sv -= fmin(k2 * nx, k1 * ix);
+      T eg = fmin(k2 * nd, k1 * id);
+      if (corrn != nullptr) eg += kr[3 * i + 2] * static_cast<T>(corrn[k]);
+      ad = ad > T(0) ? ad + eg : (ad < T(0) ? ad - eg : ad);
+    }
     if (!isfinite(sv) || !isfinite(ad)) { bad = true; continue; }
     if (sv < T(0)) sv = T(0);
     if (ad > T(0)) {
@@ -790,39 +936,128 @@ __global__ void reproject_kernel(int z, int n, int n_ld, int mE, const double* A
 // Tensor-core operands: columns multiplied by the coordinate scales sigma
 // (powers of two), then a per-row power-of-two scale s_r with
 // max_i |a_ri sigma_i| / s_r in [0.5, 1), then the row split into FP16 hi + lo.
-// FP32 copy of b / s_r, padded.
-__global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, const double* A,
-                                  const double* b, __half* Ah, __half* Al, float* row_scale,
-                                  float* bS, const float* sigma) {
+// FP32 copy of b / s_r, padded.  With them, the error bounds of the chord
+// epilogue (tc_common.cuh, row_block), from the row a_hat = a_r sigma / s_r in
+// FP64 and its FP16 pair (hi, lo), in two forms, for the 2-norms and for the
+// max-norms of the walker's operands (|.|_p below is the p-norm of a row):
+//   Kg_p = |a_hat - hi - lo|_p + 2^-11 |lo|_p (1 + 2^-11)
+//          + (T + 1) 2^-22 |a_hat|_p (1 + 2^-9)
+//     -- |computed - exact| of a_hat . d per unit |d_hat|_q (1/p + 1/q = 1):
+//     the pair's exact representation error, the dropped lo.lo product
+//     (|d_lo| <= 2^-11 |d_hi|), and the FP32 accumulation of the T MMAs that
+//     meet the row's nonzeros (T = `per_step` per 16-column block holding a
+//     nonzero: at most (T + 1) 2^-22 of the sum of |products| on GB300,
+//     Hoelder's inequality bounds that by |a_hat|_p |d_hat|_q);
+//   Ks_p = Kg_p + |a_hat|_p (2^-21 + 2^-24 c_p) + 2^-22 |a_hat|_p
+//     -- the same for a_hat . x_hat per unit |x_hat|_q (max |x_hat| in
+//     [0.5, 1)), adding the split of the point (2^-21 relative plus 2^-25
+//     absolute per coordinate: c_2 = sqrt(nonzeros), c_1 = 1) and the
+//     relative rounding of the ratio and of theta (2^-22 of |a_hat . x_hat|).
+// The other relative roundings (b / s_r in FP32, the slack's FMA, the ratio,
+// theta) are at most 2^-21 |b / s_r| and lower bS by that much.  Every bound
+// is rounded up to FP32.  rowk[4 r ..]: Ks_2, Kg_2, Ks_1, Kg_1.
+__global__ void prepare_tc_kernel(int m, int n, int n_ld, int m_pad, int k_pad, int per_step,
+                                  const double* A, const double* b, __half* Ah, __half* Al,
+                                  float* row_scale, float* bS, float* rowk, const float* sigma) {
   const int r = blockIdx.x;
   if (r >= m_pad) return;
-  __shared__ double red[kThreads];
+  __shared__ double red[7][kThreads];
+  __shared__ unsigned int blocks[4];   // nonzero 16-column blocks (k_pad <= 2048)
+  if (threadIdx.x < 4) blocks[threadIdx.x] = 0u;
   double mx = 0.0;
   if (r < m)
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       mx = fmax(mx, fabs(A[static_cast<size_t>(r) * n_ld + i] * static_cast<double>(sigma[i])));
-  red[threadIdx.x] = mx;
+  red[0][threadIdx.x] = mx;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    if (threadIdx.x < s) red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
     __syncthreads();
   }
-  mx = red[0];
+  mx = red[0][0];
+  __syncthreads();
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
   const double scale = ldexp(1.0, e);
-  if (threadIdx.x == 0) {
-    row_scale[r] = r < m ? static_cast<float>(scale) : 1.0f;
-    bS[r] = r < m ? static_cast<float>(b[r] / scale) : 0.0f;
-  }
+  double q[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // |a|_2^2 |a|_1 |rep|_2^2 |rep|_1 |lo|_2^2 |lo|_1 nnz
   for (int i = threadIdx.x; i < k_pad; i += blockDim.x) {
-    float v = 0.0f;
-    if (r < m && i < n)
-      v = static_cast<float>(A[static_cast<size_t>(r) * n_ld + i] * static_cast<double>(sigma[i]) /
-                             scale);
+    double a = 0.0;
+    if (r < m && i < n) a = A[static_cast<size_t>(r) * n_ld + i] * static_cast<double>(sigma[i]) / scale;
+    const float v = static_cast<float>(a);
     const __half h = __float2half_rn(v);
+    const __half l = __float2half_rn(v - __half2float(h));
     Ah[static_cast<size_t>(r) * k_pad + i] = h;
-    Al[static_cast<size_t>(r) * k_pad + i] = __float2half_rn(v - __half2float(h));
+    Al[static_cast<size_t>(r) * k_pad + i] = l;
+    const double hl = static_cast<double>(__half2float(h));
+    const double ll = static_cast<double>(__half2float(l));
+    const double rep = a - hl - ll;
+    q[0] += a * a;
+    q[1] += fabs(a);
+    q[2] += rep * rep;
+    q[3] += fabs(rep);
+    q[4] += ll * ll;
+    q[5] += fabs(ll);
+    if (a != 0.0) {
+      q[6] += 1.0;
+      atomicOr(&blocks[(i >> 4) >> 5], 1u << ((i >> 4) & 31));
+    }
+  }
+  for (int t = 0; t < 7; ++t) red[t][threadIdx.x] = q[t];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int t = 0; t < 7; ++t) red[t][threadIdx.x] += red[t][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int nblk = __popc(blocks[0]) + __popc(blocks[1]) + __popc(blocks[2]) + __popc(blocks[3]);
+    const double g = static_cast<double>(per_step * nblk + 1) * 0x1p-22 * (1.0 + 0x1p-9);
+    const double up = 1.0 + 1e-12;   // the FP64 sums and square roots
+    const double na2 = sqrt(red[0][0]) * up, na1 = red[1][0] * up;
+    const double rp2 = sqrt(red[2][0]) * up, rp1 = red[3][0] * up;
+    const double lo2 = sqrt(red[4][0]) * up, lo1 = red[5][0] * up;
+    const double nnz = red[6][0];
+    const double kg2 = rp2 + 0x1p-11 * lo2 * (1.0 + 0x1p-11) + g * na2;
+    const double ks2 = kg2 + na2 * (0x1p-21 + 0x1p-24 * sqrt(nnz)) + 0x1p-22 * na2;
+    const double kg1 = rp1 + 0x1p-11 * lo1 * (1.0 + 0x1p-11) + g * na1;
+    const double ks1 = kg1 + na1 * (0x1p-21 + 0x1p-24) + 0x1p-22 * na1;
+    const double bs = r < m ? b[r] / scale : 0.0;
+    float bf = static_cast<float>(bs);
+    bf = bf - 0x1p-21f * fabsf(bf);           // the relative roundings (see above)
+    if (static_cast<double>(bf) > bs) bf = nextafterf(bf, -INFINITY);
+    const double kk[4] = {ks2, kg2, ks1, kg1};
+    for (int t = 0; t < 4; ++t) {
+      float f = static_cast<float>(kk[t]);
+      if (static_cast<double>(f) < kk[t]) f = nextafterf(f, INFINITY);
+      rowk[4 * r + t] = r < m ? f : 0.0f;
+    }
+    row_scale[r] = r < m ? static_cast<float>(scale) : 1.0f;
+    bS[r] = r < m ? bf : 0.0f;
+  }
+}
+
+// The per-32-row blocks of the chord epilogue (tc_common.cuh, row_block): each
+// group of 32 rows takes the bound form (2-norms or max-norms of the walker's
+// operands) whose sum of Kg over the group, times the typical norm of the
+// scaled direction (d2, dinf), is smaller -- the max-norm form wins for rows
+// with few nonzeros, the 2-norm form for dense ones.
+__global__ void row_blocks_kernel(int groups, const float* bS, const float* rowk, float d2,
+                                  float dinf, float* rows) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= groups) return;
+  double s2 = 0.0, s1 = 0.0;
+  for (int t = 0; t < 32; ++t) {
+    s2 += rowk[4 * (32 * g + t) + 1];
+    s1 += rowk[4 * (32 * g + t) + 3];
+  }
+  const int inf = s1 * dinf < s2 * d2 ? 1 : 0;
+  float* blk = rows + g * 128;
+  for (int t = 0; t < 32; ++t) {
+    const int r = 32 * g + t;
+    blk[t] = bS[r];
+    blk[32 + t] = rowk[4 * r + (inf ? 2 : 0)];
+    blk[64 + t] = rowk[4 * r + (inf ? 3 : 1)];
+    blk[96 + t] = inf ? 1.0f : 0.0f;
   }
 }
 
@@ -853,7 +1088,7 @@ cudaError_t launch_directions(mhar_ctx* c, int j) {
   directions_kernel<<<blocks_for(threads, block), block, 0, c->stream>>>(
       mode, (c->mE == 0 && c->pc_rank < 0) ? 1 : 0, c->opts.seed, c->d.step, j, c->opts.walker0,
       c->z, c->n, c->n_ld,
-      c->k_pad, c->d.D64, c->d.D32, c->d.Dh, c->d.Dl);
+      c->k_pad, c->d.sigma, c->d.D64, c->d.D32, c->d.Dh, c->d.Dl);
   return cudaGetLastError();
 }
 
@@ -862,14 +1097,14 @@ cudaError_t launch_projection(mhar_ctx* c, int j) {
   if (c->opts.precision == MHAR_FP64) {
     projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr, c->d.status);
+        nullptr, nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr, c->d.status);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
     projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
         c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
-        c->d.Dh, c->d.Dl, c->d.corr, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0, c->d.sigma,
-        c->d.step, j, c->d.Dh2, c->d.Dl2, c->d.status);
+        c->d.Dh, c->d.Dl, c->d.corr, c->d.corrn, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0,
+        c->d.sigma, c->d.step, j, c->d.Dh2, c->d.Dl2, c->d.status);
   }
   return cudaGetLastError();
 }
@@ -902,13 +1137,14 @@ cudaError_t launch_chord_update_warp(mhar_ctx* c, int j) {
   const int g = blocks_for(c->z, kWarpChordThreads / 32);
   if (c->opts.precision == MHAR_FP64)
     chord_warp_kernel<double><<<g, kWarpChordThreads, 0, c->stream>>>(
-        c->d.A64, c->d.b64, c->d.X64, c->d.D64, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
+        c->d.A64, c->d.b64, static_cast<const double*>(nullptr), c->d.sigma, nullptr, c->d.X64,
+        c->d.D64, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
         c->d.key_hi, c->d.status, 1, c->opts.seed, c->d.step, j, c->opts.walker0, c->d.lmin,
         c->d.lmax, c->d.theta, c->d.counters, c->d.X64, c->d.D64, nullptr, nullptr, nullptr,
         c->mE, nullptr, nullptr);
   else
     chord_warp_kernel<float><<<g, kWarpChordThreads, 0, c->stream>>>(
-        c->d.A32, c->d.b32, c->d.Xhi, c->d.D32, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
+        c->d.A32, c->d.b32, c->d.kr32, c->d.sigma, c->d.corrn, c->d.Xhi, c->d.D32, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
         c->d.key_hi, c->d.status, 1, c->opts.seed, c->d.step, j, c->opts.walker0, c->d.lmin,
         c->d.lmax, c->d.theta, c->d.counters, nullptr, nullptr, c->d.Xhi, c->d.Xlo, c->d.D32,
         c->mE, c->d.AE32, c->d.corr);
@@ -919,12 +1155,14 @@ cudaError_t launch_chord_simt(mhar_ctx* c) {
   dim3 grid(blocks_for(c->m, 64), blocks_for(c->z, 64));
   if (c->opts.precision == MHAR_FP64) {
     chord_simt_kernel<double><<<grid, kThreads, 0, c->stream>>>(
-        c->d.A64, c->d.b64, c->d.X64, c->d.D64, c->m, c->n_ld, c->z, c->d.key_lo, c->d.key_hi,
-        c->d.status);
+        c->d.A64, c->d.b64, static_cast<const double*>(nullptr), c->d.X64, c->d.D64, c->d.sigma,
+        nullptr, c->m, c->n_ld, c->z,
+        c->d.key_lo, c->d.key_hi, c->d.status);
   } else {
     chord_simt_kernel<float><<<grid, kThreads, 0, c->stream>>>(
-        c->d.A32, c->d.b32, c->d.Xhi, c->d.D32, c->m, c->n_ld, c->z, c->d.key_lo, c->d.key_hi,
-        c->d.status);
+        c->d.A32, c->d.b32, c->d.kr32, c->d.Xhi, c->d.D32, c->d.sigma, c->d.corrn, c->m, c->n_ld,
+        c->z,
+        c->d.key_lo, c->d.key_hi, c->d.status);
   }
   return cudaGetLastError();
 }
@@ -979,14 +1217,21 @@ cudaError_t launch_set_points(mhar_ctx* c, const double* X_dev) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_check(mhar_ctx* c) {
+cudaError_t launch_check(mhar_ctx* c, int walkers, unsigned long long* out_keys) {
   const int mode = c->opts.precision == MHAR_FP64 ? 0 : 1;
   const int block = 128;
   const int rows = c->m > c->mE ? c->m : c->mE;
-  dim3 grid(blocks_for(rows, block), c->z);
+  dim3 grid(blocks_for(rows, block), walkers);
   check_kernel<<<grid, block, sizeof(double) * c->n, c->stream>>>(
       mode, c->m, c->n, c->n_ld, c->mE, c->d.A64, c->d.b64, c->d.AE64, c->d.bE64, c->d.X64,
-      c->d.Xhi, c->d.Xlo, reinterpret_cast<unsigned long long*>(c->d.check));
+      c->d.Xhi, c->d.Xlo, out_keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stored_reset(mhar_ctx* c) {
+  stored_reset_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
+      c->z, c->n, c->n_ld, c->d.Xhi, c->d.Xlo, c->d.sigma, c->d.step, c->d.nx_ref,
+      c->d.theta_acc, c->d.refresh_step);
   return cudaGetLastError();
 }
 
@@ -1006,9 +1251,13 @@ cudaError_t launch_reproject(mhar_ctx* c) {
 }
 
 cudaError_t launch_prepare_tc_operands(mhar_ctx* c) {
-  prepare_tc_kernel<<<c->m_pad, kThreads, 0, c->stream>>>(c->m, c->n, c->n_ld, c->m_pad, c->k_pad,
-                                                         c->d.A64, c->d.b64, c->d.Ah, c->d.Al,
-                                                         c->d.row_scale, c->d.bS, c->d.sigma);
+  prepare_tc_kernel<<<c->m_pad, kThreads, 0, c->stream>>>(
+      c->m, c->n, c->n_ld, c->m_pad, c->k_pad, mma_per_step(c), c->d.A64, c->d.b64, c->d.Ah,
+      c->d.Al, c->d.row_scale, c->d.bS, c->d.rowk, c->d.sigma);
+  const int groups = c->m_pad / 32;
+  row_blocks_kernel<<<blocks_for(groups, 128), 128, 0, c->stream>>>(
+      groups, c->d.bS, c->d.rowk, static_cast<float>(c->dir_norm2), static_cast<float>(c->dir_norminf),
+      c->d.rows);
   return cudaGetLastError();
 }
 

@@ -53,7 +53,8 @@ struct SkSeg {
 };
 
 struct SkParams {
-  const float* bS;
+  const float* rows;        // 3 m_pad: b_i / row_scale_i and the error bounds (row_block)
+  const __half* Xh;         // z_ld x k_pad, row-major: FP16 hi of the scaled points
   const float* wscale;
   double* lmin;
   double* lmax;
@@ -64,7 +65,7 @@ struct SkParams {
   const uint64_t* step_ptr;
   uint64_t seed;
   uint32_t walker0;
-  int z, kdim, k_chunks;
+  int z, kdim, k_chunks, k_pad;
   const SkSeg* segs;        // all segments, grouped by CTA
   const int* seg_begin;     // CTA b owns segs[seg_begin[b] .. seg_begin[b + 1])
   float* partials;          // [strip][slot][2][128]: lambda_min, lambda_max of a segment
@@ -87,10 +88,12 @@ struct SkTail {
   float part_hi[4][kWalkers];
   float theta_s[kWalkers];
   unsigned int red[kWalkers];
+  float nrm[3 * kWalkers];        // operand_norms
 };
 
 constexpr size_t kSmemSk = 1024 + static_cast<size_t>(kWSlots) * kWBytes +
                            static_cast<size_t>(kASlots) * kABytes + sizeof(SkTail);
+static_assert(kSmemSk <= 232448, "recompute_sk_kernel exceeds the shared memory of a CTA");
 
 __device__ __forceinline__ void mbar_arrive_sk(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -232,8 +235,8 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     for (int sg = sb; sg < se; ++sg) {
       const SkSeg seg = p.segs[sg];
       const int strip = seg.strip;
-      const float* bS_rows = p.bS + cg * 32;
-      if (lane == 0 && seg.t1 > seg.t0) prefetch_l1(bS_rows + seg.t0 * kRowsTile);
+      const int row0 = cg * 32;
+      if (lane == 0 && seg.t1 > seg.t0) prefetch_l1(row_block(p.rows, row0 + seg.t0 * kRowsTile));
       // Iteration s+1's directions for this segment's share of the strip's
       // walkers, into the other pair (while the segment's first tile loads).
       if (p.wt.draw) {
@@ -244,11 +247,14 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       }
       const int k = strip * kWalkers + wl;
       const float ws = p.wscale[k];
+      WalkerNorms wn =
+          operand_norms<kEpiWarps * 32>(p.wt.Dh[cur], p.Xh, p.k_pad, k, wl, cg, ws, tail->nrm);
+      if (k < p.z) add_correction(p.wt, k, wn);
       ChordAcc acc;
       acc.init();
       for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
         const int b = gt & 1;
-        if (lane == 0 && nt + 1 < seg.t1) prefetch_l1(bS_rows + (nt + 1) * kRowsTile);
+        if (lane == 0 && nt + 1 < seg.t1) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile));
         mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, p.err, true);
         tc_fence_after();
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -260,10 +266,11 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_sk(&tail->t_empty[b]);
-        slack32(sv, bS_rows + nt * kRowsTile, ws, acc);
-        scan32(sv, gv, acc);
+        float fx, fd;
+        wn.pick(p.rows, row0 + nt * kRowsTile, fx, fd);
+        slack32(sv, p.rows, row0 + nt * kRowsTile, ws, fx);
+        scan32(sv, gv, p.rows, row0 + nt * kRowsTile, fd, acc);
       }
-      if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
       const float lo = acc.lo_all(), hi = acc.hi_all();
       tail->part_lo[cg][wl] = lo;
       tail->part_hi[cg][wl] = hi;
@@ -429,7 +436,9 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   const TcPlan* tp = static_cast<const TcPlan*>(c->tc);
   const SkPlan* plan = static_cast<const SkPlan*>(c->sk);
   SkParams p;
-  p.bS = c->d.bS;
+  p.rows = c->d.rows;
+  p.Xh = c->d.Xh;
+  p.k_pad = c->k_pad;
   p.wscale = c->d.wscale;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;

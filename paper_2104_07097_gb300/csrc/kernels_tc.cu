@@ -36,6 +36,7 @@
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
 #include "tc_common.cuh"
+#include "walker_tail.cuh"
 
 namespace mhar {
 namespace {
@@ -58,6 +59,18 @@ struct TcParams {
   float* S;                 // slack / row_scale, blocked: [(i/4) z_ld + k] * 4 + i%4
   float* Xhi;               // z x n_ld
   float* Xlo;
+  const float* rowk;        // 4 m_pad: Ks_2, Kg_2, Ks_1, Kg_1 of every row (prepare_tc_kernel)
+  const __half* Xh;         // z_ld x k_pad: FP16 hi of the points split at the last refresh
+  const float* corrn;       // z or null: ||A_E^T corr / sigma||_2 (see add_correction)
+  // The tracked slack's error since the last refresh, per walker: bounded by
+  // Ks_i E_k + k 2^-24 |b_i / scale_i| after k updates, with
+  //   E_k = (||x_r / sigma|| + sum_t |theta_t| ||d_hat_t||) (1 + k / (4 T + 4)),
+  // x_r the point at the refresh and T the MMAs of one product chain.
+  const float* nx_ref;      // z: ||x_r / sigma||_2 bound, set by every refresh
+  float* theta_acc;         // z: sum_t |theta_t| ||d_hat_t||_2 since the refresh
+  const uint64_t* refresh_step;  // iteration counter at the last refresh
+  float growth;             // 1 / (4 T + 4)
+  int check_drift;          // refresh: compare the tracked slack with its bound
   const __half* Dh;         // z_ld x k_pad
   const __half* Dl;
   const float* sigma;       // n_ld: coordinate scales (operands hold x / sigma, d / sigma)
@@ -90,9 +103,15 @@ struct SmemTail {
   float theta[kWalkers];
   float scale[kMaxTilesPerCta * kRowsTile];
   float brow[kMaxTilesPerCta * kRowsTile];
+  float ks[kMaxTilesPerCta * kRowsTile];   // Ks_i of this CTA's rows
+  float kg[kMaxTilesPerCta * kRowsTile];   // Kg_i
+  float jk[kMaxTilesPerCta * kRowsTile];   // k 2^-24 |b_i / scale_i|, k updates since the refresh
+  float nrm[3 * kWalkers];                 // operand_norms
+  float nd[kWalkers];                      // ||d_hat||_2 bound of each walker's direction
 };
 
 constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + sizeof(SmemTail);
+static_assert(kSmemBytes <= 232448, "walker_tc_kernel exceeds the shared memory of a CTA");
 
 // The slack is stored blocked by 4 rows: element (i, k) sits at
 // ((i / 4) z_ld + k) 4 + i % 4, so one 16-byte access gives a walker four
@@ -153,10 +172,16 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // Updates of the tracked slack since the last refresh.
+  const float since = static_cast<float>(*p.step_ptr + static_cast<uint64_t>(p.j) -
+                                         *p.refresh_step);
   for (int r = threadIdx.x; r < p.tiles_per_cta * kRowsTile; r += blockDim.x) {
     const bool in = r < ntiles * kRowsTile;
     tail->scale[r] = in ? p.row_scale[row_base + r] : 1.0f;
     tail->brow[r] = in ? p.bS[row_base + r] : 0.0f;
+    tail->ks[r] = in ? p.rowk[4 * (row_base + r)] : 0.0f;
+    tail->kg[r] = in ? p.rowk[4 * (row_base + r) + 1] : 0.0f;
+    tail->jk[r] = in ? since * 5.9604645e-8f * fabsf(p.bS[row_base + r]) * 1.0001f : 0.0f;
   }
   tc_fence_before();
   __syncthreads();
@@ -224,6 +249,17 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const int k = strip * kWalkers + wl;
     const float ws = p.wscale[k];
     float drift = 0.0f;
+    // Bound on |tracked - recomputed| per unit Ks_i: the tracked slack's bound
+    // (see TcParams) plus the recomputation's own (ws ||x_hat||_2).
+    const float nxw =
+        operand_norms<kEpiWarps * 32>(p.Dh, p.Xh, p.k_chunks * kTcKChunk, k, wl, cg, ws, tail->nrm)
+            .nxw2;
+    const float Eb = (k < p.z && p.check_drift)
+                         ? (p.nx_ref[k] + p.theta_acc[k]) *
+                                   (1.0f + since * (p.growth + 2.384185791e-7f)) * 1.0001f +
+                               nxw
+                         : INFINITY;
+    bool off = false;
     for (int nt = 0; nt < ntiles; ++nt) {
       const int col = nt * kRowsTile + cg * 32;
       float* Sb = s_block(p, row_base + col, k);
@@ -241,6 +277,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
           const float sn = fmaf(-g[c], ws, tail->brow[col + cc]);
           // drift in the units of the constraint: |change| * row scale
           drift = fmaxf(drift, fabsf(sn - sv[cc]) * tail->scale[col + cc]);
+          off = off || fabsf(sn - sv[cc]) > fmaf(tail->ks[col + cc], Eb, tail->jk[col + cc]);
           sv[cc] = sn;
         }
       }
@@ -249,6 +286,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
     if (lane == 0 && drift > 0.0f) atomicMax(p.drift_key, f64_key(static_cast<double>(drift)));
+    if (off && k < p.z) atomicOr(p.status, MHAR_ST_DRIFT);
   } else {
     // ---- chord epilogue, pass 1: partial (lambda_min, lambda_max) ---------------
     const int e = warp - 2;
@@ -256,6 +294,16 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const int cg = e >> 2;        // which 32-column group of each tile
     const int wl = q * 32 + lane; // walker within the strip
     const int k = strip * kWalkers + wl;
+    const float nd =
+        operand_norms<kEpiWarps * 32>(p.Dh, p.Xh, p.k_chunks * kTcKChunk, k, wl, cg, 1.0f, tail->nrm)
+            .nd2 +
+        ((p.corrn != nullptr && k < p.z) ? 4194304.0f * p.corrn[k] : 0.0f);
+    // Error bound of this walker's tracked slack, in units of Ks_i (see TcParams).
+    // (The last factors cover the FP32 sums of theta_acc and E itself.)
+    const float E = k < p.z ? (p.nx_ref[k] + p.theta_acc[k]) *
+                                  (1.0f + since * (p.growth + 2.384185791e-7f)) * 1.0001f
+                            : 0.0f;
+    if (cg == 0) tail->nd[wl] = nd;
     ChordAcc acc;
     acc.init();
     float s_cur[32], s_nxt[32];
@@ -273,11 +321,14 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           // Both the slack and G are in units of the row's power-of-two
-          // scale, so their ratio is the paper's lambda_i unchanged.
+          // scale, so their ratio is the paper's lambda_i unchanged.  The
+          // slack is lowered by its error bound and g pushed away from zero
+          // by its own (the margins of tc_common.cuh's slack32 / scan32).
+          const int r = col + 16 * half + c;
           const float gg = g[c];
-          const float ss = clamp_slack(s_cur[16 * half + c]);
-          acc.check(gg);
-          acc.add(ss, gg);
+          const float ss = clamp_slack(s_cur[16 * half + c] - fmaf(tail->ks[r], E, tail->jk[r]));
+          const float sd = __int_as_float(__float_as_int(nd) | (__float_as_int(gg) & 0x80000000));
+          acc.add(ss, fmaf(tail->kg[r], sd, gg));
         }
       }
 #pragma unroll
@@ -286,13 +337,11 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
     const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
     tail->part_hi[cg][wl] = hi;
-    const int bad = !acc.finite();
     named_bar<kEpiWarps * 32>();
     if (cg == 0) {
       tail->cta_lo[wl] = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
       tail->cta_hi[wl] = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
     }
-    if (bad) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
 
   // Partials of every CTA of the cluster are now in shared memory.
@@ -329,6 +378,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
           p.lmin[k] = L;
           p.lmax[k] = H;
           p.theta[k] = t;
+          p.theta_acc[k] += fabsf(t) * tail->nd[wl];
           if (flag) {
             atomicOr(p.status, flag);
             atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
@@ -431,15 +481,23 @@ __global__ void split_points_kernel(int z, int z_ld, int n, int n_ld, int k_pad,
   }
 }
 
-TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j) {
+TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j, bool check_drift) {
   TcParams p;
   p.mode = mode;
+  p.check_drift = check_drift ? 1 : 0;
   p.row_scale = c->d.row_scale;
   p.bS = c->d.bS;
   p.wscale = c->d.wscale;
   p.S = c->d.S;
   p.Xhi = c->d.Xhi;
   p.Xlo = c->d.Xlo;
+  p.rowk = c->d.rowk;
+  p.Xh = c->d.Xh;
+  p.corrn = c->d.corrn;
+  p.nx_ref = c->d.nx_ref;
+  p.theta_acc = c->d.theta_acc;
+  p.refresh_step = c->d.refresh_step;
+  p.growth = 1.0f / static_cast<float>(4 * mma_chain(c) + 4);
   p.Dh = c->d.Dh;
   p.Dl = c->d.Dl;
   p.sigma = c->d.sigma;
@@ -469,9 +527,9 @@ TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j) {
   return p;
 }
 
-cudaError_t launch_walker_tc(mhar_ctx* c, int mode, int j) {
+cudaError_t launch_walker_tc(mhar_ctx* c, int mode, int j, bool check_drift = false) {
   const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
-  const TcParams p = make_params(c, plan, mode, j);
+  const TcParams p = make_params(c, plan, mode, j, check_drift);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan->C, plan->strips, 1);
   cfg.blockDim = dim3(kThreadsTc, 1, 1);
@@ -542,10 +600,10 @@ cudaError_t launch_split_points(mhar_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_tc(mhar_ctx* c) {
+cudaError_t launch_refresh_tc(mhar_ctx* c, bool check_drift) {
   cudaError_t e = launch_split_points(c);
   if (e != cudaSuccess) return e;
-  return launch_walker_tc(c, kModeRefresh, 0);
+  return launch_walker_tc(c, kModeRefresh, 0, check_drift);
 }
 
 int tc_plan_strips(const mhar_ctx* c) { return static_cast<const TcPlan*>(c->tc)->strips; }

@@ -57,7 +57,7 @@ constexpr int kMaxCluster = 8;
 constexpr uint32_t kOpCol = 256;                     // first TMEM column of the walker operands
 
 struct TsParams {
-  const float* bS;          // m_pad: b_i / row_scale_i
+  const float* rows;        // 3 m_pad: b_i / row_scale_i and the error bounds (row_block)
   const float* wscale;      // z_ld
   const __half* Xh;         // z_ld x k_pad (operands copied into TMEM at start)
   const __half* Xl;
@@ -89,6 +89,7 @@ struct alignas(16) TsTail {
   float theta_s[kWalkers];
   double theta_u[kWalkers];           // the chord's uniform u (Philox stream 1), drawn early
   unsigned int red[kWalkers];
+  float nrm[3][kWalkers];             // each walker's ||d_hat||_2, ||x_hat||_2, max |d_hat|
   float gs[kWalkers * kMaxPcRank];    // low-rank normals of a preconditioned draw
 };
 
@@ -235,6 +236,29 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     tc_fence_before();
     // Operands ready: release the MMA warp (the producer never waits on this).
     asm volatile("bar.arrive 2, %0;" ::"n"((kEpiWarps + 1) * 32) : "memory");
+    if (op == 0 || op == 2) {
+      // The 2-norm bound of the walker's direction (op 0) or scaled point
+      // (op 2) from its FP16 hi row, for the chord's error margins.
+      // Sums of squares in chunk order: the same bits as operand_norms in the
+      // shared-memory-operand kernels.
+      float ss = 0.0f, mx = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint4 u = make_uint4(r0[4 * i], r0[4 * i + 1], r0[4 * i + 2], r0[4 * i + 3]);
+        ss += sumsq8(u);
+        mx = fmaxf(mx, absmax8(u));
+      }
+      if (p.k_pad > 64) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint4 u = make_uint4(r1[4 * i], r1[4 * i + 1], r1[4 * i + 2], r1[4 * i + 3]);
+          ss += sumsq8(u);
+          mx = fmaxf(mx, absmax8(u));
+        }
+      }
+      tail->nrm[op >> 1][q * 32 + lane] = norm_bound(ss);
+      if (op == 0) tail->nrm[2][q * 32 + lane] = mx * 1.00390625f;
+    }
   }
 
   if (warp == 0) {
@@ -293,8 +317,8 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int e = warp - 2;
     const int q = warp & 3;
     const int cg = e >> 2;              // 32-column group of each 128-column tile
-    const float* bS_rows = p.bS + row_base + cg * 32;
-    if (lane == 0 && ntiles > 0) prefetch_l1(bS_rows);
+    const int row0 = row_base + cg * 32;
+    if (lane == 0 && ntiles > 0) prefetch_l1(row_block(p.rows, row0));
     // This thread's walker-side item, copied to shared memory in the background.
     walker_tail_stage<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
                                       static_cast<int>(threadIdx.x) - 64,
@@ -313,6 +337,15 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
     const float ws = p.wscale[k];
+    // The operand norms of this thread's walker (written by the warps that
+    // loaded the operands into tensor memory, before the draw above).
+    named_bar<kEpiWarps * 32>();
+    WalkerNorms wn;
+    wn.nd2 = tail->nrm[0][wl];
+    wn.nxw2 = ws * tail->nrm[1][wl];
+    wn.ws = ws;
+    wn.ndinf = tail->nrm[2][wl];
+    if (k < p.z) add_correction(p.wt, k, wn);
     ChordAcc acc;
     acc.init();
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -320,7 +353,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     for (int nt = 0; nt < ntiles; ++nt) {
       // P first (its pass ends first), then G; each accumulator is released
       // as soon as it is in registers.
-      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(bS_rows + (nt + 1) * kTile);
+      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kTile));
       float sv[32], gv[32];
       mbar_wait(&tail->p_full, nt & 1, timed_out, p.err);
       tc_fence_after();
@@ -329,14 +362,16 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       __syncwarp();
       if (lane == 0) arrive(&tail->p_empty);
       // The slacks while the G pass finishes.
-      slack32(sv, bS_rows + nt * kTile, ws, acc);
+      float fx, fd;
+      wn.pick(p.rows, row0 + nt * kTile, fx, fd);
+      slack32(sv, p.rows, row0 + nt * kTile, ws, fx);
       mbar_wait(&tail->g_full, nt & 1, timed_out, p.err);
       tc_fence_after();
       tmem_ld32(gcol, gv);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) arrive(&tail->g_empty);
-      scan32(sv, gv, acc);
+      scan32(sv, gv, p.rows, row0 + nt * kTile, fd, acc);
     }
     const float lo = acc.lo_all(), hi = acc.hi_all();
     tail->part_lo[cg][wl] = lo;
@@ -352,7 +387,6 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
         st_dsmem(&tail->recv_hi[rank][wl], r, H);
       }
     }
-    if (!acc.finite()) atomicOr(p.status, MHAR_ST_NONFINITE);
   }
 
   // Every push is visible after this barrier; no remote access follows it.
@@ -473,7 +507,7 @@ cudaError_t launch_recompute_ts(mhar_ctx* c, int j) {
   const TcPlan* plan = static_cast<const TcPlan*>(c->tc);
   const TsShape s = ts_shape(c, plan);
   TsParams p;
-  p.bS = c->d.bS;
+  p.rows = c->d.rows;
   p.wscale = c->d.wscale;
   p.Xh = c->d.Xh;
   p.Xl = c->d.Xl;

@@ -16,9 +16,23 @@
 #include "mhar_device.cuh"
 #include "mhar_internal.h"
 
+thread_local char g_null_err[512] = {0};
+
+namespace mhar {
+void set_null_error(const char* msg) {
+  if (!msg) {
+    g_null_err[0] = 0;
+    return;
+  }
+  snprintf(g_null_err, sizeof(g_null_err), "%s", msg);
+}
+}  // namespace mhar
+
 namespace {
 
 constexpr int kMaxEqualities = 32;
+
+void remember_create_error(const char* msg) { mhar::set_null_error(msg); }
 
 void set_err(mhar_ctx* c, const char* fmt, ...) {
   if (!c) return;
@@ -80,8 +94,9 @@ bool recompute(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_RECOM
 
 void free_all(mhar_ctx* c) {
   mhar::DeviceBuffers& d = c->d;
-  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.AE64, d.AE32, d.bE64, d.Lchol, d.Ah, d.Al,
-                  d.row_scale, d.bS, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.Xh, d.Xl, d.wscale, d.Dh2, d.Dl2,
+  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.kr32, d.AE64, d.AE32, d.bE64,
+                  d.Lchol, d.Ah, d.Al, d.row_scale, d.bS, d.rows, d.rowk, d.nx_ref, d.theta_acc,
+                  d.refresh_step, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.corrn, d.Xh, d.Xl, d.wscale, d.Dh2, d.Dl2,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
                   d.emit, d.check, d.pc_delta64, d.pc_U64, d.pc_delta32, d.pc_U32, d.sigma};
   for (void* p : ptrs)
@@ -255,7 +270,11 @@ int advance(mhar_ctx* c, int64_t count) {
   return MHAR_OK;
 }
 
-int refresh(mhar_ctx* c) {
+// Stored-slack mode: S = b - A X from the current points.  `periodic`: the
+// refresh of a run, whose tracked slack it also checks against the tracked
+// error bound (MHAR_ST_DRIFT when exceeded); otherwise the slack is new
+// (creation, a new state or preconditioner) and there is nothing to check.
+int refresh(mhar_ctx* c, bool periodic = false) {
   if (c->mE > 0) {
     MHAR_CUDA(mhar::launch_reproject(c), "re-projection kernel");
     ++c->launches;
@@ -264,9 +283,11 @@ int refresh(mhar_ctx* c) {
     MHAR_CUDA(mhar::launch_refresh_simt(c), "slack refresh kernel");
     ++c->launches;
   } else {
-    MHAR_CUDA(mhar::launch_refresh_tc(c), "tensor-core slack refresh");
+    MHAR_CUDA(mhar::launch_refresh_tc(c, periodic), "tensor-core slack refresh");
     c->launches += 2;
   }
+  MHAR_CUDA(mhar::launch_stored_reset(c), "slack error reset");
+  ++c->launches;
   c->since_refresh = 0;
   return MHAR_OK;
 }
@@ -324,13 +345,146 @@ int alloc_preconditioner(mhar_ctx* c) {
   return MHAR_OK;
 }
 
-int set_unit_sigma(mhar_ctx* c) {
+int set_sigma(mhar_ctx* c, const std::vector<float>& sig) {
+  c->sigma_host = sig;
   if (!c->d.sigma) return MHAR_OK;
-  std::vector<float> ones(c->n_ld, 1.0f);
-  MHAR_CUDA(cudaMemcpyAsync(c->d.sigma, ones.data(), sizeof(float) * ones.size(),
+  c->unit_sigma = true;
+  for (float v : sig) c->unit_sigma = c->unit_sigma && v == 1.0f;
+  MHAR_CUDA(cudaMemcpyAsync(c->d.sigma, sig.data(), sizeof(float) * sig.size(),
                             cudaMemcpyHostToDevice, c->stream), "copy sigma");
   MHAR_CUDA(cudaStreamSynchronize(c->stream), "sigma sync");
   return MHAR_OK;
+}
+
+// Column scales of A: sigma_j = 2^-e_j with max_i |a_ij| = f 2^e_j, f in
+// [0.5, 1), then divided by the largest of them (so max sigma = 1) and kept
+// >= 2^-13, so that a unit normal divided by sigma stays inside the FP16
+// range (|h| <= 6.8 for the 32-bit uniforms of the draw).  All-zero columns
+// get 1.  n_ld entries, 1 beyond n.
+std::vector<float> column_scales(const double* A, int m, int n, int n_ld) {
+  std::vector<double> colmax(n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j)
+      colmax[j] = std::max(colmax[j], std::fabs(A[static_cast<size_t>(i) * n + j]));
+  std::vector<float> sig(n_ld, 1.0f);
+  double smax = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    if (colmax[j] > 0.0) {
+      int e = 0;
+      std::frexp(colmax[j], &e);
+      v = std::ldexp(1.0, -e);
+    }
+    sig[j] = static_cast<float>(v);
+    smax = std::max(smax, v);
+  }
+  for (int j = 0; j < n; ++j)
+    sig[j] = std::max(static_cast<float>(sig[j] / smax), 0x1p-13f);
+  return sig;
+}
+
+// Typical 2-norm and max-norm of a scaled direction d / sigma when d_i has
+// variance var_i (1 for isotropic directions): sqrt(sum var_i / sigma_i^2)
+// and 3 max sqrt(var_i) / sigma_i.  They only choose the bound form of each
+// 32-row block (row_blocks_kernel); the bounds themselves use the actual
+// norms of every walker's direction.
+void direction_norms(mhar_ctx* c, const std::vector<double>& var) {
+  const std::vector<float>& sig = c->sigma_host;
+  double s2 = 0.0, mx = 0.0;
+  for (int i = 0; i < c->n; ++i) {
+    const double v = var.empty() ? 1.0 : var[i];
+    const double r = std::sqrt(v) / static_cast<double>(sig[i]);
+    s2 += r * r;
+    mx = std::max(mx, r);
+  }
+  c->dir_norm2 = std::max(std::sqrt(s2), 1e-30);
+  c->dir_norminf = std::max(3.0 * mx, 1e-30);
+}
+
+// Coordinate scales with a preconditioner (delta: n_ld values, U: n_ld x 32,
+// zero beyond its rank).  Tensor-core modes: A's column scales times one
+// power of two c that brings the largest typical |d_i| / sigma_i near 1; then
+// each sigma_i at most 2^8 sd_i (so d_i / sigma_i is well above the FP16
+// subnormals) and at least 6.8 l1_i / 65504 rounded up (|d_i| <= 6.8 (delta_i
+// + sum_q |U_iq|) for the 32-bit uniforms of the draw, so the scaled
+// direction stays inside the FP16 range); sd_i^2 = delta_i^2 + (U U^T)_ii,
+// l1_i = delta_i + sum_q |U_iq|.  The CUDA-core modes keep A's column scales
+// (their margins only need some sigma).
+int precond_scales(mhar_ctx* c, const double* delta, const double* U) {
+  const int n = c->n, R = mhar::kMaxPcRank;
+  std::vector<double> sd(n, 0.0), l1(n, 0.0), var(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double v = delta[i] * delta[i], a1 = delta[i];
+    for (int q = 0; q < R; ++q) {
+      const double u = U[static_cast<size_t>(i) * R + q];
+      v += u * u;
+      a1 += std::fabs(u);
+    }
+    var[i] = v;
+    sd[i] = std::sqrt(v);
+    l1[i] = a1;
+  }
+  std::vector<float> sig = c->sigma_A;
+  if (mixed(c)) {
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) rmax = std::max(rmax, sd[i] / c->sigma_A[i]);
+    int ec = 0;
+    if (rmax > 0.0 && std::isfinite(rmax)) std::frexp(rmax, &ec);
+    for (int i = 0; i < n; ++i) {
+      double v = std::ldexp(static_cast<double>(c->sigma_A[i]), ec);
+      if (sd[i] > 0.0) {
+        int e = 0;
+        std::frexp(sd[i] * 256.0, &e);
+        v = std::min(v, std::ldexp(1.0, e - 1));
+      }
+      const double lo = 6.8 * l1[i] / 65504.0;
+      if (lo > 0.0) {
+        int e = 0;
+        std::frexp(lo, &e);
+        v = std::max(v, std::ldexp(1.0, e));
+      }
+      sig[i] = static_cast<float>(v);
+    }
+  }
+  int rc = set_sigma(c, sig);
+  if (rc) return rc;
+  direction_norms(c, var);
+  return MHAR_OK;
+}
+
+// FP32 mode: b lowered by 3 u |b_i| and the row bounds of chord_simt_kernel
+// (kernels_simt.cu), K_i,2 = gamma ||a_i sigma||_2 and K_i,1 = gamma
+// ||a_i sigma||_1 with gamma = gamma_{nnz_i + 4} (products of exact zeros add
+// nothing), and ||a_i sigma||_2 itself.  kr[3 i .. 3 i + 2].
+void simt_bounds(const double* A, const double* b, int m, int n, const std::vector<float>& sig,
+                 std::vector<float>* bm, std::vector<float>* kr) {
+  const double u = 0x1p-24;
+  bm->resize(m);
+  kr->resize(3 * static_cast<size_t>(m));
+  auto up = [](double v) {
+    float f = static_cast<float>(v);
+    if (static_cast<double>(f) < v) f = std::nextafter(f, INFINITY);
+    return f;
+  };
+  for (int i = 0; i < m; ++i) {
+    double s2 = 0.0, s1 = 0.0;
+    int nnz = 0;
+    for (int j = 0; j < n; ++j) {
+      const double v = A[static_cast<size_t>(i) * n + j] * static_cast<double>(sig[j]);
+      s2 += v * v;
+      s1 += std::fabs(v);
+      nnz += v != 0.0;
+    }
+    const double k = static_cast<double>(nnz + 4);
+    const double gamma = k * u / (1.0 - k * u) * (1.0 + 1e-6);
+    (*kr)[3 * i] = up(gamma * std::sqrt(s2));
+    (*kr)[3 * i + 1] = up(gamma * s1);
+    (*kr)[3 * i + 2] = up(std::sqrt(s2) * (1.0 + 1e-6));
+    const double lb = b[i] - 3.0 * u * std::fabs(b[i]);
+    float bt = static_cast<float>(lb);
+    if (static_cast<double>(bt) > lb) bt = std::nextafter(bt, -INFINITY);
+    (*bm)[i] = bt;
+  }
 }
 
 int reset_drift(mhar_ctx* c) {
@@ -341,9 +495,29 @@ int reset_drift(mhar_ctx* c) {
   return MHAR_OK;
 }
 
+// FP64 audit of the running walkers (opts.audit_every): folds into the
+// running maxima at check keys 3 and 4.
+int audit(mhar_ctx* c) {
+  const int w = c->opts.audit_walkers > 0 ? c->opts.audit_walkers : c->z;
+  MHAR_CUDA(mhar::launch_check(c, w, reinterpret_cast<unsigned long long*>(c->d.check) + 3),
+            "audit kernel");
+  ++c->launches;
+  ++c->audits;
+  c->since_audit = 0;
+  return MHAR_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mhar_status_code(int32_t status_bits, int32_t wait_expired) {
+  if (wait_expired) return MHAR_E_TIMEOUT;
+  if (status_bits & MHAR_ST_NONFINITE) return MHAR_E_NONFINITE;
+  if (status_bits & MHAR_ST_DRIFT) return MHAR_E_INFEASIBLE_DRIFT;
+  if (status_bits & MHAR_ST_UNBOUNDED) return MHAR_E_UNBOUNDED;
+  return MHAR_OK;
+}
 
 void mhar_default_opts(mhar_opts* o) {
   if (!o) return;
@@ -367,6 +541,8 @@ const char* mhar_strerror(int code) {
     case MHAR_E_CUDA: return "MHAR_E_CUDA";
     case MHAR_E_RANK: return "MHAR_E_RANK";
     case MHAR_E_UNSUPPORTED: return "MHAR_E_UNSUPPORTED";
+    case MHAR_E_TIMEOUT: return "MHAR_E_TIMEOUT";
+    case MHAR_E_INFEASIBLE_DRIFT: return "MHAR_E_INFEASIBLE_DRIFT";
     default: return "MHAR_E_UNKNOWN";
   }
 }
@@ -379,7 +555,7 @@ const char* mhar_kernel_name(const mhar_ctx* c) {
 }
 
 const char* mhar_last_error(const mhar_ctx* c) {
-  if (!c) return mhar::noalloc_last_error();
+  if (!c) return g_null_err[0] ? g_null_err : "no error";
   return c->err[0] ? c->err : "no error";
 }
 
@@ -459,16 +635,26 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
                             c->stream), "copy A");
   MHAR_CUDA(cudaMemcpyAsync(d.b64, b, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream),
             "copy b");
+  // Column scales of A (every mode) and the CUDA-core modes' rounding bounds.
+  c->sigma_A = column_scales(A, m, n, c->n_ld);
+  if ((rc = dmalloc(c, &d.sigma, c->n_ld)) || (rc = set_sigma(c, c->sigma_A))) return rc;
+  direction_norms(c, {});
   if (c->opts.precision == MHAR_FP32) {
     std::vector<float> Af(Ap.begin(), Ap.end());
-    std::vector<float> bf(b, b + m);
-    if ((rc = dmalloc(c, &d.A32, Af.size())) || (rc = dmalloc(c, &d.b32, m))) return rc;
+    std::vector<float> bf, kr;
+    simt_bounds(A, b, m, n, c->sigma_A, &bf, &kr);
+    if ((rc = dmalloc(c, &d.A32, Af.size())) || (rc = dmalloc(c, &d.b32, m)) ||
+        (rc = dmalloc(c, &d.kr32, kr.size())))
+      return rc;
     MHAR_CUDA(cudaMemcpyAsync(d.A32, Af.data(), sizeof(float) * Af.size(), cudaMemcpyHostToDevice,
                               c->stream), "copy A32");
     MHAR_CUDA(cudaMemcpyAsync(d.b32, bf.data(), sizeof(float) * m, cudaMemcpyHostToDevice,
                               c->stream), "copy b32");
+    MHAR_CUDA(cudaMemcpyAsync(d.kr32, kr.data(), sizeof(float) * kr.size(),
+                              cudaMemcpyHostToDevice, c->stream), "copy bounds");
     MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
   }
+
   if (mE > 0) {
     std::vector<double> AEp(static_cast<size_t>(mE) * c->n_ld, 0.0);
     for (int e = 0; e < mE; ++e)
@@ -492,8 +678,14 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       (rc = dmalloc(c, &d.lmin, z)) || (rc = dmalloc(c, &d.lmax, z)) ||
       (rc = dmalloc(c, &d.theta, z)) || (rc = dmalloc(c, &d.status, 2)) ||
       (rc = dmalloc(c, &d.counters, 2)) || (rc = dmalloc(c, &d.step, 1)) ||
-      (rc = dmalloc(c, &d.emit, static_cast<size_t>(z) * n)) || (rc = dmalloc(c, &d.check, 4)))
+      (rc = dmalloc(c, &d.emit, static_cast<size_t>(z) * n)) || (rc = dmalloc(c, &d.check, 6)))
     return rc;
+  {
+    // Audit keys: running max violation from -inf, running residual from 0.
+    const unsigned long long init[2] = {host_key(-INFINITY), host_key(0.0)};
+    MHAR_CUDA(cudaMemcpyAsync(reinterpret_cast<unsigned long long*>(d.check) + 3, init, sizeof(init),
+                              cudaMemcpyHostToDevice, c->stream), "audit init");
+  }
   const size_t zn = static_cast<size_t>(z) * c->n_ld;
   if (mode == 0) {
     if ((rc = dmalloc(c, &d.X64, zn)) || (rc = dmalloc(c, &d.D64, zn))) return rc;
@@ -501,21 +693,27 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     if ((rc = dmalloc(c, &d.Xhi, zn)) || (rc = dmalloc(c, &d.Xlo, zn))) return rc;
     if (c->opts.precision == MHAR_FP32 || mE > 0)
       if ((rc = dmalloc(c, &d.D32, zn))) return rc;
-    if (mE > 0 && (rc = dmalloc(c, &d.corr, static_cast<size_t>(z) * mE))) return rc;
+    if (mE > 0 && ((rc = dmalloc(c, &d.corr, static_cast<size_t>(z) * mE)) ||
+                   (rc = dmalloc(c, &d.corrn, z))))
+      return rc;
   }
   if (mixed(c)) {
     const size_t opnd = static_cast<size_t>(c->m_pad) * c->k_pad;
     const size_t dsz = static_cast<size_t>(z_ld) * c->k_pad;
     if ((rc = dmalloc(c, &d.Ah, opnd)) || (rc = dmalloc(c, &d.Al, opnd)) ||
         (rc = dmalloc(c, &d.row_scale, c->m_pad)) || (rc = dmalloc(c, &d.bS, c->m_pad)) ||
+        (rc = dmalloc(c, &d.rows, static_cast<size_t>(4) * c->m_pad)) ||
+        (rc = dmalloc(c, &d.rowk, static_cast<size_t>(4) * c->m_pad)) ||
         (rc = dmalloc(c, &d.Dh, dsz)) || (rc = dmalloc(c, &d.Dl, dsz)) ||
         (rc = dmalloc(c, &d.Xh, dsz)) || (rc = dmalloc(c, &d.Xl, dsz)) ||
         (rc = dmalloc(c, &d.wscale, z_ld)))
       return rc;
-    if (stored(c) && (rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld))) return rc;
+    if (stored(c) && ((rc = dmalloc(c, &d.S, static_cast<size_t>(c->m_pad) * z_ld)) ||
+                      (rc = dmalloc(c, &d.nx_ref, z)) || (rc = dmalloc(c, &d.theta_acc, z)) ||
+                      (rc = dmalloc(c, &d.refresh_step, 1))))
+      return rc;
     if (recompute(c) && ((rc = dmalloc(c, &d.Dh2, dsz)) || (rc = dmalloc(c, &d.Dl2, dsz))))
       return rc;
-    if ((rc = dmalloc(c, &d.sigma, c->n_ld)) || (rc = set_unit_sigma(c))) return rc;
   }
 
   // Projector factor on the device.
@@ -587,7 +785,9 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
     rc = MHAR_E_UNSUPPORTED;
   } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
              c->opts.refresh_k < 0 || c->opts.graph_chunk < 0 || c->opts.emit_walkers < 0 ||
-             c->opts.emit_walkers > z || c->opts.schedule < 0 || c->opts.schedule > 2) {
+             c->opts.emit_walkers > z || c->opts.schedule < 0 || c->opts.schedule > 2 ||
+             c->opts.audit_every < 0 || c->opts.audit_walkers < 0 ||
+             c->opts.audit_walkers > z || c->opts.reserved != 0) {
     set_err(c, "bad option (precision=%d refresh_k=%d graph_chunk=%d emit_walkers=%d)",
             c->opts.precision, c->opts.refresh_k, c->opts.graph_chunk, c->opts.emit_walkers);
     rc = MHAR_E_ARG;
@@ -600,11 +800,9 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
     rc = create_impl(c, A, b, AE, bE, x0);
   }
   if (rc != MHAR_OK) {
-    // Keep the message: hand back a context that only reports the error.
-    char msg[512];
-    std::memcpy(msg, c->err, sizeof(msg));
+    // The message survives the context for mhar_last_error(NULL).
+    remember_create_error(c->err);
     mhar_destroy(c);
-    fprintf(stderr, "mhar_create: %s (%s)\n", msg, mhar_strerror(rc));
     return rc;
   }
   *out = c;
@@ -628,16 +826,22 @@ int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
   if (stored(c) && (rc = reset_drift(c))) return rc;
   int64_t done = 0, emitted = 0;
   const int64_t k = stored(c) ? c->opts.refresh_k : 0;
+  const int64_t au = c->opts.audit_every;
   while (done < steps) {
     int64_t adv = steps - done;
     if (thin > 0) adv = std::min<int64_t>(adv, thin - (done % thin));
     if (k > 0) adv = std::min<int64_t>(adv, k - c->since_refresh);
+    if (au > 0) adv = std::min<int64_t>(adv, au - c->since_audit);
     if ((rc = advance(c, adv))) return rc;
     done += adv;
     c->step += static_cast<uint64_t>(adv);
+    if (au > 0) {
+      c->since_audit += adv;
+      if (c->since_audit >= au && (rc = audit(c))) return rc;
+    }
     if (k > 0) {
       c->since_refresh += adv;
-      if (c->since_refresh >= k && (rc = refresh(c))) return rc;
+      if (c->since_refresh >= k && (rc = refresh(c, true))) return rc;
     }
     if (thin > 0 && done % thin == 0 && emitted < nsamp) {
       if ((rc = emit_to(c, out + static_cast<size_t>(emitted) * emit_count(c) * c->n,
@@ -657,19 +861,19 @@ int mhar_run(mhar_ctx* c, int64_t steps, int64_t thin, double* out) {
     c->last_drift = host_unkey(kd);
   }
   c->status_bits |= st[0];
-  if (st[1]) {
-    set_err(c, "tensor-core pipeline wait timed out");
-    return MHAR_E_CUDA;
+  const int code = mhar_status_code(st[0], st[1]);
+  switch (code) {
+    case MHAR_E_TIMEOUT: set_err(c, "a tensor-core pipeline wait expired"); break;
+    case MHAR_E_NONFINITE: set_err(c, "non-finite slack or direction met"); break;
+    case MHAR_E_INFEASIBLE_DRIFT:
+      set_err(c, "a refresh found the tracked slack beyond its error bound");
+      break;
+    case MHAR_E_UNBOUNDED:
+      set_err(c, "a walker met a chord open on one side: the body is unbounded");
+      break;
+    default: break;
   }
-  if (st[0] & MHAR_ST_NONFINITE) {
-    set_err(c, "non-finite slack or direction met");
-    return MHAR_E_NONFINITE;
-  }
-  if (st[0] & MHAR_ST_UNBOUNDED) {
-    set_err(c, "a walker met a chord open on one side: the body is unbounded");
-    return MHAR_E_UNBOUNDED;
-  }
-  return MHAR_OK;
+  return code;
 }
 
 int mhar_get_state(const mhar_ctx* cc, double* X, uint64_t* step) {
@@ -722,7 +926,8 @@ int mhar_set_preconditioner(mhar_ctx* c, const double* delta, const double* U, i
   int rc = MHAR_OK;
   if (!delta) {
     if (c->pc_rank < 0) return MHAR_OK;
-    if ((rc = set_unit_sigma(c))) return rc;
+    if ((rc = set_sigma(c, c->sigma_A))) return rc;
+    direction_norms(c, {});
     return adopt_preconditioner(c, -1);
   }
   if (rank < 0 || rank > mhar::kMaxPcRank || (rank > 0 && !U)) {
@@ -742,21 +947,10 @@ int mhar_set_preconditioner(mhar_ctx* c, const double* delta, const double* U, i
     }
   if ((rc = alloc_preconditioner(c))) return rc;
   std::vector<double> d64(nl, 0.0), u64(static_cast<size_t>(nl) * R, 0.0);
-  std::vector<float> sig(nl, 1.0f);
   for (int i = 0; i < n; ++i) {
     d64[i] = delta[i];
-    double var = delta[i] * delta[i];
-    for (int q = 0; q < rank; ++q) {
-      const double u = U[static_cast<size_t>(i) * rank + q];
-      u64[static_cast<size_t>(i) * R + q] = u;
-      var += u * u;
-    }
-    // Coordinate scale 2^e with sqrt(var) = f 2^e, f in [0.5, 1).
-    if (var > 0.0 && std::isfinite(var)) {
-      int e = 0;
-      std::frexp(std::sqrt(var), &e);
-      sig[i] = static_cast<float>(std::ldexp(1.0, e));
-    }
+    for (int q = 0; q < rank; ++q)
+      u64[static_cast<size_t>(i) * R + q] = U[static_cast<size_t>(i) * rank + q];
   }
   std::vector<float> d32(d64.begin(), d64.end()), u32(u64.begin(), u64.end());
   mhar::DeviceBuffers& d = c->d;
@@ -764,8 +958,7 @@ int mhar_set_preconditioner(mhar_ctx* c, const double* delta, const double* U, i
   MHAR_CUDA(cudaMemcpy(d.pc_U64, u64.data(), sizeof(double) * u64.size(), cudaMemcpyHostToDevice), "copy U");
   MHAR_CUDA(cudaMemcpy(d.pc_delta32, d32.data(), sizeof(float) * nl, cudaMemcpyHostToDevice), "copy delta");
   MHAR_CUDA(cudaMemcpy(d.pc_U32, u32.data(), sizeof(float) * u32.size(), cudaMemcpyHostToDevice), "copy U");
-  if (d.sigma)
-    MHAR_CUDA(cudaMemcpy(d.sigma, sig.data(), sizeof(float) * nl, cudaMemcpyHostToDevice), "copy sigma");
+  if ((rc = precond_scales(c, d64.data(), u64.data()))) return rc;
   return adopt_preconditioner(c, rank);
 }
 
@@ -842,6 +1035,14 @@ int mhar_fit_preconditioner(mhar_ctx* c, int64_t warmup, int32_t snapshots, int3
     set_err(c, "the warm-up covariance is not finite");
     return MHAR_E_NONFINITE;
   }
+  // The coordinate scales follow the fitted (delta, U) by the rule of
+  // mhar_set_preconditioner.
+  std::vector<double> d64(c->n_ld), u64(static_cast<size_t>(c->n_ld) * mhar::kMaxPcRank);
+  MHAR_CUDA(cudaMemcpy(d64.data(), c->d.pc_delta64, sizeof(double) * d64.size(),
+                       cudaMemcpyDeviceToHost), "copy delta");
+  MHAR_CUDA(cudaMemcpy(u64.data(), c->d.pc_U64, sizeof(double) * u64.size(),
+                       cudaMemcpyDeviceToHost), "copy U");
+  if ((rc = precond_scales(c, d64.data(), u64.data()))) return rc;
   return adopt_preconditioner(c, rank);
 }
 
@@ -861,6 +1062,13 @@ int mhar_get_stats(const mhar_ctx* c, mhar_stats* s) {
   s->max_violation = c->max_violation;
   s->eq_residual = c->eq_residual;
   s->kernel_launches = c->launches;
+  unsigned long long keys[2];
+  e = cudaMemcpy(keys, reinterpret_cast<unsigned long long*>(c->d.check) + 3, sizeof(keys),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return MHAR_E_CUDA;
+  s->run_max_violation = host_unkey(keys[0]);
+  s->run_eq_residual = c->mE > 0 ? host_unkey(keys[1]) : 0.0;
+  s->audits = c->audits;
   return MHAR_OK;
 }
 
@@ -938,12 +1146,13 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
       cudaError_t e2 = cudaSuccess;
       if (c->mE > 0) e2 = mhar::launch_reproject(c);
       if (e2 == cudaSuccess)
-        e2 = c->opts.refresh_fp64 ? mhar::launch_refresh_simt(c) : mhar::launch_refresh_tc(c);
+        e2 = c->opts.refresh_fp64 ? mhar::launch_refresh_simt(c) : mhar::launch_refresh_tc(c, false);
+      if (e2 == cudaSuccess) e2 = mhar::launch_stored_reset(c);
       return e2;
     };
     e = time_graph(c, ref, &t_ref);
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
-    c->launches += (c->mE > 0 ? 1 : 0) + (c->opts.refresh_fp64 ? 1 : 2);
+    c->launches += (c->mE > 0 ? 1 : 0) + (c->opts.refresh_fp64 ? 1 : 2) + 1;
     c->since_refresh = 0;
   }
   ms[0] = t_dir / iters;
@@ -952,12 +1161,25 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   return MHAR_OK;
 }
 
+int mhar_set_audit(mhar_ctx* c, int32_t every, int32_t walkers) {
+  if (!c) return MHAR_E_ARG;
+  if (every < 0 || walkers < 0 || walkers > c->z) {
+    set_err(c, "bad audit setting (every=%d walkers=%d, z=%d)", every, walkers, c->z);
+    return MHAR_E_ARG;
+  }
+  c->opts.audit_every = every;
+  c->opts.audit_walkers = walkers;
+  c->since_audit = 0;
+  return MHAR_OK;
+}
+
 int mhar_check(mhar_ctx* c, mhar_stats* s) {
   if (!c) return MHAR_E_ARG;
   const unsigned long long init[2] = {host_key(-INFINITY), host_key(0.0)};
   MHAR_CUDA(cudaMemcpyAsync(c->d.check, init, sizeof(init), cudaMemcpyHostToDevice, c->stream),
             "check init");
-  MHAR_CUDA(mhar::launch_check(c), "check kernel");
+  MHAR_CUDA(mhar::launch_check(c, c->z, reinterpret_cast<unsigned long long*>(c->d.check)),
+            "check kernel");
   unsigned long long res[2];
   MHAR_CUDA(cudaMemcpyAsync(res, c->d.check, sizeof(res), cudaMemcpyDeviceToHost, c->stream),
             "check copy");
@@ -984,6 +1206,7 @@ struct mhar_batch {
   int graph_len = 16;
   int64_t launches = 0;
   int64_t walker_steps = 0;
+  int64_t since_audit = 0;
   mhar_opts opts{};
   char err[512] = {0};
 };
@@ -1125,7 +1348,7 @@ int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
     rc = batch_set_shape(b, C);
   }
   if (rc != MHAR_OK) {
-    fprintf(stderr, "mhar_batch_create: %s (%s)\n", b->err, mhar_strerror(rc));
+    remember_create_error(b->err);
     mhar_batch_destroy(b);
     return rc;
   }
@@ -1184,12 +1407,23 @@ int mhar_batch_run(mhar_batch* b, int64_t steps, int64_t thin, double* const* ou
     if (e != cudaSuccess) return batch_cuda(b, e, "status reset");
   }
   int64_t done = 0, emitted = 0;
+  const int64_t au = b->opts.audit_every;
   while (done < steps) {
     int64_t adv = steps - done;
     if (thin > 0) adv = std::min<int64_t>(adv, thin - (done % thin));
+    if (au > 0) adv = std::min<int64_t>(adv, au - b->since_audit);
     int rc = batch_advance(b, adv);
     if (rc) return rc;
     done += adv;
+    if (au > 0 && (b->since_audit += adv) >= au) {
+      for (mhar_ctx* c : b->ctx) {
+        if ((rc = audit(c))) {
+          batch_err(b, "audit: %s", c->err);
+          return rc;
+        }
+      }
+      b->since_audit = 0;
+    }
     if (thin > 0 && done % thin == 0 && emitted < nsamp) {
       for (size_t q = 0; q < b->ctx.size(); ++q) {
         mhar_ctx* c = b->ctx[q];
@@ -1213,8 +1447,8 @@ int mhar_batch_run(mhar_batch* b, int64_t steps, int64_t thin, double* const* ou
     if (e != cudaSuccess) return batch_cuda(b, e, "status copy");
     c->status_bits |= st[0];
     if (st[1]) {
-      batch_err(b, "problem %zu: tensor-core pipeline wait timed out", q);
-      return MHAR_E_CUDA;
+      batch_err(b, "problem %zu: a tensor-core pipeline wait expired", q);
+      return MHAR_E_TIMEOUT;
     }
     if ((st[0] & MHAR_ST_NONFINITE) && worst == MHAR_OK) {
       batch_err(b, "problem %zu: non-finite slack or direction met", q);
@@ -1238,6 +1472,21 @@ int mhar_batch_check(mhar_batch* b, int32_t problem, mhar_stats* stats) {
   int rc = mhar_check(b->ctx[problem], stats);
   if (rc == MHAR_OK && stats) stats->kernel_launches += b->launches;  // the batch's own launches
   return rc;
+}
+
+int mhar_batch_set_audit(mhar_batch* b, int32_t every, int32_t walkers) {
+  if (!b) return MHAR_E_ARG;
+  for (mhar_ctx* c : b->ctx) {
+    const int rc = mhar_set_audit(c, every, walkers);
+    if (rc) {
+      batch_err(b, "%s", c->err);
+      return rc;
+    }
+  }
+  b->opts.audit_every = every;
+  b->opts.audit_walkers = walkers;
+  b->since_audit = 0;
+  return MHAR_OK;
 }
 
 const char* mhar_batch_last_error(const mhar_batch* b) {

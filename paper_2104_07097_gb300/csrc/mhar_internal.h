@@ -2,6 +2,7 @@
 // library's translation units.  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 
@@ -19,7 +20,8 @@ struct DeviceBuffers {
   double* A64 = nullptr;   // m x n_ld
   double* b64 = nullptr;   // m
   float* A32 = nullptr;    // m x n_ld (FP32 mode)
-  float* b32 = nullptr;    // m
+  float* b32 = nullptr;    // m (FP32 mode: lowered by 3 u |b_i|, see kernels_simt.cu)
+  float* kr32 = nullptr;   // 2 m (FP32 mode: the row bounds of chord_simt_kernel)
   double* AE64 = nullptr;  // mE x n_ld
   float* AE32 = nullptr;   // mE x n_ld
   double* bE64 = nullptr;  // mE
@@ -29,7 +31,12 @@ struct DeviceBuffers {
   __half* Ah = nullptr;    // m_pad x k_pad
   __half* Al = nullptr;    // m_pad x k_pad
   float* row_scale = nullptr; // m_pad: A[i,:] = row_scale[i] * (Ah + Al)[i,:]
-  float* bS = nullptr;     // m_pad (FP32 b / row_scale, 0 beyond m)
+  float* bS = nullptr;     // m_pad (FP32 b / row_scale, lowered, 0 beyond m)
+  // 4 m_pad: per 32-row block, bS (as above), then Ks (error bound of a_i . x
+  // per unit of the walker's point norm), then Kg (of a_i . d per unit of its
+  // direction norm), then the block's norm type; tc_common.cuh, row_block.
+  float* rows = nullptr;
+  float* rowk = nullptr;   // 4 m_pad: Ks_2, Kg_2, Ks_1, Kg_1 of every row (kernels_simt.cu)
 
   // Walker state.
   double* X64 = nullptr;   // z x n_ld          (FP64 mode)
@@ -46,9 +53,14 @@ struct DeviceBuffers {
   float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack / row_scale, blocked:
                            //  element (i, k) at ((i / 4) z_ld + k) 4 + i % 4)
   float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix)
+  float* corrn = nullptr;  // z                 (the same: ||A_E^T corr / sigma||_2 bound)
   __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
   __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
   float* wscale = nullptr; // z_ld              (mixed: power-of-two scale of each walker)
+  // Stored-slack mode: the tracked slack's error since the last refresh.
+  float* nx_ref = nullptr;       // z: ||x / sigma||_2 bound at the refresh
+  float* theta_acc = nullptr;    // z: sum |theta| ||d_hat||_2 since the refresh
+  uint64_t* refresh_step = nullptr;  // iteration counter at the refresh
 
   // Chord bookkeeping.
   unsigned long long* key_lo = nullptr;  // z: ordered key of lambda_min (atomic max)
@@ -60,19 +72,23 @@ struct DeviceBuffers {
   unsigned long long* counters = nullptr;  // [0] stalls, [1] unbounded
   uint64_t* step = nullptr;  // device iteration counter (graph replays read it)
   double* emit = nullptr;  // z x n staging for host output
-  double* check = nullptr; // [0] max violation, [1] eq residual, [2] drift
+  double* check = nullptr; // keys: [0] max violation, [1] eq residual, [2] drift,
+                           // [3], [4] running max violation / eq residual of the audits
 
   // Direction preconditioner d = P (delta .* h + U g) (allocated when set).
   double* pc_delta64 = nullptr;  // n_ld
   double* pc_U64 = nullptr;      // n_ld x 32, row i = U[i, :], zero beyond the rank
   float* pc_delta32 = nullptr;   // n_ld
   float* pc_U32 = nullptr;       // n_ld x 32
-  // Tensor-core modes: power-of-two scale of each coordinate.  The FP16
-  // operands hold x_i / sigma_i and d_i / sigma_i, and A's columns are
-  // multiplied by sigma_i, so A x and A d are unchanged while coordinates of
-  // very different size keep their relative precision.  All ones unless a
-  // preconditioner chose them.
-  float* sigma = nullptr;        // n_ld
+  // Power-of-two scale of each coordinate, from the columns of A (every
+  // column of A sigma has its largest entry in [0.5, 1) up to one common
+  // power of two) and, with a preconditioner, kept within the FP16 range of
+  // the scaled directions.  The tensor-core operands hold x_i / sigma_i and
+  // d_i / sigma_i and A's columns are multiplied by sigma_i, so A x and A d
+  // are unchanged while coordinates of very different size keep their
+  // relative precision; every mode bounds its rounding errors in these
+  // coordinates (Cauchy-Schwarz on |a_i sigma| . |x / sigma|).
+  float* sigma = nullptr;        // n_ld (1 beyond n)
 };
 
 }  // namespace mhar
@@ -105,6 +121,14 @@ struct mhar_ctx {
   // directions; `operands_fresh` says whether the FP16 operands of the next
   // iteration are in place (false after any change of state from the host).
   bool operands_fresh = false;
+  bool unit_sigma = true;      // every sigma_i == 1
+  std::vector<float> sigma_A;  // the column scales of A alone (host copy)
+  std::vector<float> sigma_host;  // the scales in force (host copy of d.sigma)
+  int64_t since_audit = 0;     // iterations since the last audit (opts.audit_every)
+  // Typical 2-norm and max-norm of a scaled direction d / sigma, for the
+  // choice of bound form per 32-row block (kernels_simt.cu, row_blocks_kernel).
+  double dir_norm2 = 1.0, dir_norminf = 1.0;
+  int64_t audits = 0;
   double last_drift = 0.0;
   double max_violation = 0.0;
   double eq_residual = 0.0;
@@ -113,6 +137,13 @@ struct mhar_ctx {
 };
 
 namespace mhar {
+
+// MMAs (K = 16) accumulated into one output of the tensor-core products: three
+// FP16 products per K step in the recompute mode, four in the stored mode.
+inline int mma_per_step(const mhar_ctx* c) {
+  return c->opts.precision == MHAR_MIXED_F16X3 ? 4 : 3;
+}
+inline int mma_chain(const mhar_ctx* c) { return mma_per_step(c) * (c->kdim / kTcK); }
 
 // ---- kernel launchers (kernels_simt.cu) -------------------------------------
 // Every launcher enqueues on ctx->stream and returns cudaGetLastError().
@@ -129,7 +160,12 @@ cudaError_t launch_advance(mhar_ctx* ctx, int steps);
 // Recompute mode: flags bit 1 split X, bit 2 draw D (for iteration step + j).
 cudaError_t launch_prep_walkers(mhar_ctx* ctx, int j, int flags);
 cudaError_t launch_emit(mhar_ctx* ctx, double* out_device, int walkers);  // walkers 0..walkers-1
-cudaError_t launch_check(mhar_ctx* ctx);
+// FP64 feasibility of walkers 0..walkers-1 into the keys at out_keys[0]
+// (max a_i x - b_i) and out_keys[1] (max |A_E x - b_E|).
+cudaError_t launch_check(mhar_ctx* ctx, int walkers, unsigned long long* out_keys);
+// Stored-slack mode, after a refresh: ||x / sigma|| of every walker, the
+// accumulated step sum reset, the refresh's iteration recorded.
+cudaError_t launch_stored_reset(mhar_ctx* ctx);
 cudaError_t launch_set_points(mhar_ctx* ctx, const double* X_dev);
 cudaError_t launch_prepare_tc_operands(mhar_ctx* ctx);
 cudaError_t launch_refresh_simt(mhar_ctx* ctx);
@@ -153,8 +189,11 @@ cudaError_t launch_fit_accumulate(mhar_ctx* ctx, FitScratch* f);
 cudaError_t launch_fit_factor(mhar_ctx* ctx, FitScratch* f, long long samples, int rank,
                               int power_iters);
 
-// ---- allocation-free chord entry point (noalloc.cu) ---------------------------
-const char* noalloc_last_error();
+// ---- errors without a context (mhar_api.cu) -----------------------------------
+// The message mhar_last_error(NULL) returns on this host thread: the last
+// failed mhar_create / mhar_batch_create, or the last mhar_chord_noalloc
+// (cleared when that call succeeds).  NULL clears it.
+void set_null_error(const char* msg);
 
 // ---- tensor-core path (kernels_tc.cu) ---------------------------------------
 int tc_plan_create(mhar_ctx* ctx);            // 0 or MHAR_E_*
@@ -162,7 +201,9 @@ int tc_plan_strips(const mhar_ctx* ctx);      // walker strips of 128
 int tc_plan_m_tiles(const mhar_ctx* ctx);     // row tiles of 128
 void tc_plan_destroy(mhar_ctx* ctx);
 cudaError_t launch_chord_tc(mhar_ctx* ctx, int j);
-cudaError_t launch_refresh_tc(mhar_ctx* ctx);       // X split + S = b - A X (2 launches)
+// X split + S = b - A X (2 launches); check_drift: flag MHAR_ST_DRIFT where the
+// tracked slack differs from the recomputed one by more than its error bound.
+cudaError_t launch_refresh_tc(mhar_ctx* ctx, bool check_drift);
 cudaError_t launch_split_points(mhar_ctx* ctx);     // X -> FP16 pair + per-walker scale
 
 // ---- recompute-slack tensor-core path (kernels_rc.cu) ------------------------

@@ -30,6 +30,7 @@ namespace {
 constexpr int kNoAllocMaxWalkers = 65536;
 constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
+constexpr unsigned long long kBadKey = ~0ull;   // a walker that met a non-finite value
 
 // Keys [0, max) fold lambda_min (atomic max), keys [max, 2 max) lambda_max
 // (atomic min).
@@ -37,7 +38,6 @@ static __device__ __align__(256) unsigned long long g_chord_scratch[2 * kNoAlloc
 
 std::mutex g_setup_mu;
 unsigned long long* g_scratch_ptr[kMaxDevices] = {nullptr};
-thread_local char g_noalloc_err[256] = {0};
 
 __device__ __forceinline__ double ninf() { return -__longlong_as_double(0x7ff0000000000000ll); }
 __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000ll); }
@@ -50,9 +50,13 @@ __global__ void noalloc_clear_kernel(int z, unsigned long long* keys) {
   }
 }
 
-// Section 4.4 on caller buffers: A (m x n), X and D (z x n), all FP64
-// row-major with no padding.  Tiles of 64 rows x 64 walkers; every block folds
-// its rows into the per-walker keys.
+// The chord of every walker on caller buffers: A (m x n), X and D (z x n),
+// all FP64 row-major with no padding.  For each row, the slack b_i - a_i . x
+// (counted as 0 when rounding makes it negative) over a_i . d gives one end
+// of the walker's chord; rows with a_i . d == 0 give none.  Tiles of 64 rows
+// x 64 walkers; every block folds its rows into the per-walker keys.  A
+// non-finite slack or product marks the walker (its lambda_min key becomes
+// kBadKey) and both of its chord ends come out NaN.
 __global__ void __launch_bounds__(kThreads)
 noalloc_chord_kernel(const double* __restrict__ A, const double* __restrict__ b,
                      const double* __restrict__ X, const double* __restrict__ D, int m, int n,
@@ -106,7 +110,11 @@ noalloc_chord_kernel(const double* __restrict__ A, const double* __restrict__ b,
       if (gi >= m) continue;
       double s = b[gi] - accS[r][c];
       const double g = accG[r][c];
-      if (!isfinite(s) || !isfinite(g)) continue;
+      if (!isfinite(s) || !isfinite(g)) {
+        lo = __longlong_as_double(0x7ff8000000000000ll);   // NaN: the walker is marked
+        hi = lo;
+        break;
+      }
       if (s < 0.0) s = 0.0;
       if (g > 0.0) {
         const double lam = s / g;
@@ -122,15 +130,22 @@ noalloc_chord_kernel(const double* __restrict__ A, const double* __restrict__ b,
   __syncthreads();
   if (tid < 64) {
     double lo = red_lo[0][tid], hi = red_hi[0][tid];
+    bool bad = isnan(lo);
 #pragma unroll
     for (int t = 1; t < 16; ++t) {
+      bad = bad || isnan(red_lo[t][tid]);
       lo = red_lo[t][tid] > lo ? red_lo[t][tid] : lo;
       hi = red_hi[t][tid] < hi ? red_hi[t][tid] : hi;
     }
     const int gw = w0 + tid;
     if (gw < z) {
-      if (!isinf(lo)) atomicMax(&keys[gw], mhar::f64_key(lo));
-      if (!isinf(hi)) atomicMin(&keys[kNoAllocMaxWalkers + gw], mhar::f64_key(hi));
+      if (bad) {
+        // The all-ones key is the largest, so no later atomicMax undoes it.
+        atomicMax(&keys[gw], kBadKey);
+      } else {
+        if (!isinf(lo)) atomicMax(&keys[gw], mhar::f64_key(lo));
+        if (!isinf(hi)) atomicMin(&keys[kNoAllocMaxWalkers + gw], mhar::f64_key(hi));
+      }
     }
   }
 }
@@ -139,13 +154,18 @@ __global__ void noalloc_finish_kernel(int z, const unsigned long long* keys, dou
                                       double* lmax) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < z) {
-    lmin[k] = mhar::f64_unkey(keys[k]);
-    lmax[k] = mhar::f64_unkey(keys[kNoAllocMaxWalkers + k]);
+    const unsigned long long klo = keys[k], khi = keys[kNoAllocMaxWalkers + k];
+    const bool bad = klo == kBadKey;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    lmin[k] = bad ? nan : mhar::f64_unkey(klo);
+    lmax[k] = bad ? nan : mhar::f64_unkey(khi);
   }
 }
 
 int fail(int code, const char* msg) {
-  snprintf(g_noalloc_err, sizeof(g_noalloc_err), "mhar_chord_noalloc: %s", msg);
+  char buf[320];
+  snprintf(buf, sizeof(buf), "mhar_chord_noalloc: %s", msg);
+  mhar::set_null_error(buf);
   return code;
 }
 
@@ -172,10 +192,6 @@ int scratch_for_current_device(unsigned long long** out) {
 
 }  // namespace
 
-namespace mhar {
-const char* noalloc_last_error() { return g_noalloc_err[0] ? g_noalloc_err : "no error"; }
-}  // namespace mhar
-
 extern "C" int mhar_chord_noalloc(const double* A, const double* b, int m, int n, const double* X,
                                   const double* D, int z, double* lmin, double* lmax,
                                   void* stream) {
@@ -187,16 +203,26 @@ extern "C" int mhar_chord_noalloc(const double* A, const double* b, int m, int n
              kNoAllocMaxWalkers);
     return fail(MHAR_E_ARG, msg);
   }
+  // An error left pending by earlier, unrelated work is not this call's: report
+  // it as such and launch nothing (it stays pending for its owner).
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "a CUDA error was already pending before the call (%s); nothing launched",
+             cudaGetErrorString(e));
+    return fail(MHAR_E_CUDA, msg);
+  }
   unsigned long long* keys = nullptr;
   int rc = scratch_for_current_device(&keys);
   if (rc != MHAR_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   noalloc_clear_kernel<<<(z + kThreads - 1) / kThreads, kThreads, 0, s>>>(z, keys);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(MHAR_E_CUDA, cudaGetErrorString(e));
   dim3 grid((m + 63) / 64, (z + 63) / 64);
   noalloc_chord_kernel<<<grid, kThreads, 0, s>>>(A, b, X, D, m, n, z, keys);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(MHAR_E_CUDA, cudaGetErrorString(e));
   noalloc_finish_kernel<<<(z + kThreads - 1) / kThreads, kThreads, 0, s>>>(z, keys, lmin, lmax);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(MHAR_E_CUDA, cudaGetErrorString(e));
-  g_noalloc_err[0] = 0;
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(MHAR_E_CUDA, cudaGetErrorString(e));
+  mhar::set_null_error(nullptr);
   return MHAR_OK;
 }

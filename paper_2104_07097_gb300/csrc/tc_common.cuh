@@ -308,12 +308,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 struct ChordAcc {
   unsigned int hib;   // bits of lambda_max (starts at +Inf)
   int lob;            // bits of lambda_min (starts at -Inf)
-  float chk;
 
   __device__ __forceinline__ void init() {
     hib = 0x7f800000u;
     lob = static_cast<int>(0xff800000u);
-    chk = 0.0f;
   }
   __device__ __forceinline__ void add(float ss, float gg) {
     float rg;
@@ -322,11 +320,8 @@ struct ChordAcc {
     hib = min(hib, __float_as_uint(r));
     lob = min(lob, __float_as_int(r));
   }
-  // Non-finite detector: stays 0 unless some value is Inf or NaN.
-  __device__ __forceinline__ void check(float v) { chk = fmaf(v, 0.0f, chk); }
   __device__ __forceinline__ float lo_all() const { return __int_as_float(lob); }
   __device__ __forceinline__ float hi_all() const { return __uint_as_float(hib); }
-  __device__ __forceinline__ bool finite() const { return chk == 0.0f; }
 };
 
 // Brings one 128-byte line into L1 ahead of its use (the b_i / scale_i of a
@@ -342,32 +337,112 @@ __device__ __forceinline__ float clamp_slack(float s) {
   return __int_as_float(max(__float_as_int(s), 0));
 }
 
+// Per-row data of the chord epilogue, in blocks of 32 rows: block g (rows
+// 32 g .. 32 g + 31) is 128 floats -- b_i / scale_i, then Ks_i, then Kg_i,
+// then the block's bound form (0: 2-norms, 1: max-norms) -- so one pointer
+// serves all of it (rows in the units of the row's power-of-two scale):
+//   b_i / scale_i, lowered by 2^-21 |b_i / scale_i| (the relative rounding of
+//       this value, the slack FMA, the ratio and theta)
+//   Ks: bound on |computed - exact| of p_i = a_i . x per unit of the walker's
+//       ws |x_hat| (2-norm form: ws ||x_hat||_2; max-norm form: ws, since
+//       max |x_hat| < 1)
+//   Kg: bound on |computed - exact| of g_i = a_i . d per unit of |d_hat|
+//       (||d_hat||_2 or max |d_hat_i|)
+// Both cover the representation error of the FP16 pair of row i (exact,
+// from the split), the dropped lo.lo product, the point's own split and the
+// FP32 accumulation of the MMA chain in tensor memory.  See prepare_tc_kernel
+// in kernels_simt.cu.  `row0` below is always a multiple of 32.
+__device__ __forceinline__ const float* row_block(const float* rows, int row0) {
+  return rows + (row0 >> 5) * 128;
+}
+
+// The walker factors of a 32-row block: (ws ||x_hat||_2, ||d_hat||_2) or
+// (ws, max |d_hat|) by the block's form.
+struct WalkerNorms {
+  float nxw2, nd2, ws, ndinf;
+  __device__ __forceinline__ void pick(const float* rows, int row0, float& fx, float& fd) const {
+    const bool inf = __ldg(row_block(rows, row0) + 96) != 0.0f;
+    fx = inf ? ws : nxw2;
+    fd = inf ? ndinf : nd2;
+  }
+};
+
 // Slack of one walker at 32 rows from its P = X A^T columns (in place):
-// s_i = b_i - p_i w, clamped at 0 (Lemma 4.2's s = b - A x, in the row and
-// walker scales of the FP16 operands).  bS points at the 32 rows' b_i / scale_i
-// (16-byte aligned).
-__device__ __forceinline__ void slack32(float (&v)[32], const float* bS, float ws, ChordAcc& acc) {
-  const float4* b4 = reinterpret_cast<const float4*>(bS);
+// s_i = b_i - p_i ws - Ks_i nxw, clamped at 0 -- Lemma 4.2's s = b - A x,
+// lowered by the bound on its rounding error so that a chord end computed
+// from it never lies outside the facet (nxw = ws ||x_hat||_2 of the walker).
+__device__ __forceinline__ void slack32(float (&v)[32], const float* rows, int row0, float ws,
+                                        float nxw) {
+  const float4* b4 = reinterpret_cast<const float4*>(row_block(rows, row0));
+  const float4* k4 = b4 + 8;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 b = __ldg(b4 + i);
+    const float4 kk = __ldg(k4 + i);
     const float bb[4] = {b.x, b.y, b.z, b.w};
+    const float ks[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float sv = fmaf(-v[4 * i + j], ws, bb[j]);
-      acc.check(sv);
+      float sv = fmaf(-v[4 * i + j], ws, bb[j]);
+      sv = fmaf(-ks[j], nxw, sv);
       v[4 * i + j] = clamp_slack(sv);
     }
   }
 }
 
-// The chord scan over 32 rows: slacks s (from slack32) against G = D A^T.
-// G needs no per-row check: its FP16 operands are finite (the direction
-// split flags any value beyond the FP16 range) and so is every sum of their
-// products.
-__device__ __forceinline__ void scan32(const float (&s)[32], const float (&g)[32], ChordAcc& acc) {
+// The chord scan over 32 rows: slacks s (from slack32) against G = D A^T,
+// each g_i pushed away from zero by its error bound Kg_i nd (nd = ||d_hat||_2
+// of the walker), so that s / g never exceeds the exact ratio of the lowered
+// slack.  G and the slacks are finite: the FP16 operands are (the splits of
+// the points and directions flag any value beyond the FP16 range) and so is
+// every sum of their products.
+__device__ __forceinline__ void scan32(const float (&s)[32], const float (&g)[32],
+                                       const float* rows, int row0, float nd, ChordAcc& acc) {
+  const float4* k4 = reinterpret_cast<const float4*>(row_block(rows, row0)) + 16;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc.add(s[c], g[c]);
+  for (int i = 0; i < 8; ++i) {
+    const float4 kk = __ldg(k4 + i);
+    const float kg[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float gg = g[4 * i + j];
+      const float sd = __int_as_float(__float_as_int(nd) | (__float_as_int(gg) & 0x80000000));
+      acc.add(s[4 * i + j], fmaf(kg[j], sd, gg));
+    }
+  }
+}
+
+// Bound on the 2-norm of one walker's scaled operand from its FP16 hi part
+// (sum of squares in FP32): ||v|| <= ||v_hi|| (1 + 2^-11) for the FP16 pair,
+// and the FP32 sum of at most 1024 squares and the square root stay well
+// inside the (1 + 2^-8) factor.  The same factor bounds max |v| from max |v_hi|.
+__device__ __forceinline__ float norm_bound(float sumsq) {
+  return sqrtf(sumsq) * 1.00390625f;
+}
+
+// Largest |value| of 8 FP16 values packed in a uint4.
+__device__ __forceinline__ float absmax8(uint4 u) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  float mx = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+    mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+  }
+  return mx;
+}
+
+// Sum of squares of 8 FP16 values packed in a uint4.
+__device__ __forceinline__ float sumsq8(uint4 u) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+    acc = fmaf(f.x, f.x, acc);
+    acc = fmaf(f.y, f.y, acc);
+  }
+  return acc;
 }
 
 template <int kThreads>

@@ -40,8 +40,9 @@ struct WalkerTail {
   const float* sigma;    // n_ld
   const float* AE32;     // mE x n_ld or null
   const float* corr;     // z x mE or null
+  const float* corrn;    // z or null: ||A_E^T corr / sigma||_2 of each walker's direction
   int mE, n, n_ld, k_pad, z_ld, inter, draw;
-  int unit_sigma;        // 1: every sigma_i is 1 (no preconditioner), skip them
+  int unit_sigma;        // 1: every sigma_i is 1, skip them
   // Preconditioned draw d = delta .* h + U g (pc_rank >= 0; only kernels that
   // pass shared scratch for g to walker_draw_next draw it themselves).
   const float* pc_delta; // n_ld
@@ -66,6 +67,7 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter, bool pc_draw = 
   t.sigma = c->d.sigma;
   t.AE32 = c->d.AE32;
   t.corr = c->d.corr;
+  t.corrn = c->d.corrn;
   t.mE = c->mE;
   t.n = c->n;
   t.n_ld = c->n_ld;
@@ -73,7 +75,7 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter, bool pc_draw = 
   t.z_ld = (c->z + tc::kWalkers - 1) / tc::kWalkers * tc::kWalkers;
   t.inter = inter;
   t.draw = (c->mE == 0 && (c->pc_rank < 0 || pc_draw)) ? 1 : 0;
-  t.unit_sigma = c->pc_rank < 0 ? 1 : 0;
+  t.unit_sigma = c->unit_sigma ? 1 : 0;
   t.pc_delta = c->d.pc_delta32;
   t.pc_U = c->d.pc_U32;
   t.pc_rank = c->pc_rank;
@@ -123,6 +125,53 @@ __device__ __forceinline__ bool split_store8(const float* v, __half* hi_dst, __h
 }
 
 }  // namespace tail_detail
+
+// Norm bounds of one walker's direction and scaled point (the chord's error
+// margins, tc_common.cuh) from the FP16 hi rows of the row-major operands
+// (walker k at k * k_pad): thread part == 0 of the walker sums the squares of
+// its 8-element chunks in chunk order (the same order as the tensor-memory
+// kernel) and takes the largest |d|, and shares them through `scr` (3 x 128
+// floats of shared memory).  Run by all kThreads threads (named barrier 1).
+// Returns (ws ||x_hat||_2, ||d_hat||_2, ws, max |d_hat|) for the walker with
+// point scale ws.
+template <int kThreads>
+__device__ __forceinline__ tc::WalkerNorms operand_norms(const __half* Dh, const __half* Xh,
+                                                         int k_pad, int k, int wl, int part,
+                                                         float ws, float* scr) {
+  constexpr int W = tc::kWalkers;
+  if (part == 0) {
+    const uint4* d4 = reinterpret_cast<const uint4*>(Dh + static_cast<size_t>(k) * k_pad);
+    const uint4* x4 = reinterpret_cast<const uint4*>(Xh + static_cast<size_t>(k) * k_pad);
+    float sd = 0.0f, sx = 0.0f, md = 0.0f;
+    for (int c = 0; c < (k_pad >> 3); ++c) {
+      const uint4 dv = __ldg(d4 + c);
+      sd += tc::sumsq8(dv);
+      md = fmaxf(md, tc::absmax8(dv));
+      sx += tc::sumsq8(__ldg(x4 + c));
+    }
+    scr[wl] = sd;
+    scr[W + wl] = sx;
+    scr[2 * W + wl] = md;
+  }
+  tc::named_bar<kThreads>();
+  tc::WalkerNorms r;
+  r.nxw2 = ws * tc::norm_bound(scr[W + wl]);
+  r.nd2 = tc::norm_bound(scr[wl]);
+  r.ws = ws;
+  r.ndinf = scr[2 * W + wl] * 1.00390625f;
+  return r;
+}
+
+// With equalities the point moves along d - A_E^T c' (walker_tail (1)) while
+// the chord is found along d: |a_i . A_E^T c'| <= |a_hat_i|_p ||A_E^T c' /
+// sigma||_2 and Kg_p >= 2^-22 |a_hat_i|_p, so 2^22 ||A_E^T c' / sigma||_2 added
+// to both direction norms covers it in the margin of a_i . d.
+__device__ __forceinline__ void add_correction(const WalkerTail& t, int k, tc::WalkerNorms& wn) {
+  if (t.corrn == nullptr) return;
+  const float cc = 4194304.0f * __ldg(t.corrn + k);
+  wn.nd2 += cc;
+  wn.ndinf += cc;
+}
 
 // A thread's first item, loaded before theta is known (the loads do not
 // depend on it), so that their latency hides behind the cluster barrier.
@@ -271,6 +320,11 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if (i0 + e >= t.n) v[e] = 0.0f;
+    if (!pre && !t.unit_sigma) {
+      // The FP16 pair holds d_i / sigma_i (sigma a power of two: exact).
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] *= 1.0f / t.sigma[i0 + e];
+    }
     if (pre) {
       const float* g = gs + wo * kMaxPcRank;
 #pragma unroll

@@ -17,6 +17,15 @@ multi-chain one:
 
 Walkers are independent chains (Section 4.1), so the ESS of all z walkers is
 the ESS of a traced subset of W walkers scaled by z / W.
+
+An ESS is only meaningful once the chains have left their transient.  The
+check used with it is the split potential scale reduction (Gelman et al.,
+Bayesian Data Analysis, 3rd ed., Section 11.4): every walker's series is
+cut into halves, and for the 2W half-chains of length N
+  B = N var(half-chain means),  Wv = mean(half-chain variances),
+  R_hat = sqrt(((N - 1) / N Wv + B / N) / Wv);
+a drifting (still transient) chain has halves with different means and an
+R_hat well above 1.  The maximum over coordinates is reported.
 """
 from __future__ import annotations
 
@@ -76,3 +85,18 @@ def min_ess(trace: np.ndarray, z_total: int | None = None) -> float:
     if z_total is not None:
         e *= z_total / tr.shape[1]
     return e
+
+
+def split_rhat(trace: np.ndarray) -> np.ndarray:
+    """Split R_hat of every coordinate of a (T, W, n) trace."""
+    tr = np.asarray(trace, dtype=np.float64)
+    T, W, n = tr.shape
+    N = T // 2
+    halves = np.concatenate([tr[:N], tr[T - N:]], axis=1)   # (N, 2W, n)
+    means = halves.mean(axis=0)                             # (2W, n)
+    var = halves.var(axis=0, ddof=1)                        # (2W, n)
+    B = N * means.var(axis=0, ddof=1)
+    Wv = var.mean(axis=0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.sqrt(((N - 1) / N * Wv + B / N) / Wv)
+    return np.where(Wv > 0, r, np.inf)

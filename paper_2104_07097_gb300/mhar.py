@@ -29,10 +29,13 @@ E_NONFINITE = -4
 E_CUDA = -5
 E_RANK = -6
 E_UNSUPPORTED = -7
+E_TIMEOUT = -8
+E_INFEASIBLE_DRIFT = -9
 
 ST_UNBOUNDED = 1
 ST_STALL = 2
 ST_NONFINITE = 4
+ST_DRIFT = 8
 
 # Every symbol include/mhar.h declares.
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
@@ -41,7 +44,7 @@ EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mh
            "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_run",
            "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
            "mhar_batch_destroy", "mhar_kernel_name", "mhar_last_error", "mhar_strerror",
-           "mhar_destroy")
+           "mhar_status_code", "mhar_set_audit", "mhar_batch_set_audit", "mhar_destroy")
 
 
 class MharOpts(ctypes.Structure):
@@ -50,7 +53,8 @@ class MharOpts(ctypes.Structure):
                 ("walker0", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("graph_chunk", ctypes.c_int32), ("refresh_fp64", ctypes.c_int32),
                 ("smem_operands", ctypes.c_int32), ("emit_walkers", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("schedule", ctypes.c_int32), ("audit_every", ctypes.c_int32),
+                ("audit_walkers", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class MharStats(ctypes.Structure):
@@ -58,7 +62,9 @@ class MharStats(ctypes.Structure):
                 ("stalls", ctypes.c_int64), ("unbounded", ctypes.c_int64),
                 ("status_bits", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refresh_drift", ctypes.c_double), ("max_violation", ctypes.c_double),
-                ("eq_residual", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("eq_residual", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("run_max_violation", ctypes.c_double), ("run_eq_residual", ctypes.c_double),
+                ("audits", ctypes.c_int64)]
 
 
 class MharProblem(ctypes.Structure):
@@ -141,6 +147,12 @@ def load(path: str | None = None):
     lib.mhar_last_error.restype = ctypes.c_char_p
     lib.mhar_strerror.argtypes = [ctypes.c_int]
     lib.mhar_strerror.restype = ctypes.c_char_p
+    lib.mhar_status_code.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.mhar_status_code.restype = ctypes.c_int
+    lib.mhar_set_audit.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.mhar_set_audit.restype = ctypes.c_int
+    lib.mhar_batch_set_audit.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.mhar_batch_set_audit.restype = ctypes.c_int
     lib.mhar_destroy.argtypes = [vp]
     lib.mhar_destroy.restype = None
     _lib = lib
@@ -169,6 +181,10 @@ def mhar_last_error(ctx) -> str:
     return load().mhar_last_error(ctx).decode()
 
 
+def mhar_status_code(status_bits: int, wait_expired: int) -> int:
+    return load().mhar_status_code(int(status_bits), int(wait_expired))
+
+
 def mhar_create(A, b, AE, bE, x0, z: int, opts: MharOpts):
     A, b, x0 = _f64(A), _f64(b), _f64(x0)
     m, n = A.shape
@@ -179,7 +195,7 @@ def mhar_create(A, b, AE, bE, x0, z: int, opts: MharOpts):
     rc = load().mhar_create(_dp(A), _dp(b), m, n, _dp(AE), _dp(bE), mE, _dp(x0), int(z),
                             ctypes.byref(opts), ctypes.byref(ctx))
     if rc != OK:
-        raise MharError(rc, f"mhar_create failed: {mhar_strerror(rc)}")
+        raise MharError(rc, f"mhar_create failed: {mhar_strerror(rc)}: {mhar_last_error(None)}")
     return ctx
 
 
@@ -302,7 +318,8 @@ class Sampler:
     def __init__(self, A, b, x0, z: int, AE=None, bE=None, precision: str | int = "fp64",
                  seed: int = 0, refresh_k: int = 64, walker0: int = 0, stream=None,
                  graph_chunk: int = 16, out_on_device: bool = False, refresh_fp64: bool = False,
-                 smem_operands: bool = False, emit_walkers: int = 0, schedule: int = 0):
+                 smem_operands: bool = False, emit_walkers: int = 0, schedule: int = 0,
+                 audit_every: int = 0, audit_walkers: int = 0):
         o = mhar_default_opts()
         o.seed = int(seed)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -314,6 +331,8 @@ class Sampler:
         o.smem_operands = 1 if smem_operands else 0
         o.emit_walkers = int(emit_walkers)
         o.schedule = int(schedule)
+        o.audit_every = int(audit_every)
+        o.audit_walkers = int(audit_walkers)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         A = _f64(A)
@@ -364,6 +383,12 @@ class Sampler:
     def stats(self) -> MharStats:
         return mhar_get_stats(self._ctx)
 
+    def set_audit(self, every: int, walkers: int = 0) -> None:
+        """FP64 feasibility audit after every `every` iterations (0: off)."""
+        rc = load().mhar_set_audit(self._ctx, int(every), int(walkers))
+        if rc != OK:
+            raise MharError(rc, mhar_last_error(self._ctx))
+
     def set_preconditioner(self, delta, U=None) -> None:
         """Directions d = P (delta * h + U g); delta None restores isotropic ones."""
         mhar_set_preconditioner(self._ctx, self.n, delta, U)
@@ -408,12 +433,14 @@ class Batch:
     Philox key seed + p; every problem has z walkers; recompute tensor-core mode."""
 
     def __init__(self, problems, z: int, seed: int = 0, stream=None, out_on_device: bool = False,
-                 emit_walkers: int = 0):
+                 emit_walkers: int = 0, audit_every: int = 0, audit_walkers: int = 0):
         o = mhar_default_opts()
         o.seed = int(seed)
         o.precision = MIXED_RECOMPUTE
         o.out_on_device = 1 if out_on_device else 0
         o.emit_walkers = int(emit_walkers)
+        o.audit_every = int(audit_every)
+        o.audit_walkers = int(audit_walkers)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._keep = []
@@ -431,7 +458,8 @@ class Batch:
         ctx = ctypes.c_void_p()
         rc = load().mhar_batch_create(arr, len(problems), self.z, ctypes.byref(o), ctypes.byref(ctx))
         if rc != OK:
-            raise MharError(rc, f"mhar_batch_create failed: {mhar_strerror(rc)}")
+            raise MharError(rc, f"mhar_batch_create failed: {mhar_strerror(rc)}: "
+                                f"{mhar_last_error(None)}")
         self._b = ctx
 
     def _err(self, rc):
@@ -484,6 +512,11 @@ class Batch:
         if rc != OK:
             self._err(rc)
         return st
+
+    def set_audit(self, every: int, walkers: int = 0) -> None:
+        rc = load().mhar_batch_set_audit(self._b, int(every), int(walkers))
+        if rc != OK:
+            self._err(rc)
 
     def close(self) -> None:
         if getattr(self, "_b", None):

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mixed
 from paper_2104_07097_gb300 import mhar
 from paper_2104_07097_gb300 import workloads as wl
 
@@ -64,7 +65,8 @@ def test_batch_against_oracle(bodies):
         got = bt.run(steps, thin=1)
         stats = [bt.check(q) for q in range(len(bodies))]
     for q, p in enumerate(bodies):
-        ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, thin=1, seed=seed + q)
+        ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, "mixed_rs", thin=1,
+                              seed=seed + q)
         err = np.abs(got[q] - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
         assert err <= 1e-4, (q, err)
         assert stats[q].max_violation <= 1e-6

@@ -1,5 +1,12 @@
-"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, step
-by step, on the same seeded inputs (Algorithm 2; Sections 4.3-4.5).
+"""GPU parity: the CUDA path through the C ABI against the oracles, step by
+step, on the same seeded inputs (Algorithm 2; Sections 4.3-4.5).
+
+References: FP64 mode against the pure FP64 oracle (oracle.mhar_run); the FP32
+and tensor-core modes against the reduced-precision oracle (oracle.mixed),
+which computes in FP64 what those modes document -- quantised directions, the
+error-bounded chord of every row, theta in FP32 -- since the chords'
+feasibility margins alone move them by more than the kernels' own rounding.
+Their distance from the pure oracle is reported (and bounded loosely) too.
 
 Tolerances (normwise, err = max|gpu - ref| / max(1, max|ref|)):
   FP64 mode 1e-10, FP32 and mixed (FP16x3 tensor-core) modes 1e-4.
@@ -9,12 +16,17 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mixed
 from paper_2104_07097_gb300 import mhar
 from paper_2104_07097_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "fp32": 1e-4, "mixed": 1e-4, "mixed_rs": 1e-4}
+# Distance allowed from the pure FP64 oracle's step, whose chords lack the
+# margins (about 1e-5 of a chord typically, up to a few 1e-4 where the binding
+# row is nearly parallel to d, times the direction's length).
+TOL_PURE = 1e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,43 +76,60 @@ def test_fp64_free_running_50(body, z):
         assert st.eq_residual <= 1e-8
 
 
+def reduced_ref(p, X0, steps, prec, seed, step0=0, **kw):
+    """The reduced-precision oracle's walk for the library mode `prec`."""
+    return mixed.mixed_run(p.A, p.b, X0, steps, prec, thin=1, seed=seed, step0=step0, AE=p.AE,
+                           trace=True, **kw)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs", "mixed_rs_smem"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_step_for_step_parity_50(body, z, prec):
-    """Each of the first 50 iterations, started from the oracle's own state
+    """Each of the first 50 iterations, started from the pure oracle's state
     X_j (an oracle output, never a GPU one), must land within 1e-4 of the
-    oracle's X_{j+1}; chord ends and theta are compared on the same scale."""
+    reduced-precision oracle's step from X_j; chord ends and theta are
+    compared on the same scale.  The pure oracle's X_{j+1} is within TOL_PURE."""
     p = BODIES[body]()
     X0 = np.tile(p.x0, (z, 1))
-    ref = oracle.mhar_run(p.A, p.b, X0, steps=50, thin=1, seed=5, AE=p.AE, trace=True)
-    worst = 0.0
+    pure = oracle.mhar_run(p.A, p.b, X0, steps=50, thin=1, seed=5, AE=p.AE, trace=True)
+    worst = worst_pure = 0.0
     kw = {}
+    mode = prec
     if prec == "mixed_rs_smem":   # the shared-memory-operand kernel used for n > 128
-        prec, kw = "mixed_rs", {"smem_operands": True}
-    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5, **kw) as s:
+        mode, kw = "mixed_rs", {"smem_operands": True}
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=mode, seed=5, **kw) as s:
         for j in range(50):
-            start = X0 if j == 0 else ref["samples"][j - 1]
+            start = X0 if j == 0 else pure["samples"][j - 1]
+            ref = reduced_ref(p, start, 1, mode, seed=5, step0=j)
             s.set_state(start, j)
             got = s.run(1, thin=1)[0]
-            worst = max(worst, normwise(got, ref["samples"][j]))
+            worst = max(worst, normwise(got, ref["samples"][0]))
+            worst_pure = max(worst_pure, normwise(got, pure["samples"][j]))
             lo, hi, t = s.chord()
-            span = np.maximum(1.0, ref["lmax"][j] - ref["lmin"][j])
-            assert np.abs(t - ref["t"][j]).max() <= TOL[prec] * span.max()
-            assert np.all(np.abs(lo - ref["lmin"][j]) <= TOL[prec] * span)
-            assert np.all(np.abs(hi - ref["lmax"][j]) <= TOL[prec] * span)
-    assert worst <= TOL[prec], worst
+            span = np.maximum(1.0, ref["lmax"][0] - ref["lmin"][0])
+            assert np.abs(t - ref["t"][0]).max() <= TOL[mode] * span.max()
+            assert np.all(np.abs(lo - ref["lmin"][0]) <= TOL[mode] * span)
+            assert np.all(np.abs(hi - ref["lmax"][0]) <= TOL[mode] * span)
+    assert worst <= TOL[mode], worst
+    assert worst_pure <= TOL_PURE, worst_pure
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_free_running_parity(body, z, prec):
-    """Free-running chains: within 1e-4 over the first 10 iterations.  Over 50
-    iterations the chain itself amplifies FP32-level rounding about 1000-fold
-    (the FP64 oracle with only its directions rounded to FP32 already drifts
-    1.2e-4 from itself on cube10), so the 50-iteration bound is 5e-3."""
+    """Free-running chains against the reduced-precision oracle's: within 1e-4
+    over the first 10 iterations.  Over 50 iterations the chain amplifies the
+    kernels' own FP32 rounding of the chord (the reference computes its chord
+    in FP64) about 1000-fold, so the 50-iteration bound is 5e-3.  (Against the
+    pure oracle the margins themselves, about 1e-5 of a chord, are amplified
+    the same way: no bound is asserted on that distance.)"""
     p = BODIES[body]()
-    ref, got, _, st = run_pair(p, z, 50, prec, seed=5)
-    err = [normwise(got[s], ref["samples"][s]) for s in range(50)]
+    X0 = np.tile(p.x0, (z, 1))
+    ref = reduced_ref(p, X0, 50, prec, seed=5)
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5) as s:
+        got = s.run(50, thin=1)
+        st = s.check()
+    err = [normwise(got[i], ref["samples"][i]) for i in range(50)]
     assert max(err[:10]) <= TOL[prec], err[:10]
     assert max(err) <= 5e-3, max(err)
     assert st.max_violation <= 1e-6 * np.abs(p.b).max()
@@ -243,6 +272,10 @@ def test_tiled_chord_path_against_oracle(prec):
     z, steps = 2048, 10
     with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=5) as s:
         got = s.run(steps, thin=1)
-    ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (40, 1)), steps, thin=1, seed=5)
+    X0 = np.tile(p.x0, (40, 1))
+    if prec == "fp64":
+        ref = oracle.mhar_run(p.A, p.b, X0, steps, thin=1, seed=5)
+    else:
+        ref = mixed.mixed_run(p.A, p.b, X0, steps, prec, thin=1, seed=5)
     err = np.abs(got[:, :40] - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
     assert err <= TOL[prec], err

@@ -9,6 +9,7 @@ from scipy import stats
 
 import oracle
 import oracle.precond as opc
+from oracle import mixed
 from paper_2104_07097_gb300 import diagnostics
 from paper_2104_07097_gb300 import mhar
 from paper_2104_07097_gb300 import workloads as wl
@@ -86,28 +87,35 @@ def test_preconditioned_fp64_free_running_50(name, z):
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs", "mixed_rs_smem"])
 @pytest.mark.parametrize("name,z", CASES)
 def test_preconditioned_step_for_step_50(name, z, prec):
-    """Each iteration restarted from the oracle's state; the ill-conditioned
-    body (axes from 1e-3 to 1) is measured in its whitened coordinates."""
+    """Each iteration restarted from the pure oracle's state X_j and compared
+    with the reduced-precision oracle's step from it (oracle.mixed: quantised
+    directions, error-bounded chords); the ill-conditioned body (axes from
+    1e-3 to 1) is measured in its whitened coordinates."""
     p, s, delta, U = case(name)
     X0 = np.tile(p.x0, (z, 1))
-    ref = oracle.mhar_run_pre(p.A, p.b, X0, 50, delta, U, thin=1, seed=5, AE=p.AE, trace=True)
+    pure = oracle.mhar_run_pre(p.A, p.b, X0, 50, delta, U, thin=1, seed=5, AE=p.AE, trace=True)
     kw = {}
     if prec == "mixed_rs_smem":
         prec, kw = "mixed_rs", {"smem_operands": True}
-    worst = 0.0
+    worst = worst_pure = 0.0
     with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=5, **kw) as smp:
         smp.set_preconditioner(delta, U)
         for j in range(50):
-            smp.set_state(X0 if j == 0 else ref["samples"][j - 1], j)
+            start = X0 if j == 0 else pure["samples"][j - 1]
+            ref = mixed.mixed_run(p.A, p.b, start, 1, prec, seed=5, step0=j, AE=p.AE,
+                                  delta=delta, U=U, trace=True)
+            smp.set_state(start, j)
             got = smp.run(1, thin=1)[0]
-            worst = max(worst, scaled_err(got, ref["samples"][j], s))
+            worst = max(worst, scaled_err(got, ref["samples"][0], s))
+            worst_pure = max(worst_pure, scaled_err(got, pure["samples"][j], s))
             lo, hi, t = smp.chord()
-            span = np.maximum(1.0, ref["lmax"][j] - ref["lmin"][j])
-            assert np.all(np.abs(lo - ref["lmin"][j]) <= TOL[prec] * span)
-            assert np.all(np.abs(hi - ref["lmax"][j]) <= TOL[prec] * span)
+            span = np.maximum(1.0, ref["lmax"][0] - ref["lmin"][0])
+            assert np.all(np.abs(lo - ref["lmin"][0]) <= TOL[prec] * span)
+            assert np.all(np.abs(hi - ref["lmax"][0]) <= TOL[prec] * span)
             viol = (got @ p.A.T - p.b).max()
             assert viol <= 1e-6 * np.abs(p.b).max()
     assert worst <= TOL[prec], worst
+    assert worst_pure <= 3e-3, worst_pure
 
 
 def _snapshot_steps(warmup, snapshots):

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mixed
 from paper_2104_07097_gb300 import mhar
 from paper_2104_07097_gb300 import workloads as wl
 
@@ -30,7 +31,7 @@ def test_full_size_sampled_parity(rand100, prec):
     with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=0) as s:
         got = s.run(steps, thin=1)
     for w0, cnt in ((0, 12), (2048, 12), (4084, 12)):
-        ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (cnt, 1)), steps=steps, thin=1, seed=0,
+        ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (cnt, 1)), steps, prec, thin=1, seed=0,
                               walker0=w0)
         for j in range(steps):
             want = ref["samples"][j]

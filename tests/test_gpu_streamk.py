@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mixed
 from paper_2104_07097_gb300 import mhar
 from paper_2104_07097_gb300 import workloads as wl
 
@@ -47,7 +48,8 @@ def test_stream_k_equals_clusters(n, m, z):
 def test_stream_k_against_oracle():
     p = wl.random_polytope(150, 900, seed=5)
     z, steps = 200, 10
-    ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, thin=1, seed=3, trace=True)
+    ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, "mixed_rs", thin=1, seed=3,
+                          trace=True)
     with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=3, schedule=2) as s:
         got = s.run(steps, thin=1)
         lo, hi, t = s.chord()
@@ -88,7 +90,7 @@ def test_tall_body_goes_to_stream_k():
     with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=6, smem_operands=True) as s:
         assert s.kernel_name() == "recompute_sk_kernel"
         got = s.run(steps, thin=1)
-    ref = oracle.mhar_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, thin=1, seed=6)
+    ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, "mixed_rs", thin=1, seed=6)
     err = np.abs(got - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
     assert err <= 1e-4, err
     with pytest.raises(mhar.MharError) as e:

@@ -46,11 +46,46 @@ def test_host_only_calls(lib):
     assert mhar.mhar_strerror(12345) == "MHAR_E_UNKNOWN"
 
 
-def test_struct_layout_matches_header(lib):
+def test_struct_layout_matches_header(lib, tmp_path):
+    """The ctypes mirrors have the sizes and field offsets a C compiler gives
+    the header's structs (compiled here with gcc, host only)."""
     import ctypes
-    # mhar_opts: u64 + 4 x i32 + pointer + i32 + 7 x i32 = 64 bytes on LP64.
-    assert ctypes.sizeof(mhar.MharOpts) == 64
-    assert ctypes.sizeof(mhar.MharStats) == 72
+    import subprocess
+    fields = {"mhar_opts": mhar.MharOpts, "mhar_stats": mhar.MharStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mhar.h"', "int main(void) {"]
+    for cname, py in fields.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, what, val = line.split()
+        got[(cname, what)] = int(val)
+    for cname, py in fields.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_status_code_mapping(lib):
+    """mhar_run's return code for a device status word (no GPU needed): a
+    bounded wait that ran out wins, then non-finite values, then a refresh
+    beyond the tracked slack's bound, then an open chord; stalls alone are
+    fine."""
+    assert mhar.mhar_status_code(0, 0) == mhar.OK
+    assert mhar.mhar_status_code(mhar.ST_STALL, 0) == mhar.OK
+    assert mhar.mhar_status_code(mhar.ST_UNBOUNDED, 0) == mhar.E_UNBOUNDED
+    assert mhar.mhar_status_code(mhar.ST_UNBOUNDED | mhar.ST_DRIFT, 0) == mhar.E_INFEASIBLE_DRIFT
+    assert mhar.mhar_status_code(mhar.ST_DRIFT | mhar.ST_NONFINITE, 0) == mhar.E_NONFINITE
+    assert mhar.mhar_status_code(mhar.ST_NONFINITE, 1) == mhar.E_TIMEOUT
+    assert mhar.mhar_status_code(0, 1) == mhar.E_TIMEOUT
+    assert mhar.mhar_strerror(mhar.E_TIMEOUT) == "MHAR_E_TIMEOUT"
+    assert mhar.mhar_strerror(mhar.E_INFEASIBLE_DRIFT) == "MHAR_E_INFEASIBLE_DRIFT"
 
 
 def test_built_for_sm103a_only():
