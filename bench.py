@@ -14,9 +14,11 @@ warm-up iterations in four fit rounds, rank-32 + diagonal fit on the device,
 then 5000 frozen iterations, tensor-core recompute mode) against plain isotropic runs (FP32 on
 CUDA cores, and the same tensor-core mode), each with 500 + 5000 iterations,
 and reports min-ESS (over coordinates, from a trace of 64 walkers every 5th
-iteration, scaled to all z walkers) per second of device time.  "ess_moderate"
-repeats it on a smaller body (n = 40, m = 400, axes from 1e-2 to 1, z = 4096)
-whose long axes the warm-up reaches.
+iteration, scaled to all z walkers) per second of device time -- for arms
+whose split R_hat says they have left their transient; every arm also reports
+R_hat and how far it has spread along each axis.  "ess_moderate" repeats it on
+a smaller body (n = 40, m = 400, axes from 1e-2 to 1, z = 4096, 20000
+iterations) whose long axes the warm-up reaches.
 
 A third leg ("batched") times 256 random polytopes of different sizes (n
 uniform in 20..400, m uniform in 2n..20n, z = 512 each, 1000 iterations)
@@ -68,9 +70,10 @@ ESS_WORKLOAD = dict(name="illcond500x10000", n=500, m=10000, seed=5, smin=1e-3, 
                     warmup=500, iterations=5000, trace_walkers=64, trace_every=5, rank=32,
                     fit_rounds=4, snapshots=5, power_iters=4)
 # A smaller ill-conditioned body whose long axes the 500 warm-up iterations do
-# reach, so that the learned directions' own effect on mixing shows.
+# reach, run long enough (20000 iterations) for a chain to leave its transient,
+# so that an ESS can be taken and the learned directions' effect on it shows.
 ESS_MODERATE = dict(name="illcond40x400", n=40, m=400, seed=5, smin=1e-2, z=4096, warmup=500,
-                    iterations=5000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
+                    iterations=20000, trace_walkers=64, trace_every=5, rank=32, fit_rounds=4,
                     snapshots=5, power_iters=4)
 REF_SAMPLE = dict(walkers=64, iterations=20)
 RHAT_LIMIT = 1.05
@@ -320,8 +323,8 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
     # by the coordinates' extents read off the constraints, 1 / max_i |a_ij|
     # (a fixed diagonal law); every fit round then refits rank-32 + diagonal
     # from the chain's own warm-up points.
-    diag0 = 1.0 / np.abs(p.A).max(axis=0)
-    diag0 /= diag0.max()
+    extent = 1.0 / np.abs(p.A).max(axis=0)
+    diag0 = extent / extent.max()
     for name, prec, learned in (("learned_mixed_rs", "mixed_rs", True),
                                 ("plain_mixed_rs", "mixed_rs", False),
                                 ("plain_fp32", "fp32", False)):
@@ -363,11 +366,21 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
         trace = out.cpu().numpy()
         ess = diagnostics.ess_per_coordinate(trace) * (z / W)
         rhat = diagnostics.split_rhat(trace)
-        arms[name] = {"min_ess": float(ess.min()), "median_ess": float(np.median(ess)),
-                      "seconds": secs, "min_ess_per_s": float(ess.min()) / secs,
+        converged = bool(rhat.max() < RHAT_LIMIT)
+        # How far the chains have spread along every axis: the walkers' spread
+        # of x_j over the last quarter of the trace, in units of the axis
+        # extent 1 / max_i |a_ij| read off the constraints.
+        spread = trace[-max(1, trace.shape[0] // 4):].reshape(-1, p.n).std(axis=0) / extent
+        arms[name] = {"min_ess": float(ess.min()) if converged else None,
+                      "median_ess": float(np.median(ess)) if converged else None,
+                      "min_ess_transient": float(ess.min()),
+                      "seconds": secs,
+                      "min_ess_per_s": float(ess.min()) / secs if converged else None,
                       "walker_steps_per_s": z * (E["warmup"] + T) / secs,
                       "max_split_rhat": float(rhat.max()),
-                      "converged": bool(rhat.max() < RHAT_LIMIT),
+                      "converged": converged,
+                      "min_axis_spread": float(spread.min()),
+                      "median_axis_spread": float(np.median(spread)),
                       "max_violation": st.max_violation,
                       "audit": {"iterations": 200, "walkers": min(z, 1024),
                                 "run_max_violation": audited}}
@@ -381,11 +394,20 @@ def ess_leg(stream, torch, mhar, peaks, E=ESS_WORKLOAD) -> dict:
                        f"first round's directions are scaled by 1 / max_i |a_ij|; warm-up and "
                        f"fits are inside the timed region",
             "convergence": f"split R_hat over coordinates < {RHAT_LIMIT} (trace of the "
-                           f"{T} iterations after warm-up)",
+                           f"{T} iterations after warm-up); an arm that has not converged is "
+                           f"still in its transient and reports no ESS (min_ess_transient is "
+                           f"the estimator's value on it, not an ESS)",
+            "axis_spread": "std over walkers and the last quarter of the trace of x_j, divided "
+                           "by the axis extent 1 / max_i |a_ij|; min and median over j",
             "arms": arms,
             "roofline": kernel_roofline,
-            "min_ess_per_s_learned_vs_plain_fp32":
-                arms["learned_mixed_rs"]["min_ess_per_s"] / arms["plain_fp32"]["min_ess_per_s"]}
+            "min_ess_per_s_learned_vs_plain_fp32": _ratio(arms, "min_ess_per_s"),
+            "min_axis_spread_learned_vs_plain_fp32": _ratio(arms, "min_axis_spread")}
+
+
+def _ratio(arms, key):
+    a, b = arms["learned_mixed_rs"][key], arms["plain_fp32"][key]
+    return a / b if a is not None and b else None
 
 
 def main() -> None:

@@ -45,7 +45,7 @@ extern "C" {
                                        beyond the FP16 range of its operands  */
 #define MHAR_E_CUDA            -5  /* CUDA runtime / driver failure, or no
                                       sm_103 device                          */
-#define MHAR_E_RANK            -6  /* A_E A_E^T not positive definite        */
+#define MHAR_E_RANK            -6  /* A_E rank-deficient or cond > ~1e7      */
 #define MHAR_E_UNSUPPORTED     -7  /* size or mode the library does not cover */
 #define MHAR_E_TIMEOUT         -8  /* a bounded wait inside a tensor-core
                                       kernel expired (about 2 s): the pipeline
@@ -170,11 +170,15 @@ void mhar_default_opts(mhar_opts* opts);
  * every column of X to the same strictly interior point).
  *   A    m x n  (m >= 1, n >= 1)        b   m
  *   AE   mE x n or NULL when mE == 0    bE  mE or NULL
+ *        0 <= mE < n, mE <= 25600; A_E of full row rank, condition number below about 1e7
+ *        (MHAR_E_RANK otherwise)
  *   x0   n, strictly inside: b - A x0 > 0 and |A_E x0 - b_E|_inf <= 1e-9 (1 + |b_E|_inf)
  *   z    number of walkers; z <= 0 selects the paper's default max(m, n) + 1
  *   opts NULL for defaults
- * Copies all inputs to the device, factors A_E A_E^T (FP64 Cholesky) when
- * mE > 0, and prepares the per-mode operands.  On success *out is a new
+ * Copies all inputs to the device; when mE > 0 forms, in FP64 on the device,
+ * the orthonormal rows Q = L^{-1} A_E (L the Cholesky factor of A_E A_E^T,
+ * taken twice: CholeskyQR2), so that the projector of Section 3.2 is
+ * P = I - Q^T Q; and prepares the per-mode operands.  On success *out is a new
  * context (free with mhar_destroy). */
 int mhar_create(const double* A, const double* b, int m, int n,
                 const double* AE, const double* bE, int mE,

@@ -84,36 +84,20 @@ __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint
   }
 }
 
-// ---- Section 3.2: d = P h with P in factored form --------------------------
-// One warp per walker; mE <= 32.  y = A_E h (warp reductions), c solves
-// L L^T c = y (lane 0, FP64), d = h - A_E^T c.
+// ---- Section 3.2: d = P h with P = I - Q^T Q ------------------------------
+// One warp per walker.  Q (mE x n, orthonormal rows, Q = L^{-1} A_E): the
+// coefficients c = Q h in FP64 (warp reductions; every lane ends with the
+// sum), kept in shared memory (mE doubles per warp, dynamic), then
+// d_i = h_i - sum_e c_e q_ei in FP64, rounded once to the mode's type -- the
+// projection of the FP64 result, whatever mE is.
 // FP32 modes: the direction actually used (FP32, or the FP16 hi + lo pair of
 // the tensor-core mode) leaves a rounding residual A_E d of order 1e-7 |d|.
-// Its exact FP64 correction c' = (A_E A_E^T)^{-1} A_E d is stored per walker
-// (corr), and the point update moves along d - A_E^T c', so A_E x = b_E holds
+// Its exact FP64 coordinates c' = Q d in the row space are stored per walker
+// (corr), and the point update moves along d - Q^T c', so A_E x = b_E holds
 // to FP64 rounding instead of drifting by theta * 1e-7 per iteration.
-__device__ __forceinline__ void cholesky_solve(const double* L, int mE, double* c) {
-  for (int r = 0; r < mE; ++r) {
-    double s = c[r];
-    for (int q = 0; q < r; ++q) s -= L[r * mE + q] * c[q];
-    c[r] = s / L[r * mE + r];
-  }
-  for (int r = mE - 1; r >= 0; --r) {
-    double s = c[r];
-    for (int q = r + 1; q < mE; ++q) s -= L[q * mE + r] * c[q];
-    c[r] = s / L[r * mE + r];
-  }
-}
-
-// Equality row e, coordinate i of A_E in FP32 (the FP32 modes pass A_E as FP32).
 template <typename T>
-__device__ __forceinline__ float AE32f(const T* AE, int e, int n_ld, int i) {
-  return static_cast<float>(AE[static_cast<size_t>(e) * n_ld + i]);
-}
-
-template <typename T>
-__global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __restrict__ AE,
-                                  const double* __restrict__ AE64, const double* __restrict__ L,
+__global__ void projection_kernel(int z, int n, int n_ld, int mE, const double* __restrict__ Q64,
+                                  const float* __restrict__ Q32,
                                   T* D, int split, int k_pad, __half* Dh, __half* Dl,
                                   float* corr, float* corrn, int z_ld, int inter,
                                   const float* sigma, const uint64_t* step_ptr, int j,
@@ -122,39 +106,39 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
     Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
     Dl = Dl1;
   }
-  __shared__ double cbuf[kThreads / 32][32];
+  extern __shared__ double proj_c[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * (kThreads / 32) + warp;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
   if (k >= z) return;
   T* h = D + static_cast<size_t>(k) * n_ld;
-  double* c = cbuf[warp];
+  double* c = proj_c + static_cast<size_t>(warp) * mE;
   for (int e = 0; e < mE; ++e) {
-    T acc = T(0);
-    for (int i = lane; i < n; i += 32) acc += AE[static_cast<size_t>(e) * n_ld + i] * h[i];
+    const double* q = Q64 + static_cast<size_t>(e) * n_ld;
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) acc += q[i] * static_cast<double>(h[i]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) c[e] = static_cast<double>(acc);
+    if (lane == 0) c[e] = acc;
   }
   __syncwarp();
-  if (lane == 0) cholesky_solve(L, mE, c);
-  __syncwarp();
   for (int i = lane; i < n; i += 32) {
-    T s = h[i];
-    for (int e = 0; e < mE; ++e) s -= AE[static_cast<size_t>(e) * n_ld + i] * static_cast<T>(c[e]);
-    if (split) {
-      const float v = static_cast<float>(s) / sigma[i];  // power of two: exact
+    double v = static_cast<double>(h[i]);
+    for (int e = 0; e < mE; ++e) v -= c[e] * Q64[static_cast<size_t>(e) * n_ld + i];
+    h[i] = static_cast<T>(v);
+  }
+  if (split) {
+    for (int i = lane; i < n; i += 32) {
+      const float v = static_cast<float>(h[i]) / sigma[i];  // power of two: exact
       const __half hh = __float2half_rn(v);
       const size_t o = op_off(k, i, k_pad, z_ld, inter);
       Dh[o] = hh;
       Dl[o] = __float2half_rn(v - __half2float(hh));
       if (!(fabsf(v) <= kHalfMax)) atomicOr(status, MHAR_ST_NONFINITE);
-    } else {
-      h[i] = s;
     }
   }
   if (corr == nullptr) return;
-  __syncwarp();
-  // Residual of the rounded direction, in FP64.
+  // Row-space coordinates of the rounded direction, in FP64.
+  float* ck = corr + static_cast<size_t>(k) * mE;
   for (int e = 0; e < mE; ++e) {
     double acc = 0.0;
     for (int i = lane; i < n; i += 32) {
@@ -165,26 +149,20 @@ __global__ void projection_kernel(int z, int n, int n_ld, int mE, const T* __res
             static_cast<double>(sigma[i]);
       else
         v = static_cast<double>(h[i]);
-      acc += AE64[static_cast<size_t>(e) * n_ld + i] * v;
+      acc += Q64[static_cast<size_t>(e) * n_ld + i] * v;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) c[e] = acc;
+    if (lane == 0) ck[e] = static_cast<float>(acc);
   }
   __syncwarp();
-  if (lane == 0) {
-    cholesky_solve(L, mE, c);
-    for (int e = 0; e < mE; ++e) corr[static_cast<size_t>(k) * mE + e] = static_cast<float>(c[e]);
-  }
-  __syncwarp();
-  // The point moves along d - A_E^T c' (the update's FP32 arithmetic) while
-  // the chord is found along d: ||A_E^T c' / sigma||_2, rounded up, enters
+  // The point moves along d - Q^T c' (the update's FP32 arithmetic) while
+  // the chord is found along d: ||Q^T c' / sigma||_2, rounded up, enters
   // the chord's error margins (tc_common.cuh, kernels_simt.cu).
   float cn = 0.0f;
   for (int i = lane; i < n; i += 32) {
     float dlt = 0.0f;
-    for (int e = 0; e < mE; ++e)
-      dlt = fmaf(AE32f(AE, e, n_ld, i), corr[static_cast<size_t>(k) * mE + e], dlt);
+    for (int e = 0; e < mE; ++e) dlt = fmaf(Q32[static_cast<size_t>(e) * n_ld + i], ck[e], dlt);
     const float v = dlt / sigma[i];
     cn = fmaf(v, v, cn);
   }
@@ -434,7 +412,7 @@ __global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr,
                               double* lmin, double* lmax, double* theta, int* status,
                               unsigned long long* counters, double* X64, const double* D64,
                               float* Xhi, float* Xlo, const float* D32, int mE,
-                              const float* AE32, const float* corr) {
+                              const float* Q32, const float* corr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
   if (k >= z) return;
@@ -472,7 +450,7 @@ __global__ void update_kernel(int mode, uint64_t seed, const uint64_t* step_ptr,
       for (int i = lane; i < n; i += 32) {
         float dlt = 0.0f;
         for (int e = 0; e < mE; ++e)
-          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
+          dlt = fmaf(Q32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
         Xlo[row + i] = fmaf(-tf, dlt, Xlo[row + i]);
       }
     }
@@ -717,7 +695,7 @@ chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
                   int move, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
                   double* lmin, double* lmax, double* theta, unsigned long long* counters,
                   double* X64, const double* D64, float* Xhi, float* Xlo, const float* D32,
-                  int mE, const float* AE32, const float* corr) {
+                  int mE, const float* Q32, const float* corr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kWarpChordThreads / 32) + warp;
   if (k >= z) return;
@@ -820,7 +798,7 @@ chord_warp_kernel(const T* __restrict__ A, const T* __restrict__ b, const T* __r
       for (int i = lane; i < n; i += 32) {
         float dlt = 0.0f;
         for (int e = 0; e < mE; ++e)
-          dlt = fmaf(AE32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
+          dlt = fmaf(Q32[static_cast<size_t>(e) * n_ld + i], corr[static_cast<size_t>(k) * mE + e], dlt);
         Xlo[row + i] = fmaf(-tf, dlt, Xlo[row + i]);
       }
     }
@@ -891,45 +869,32 @@ refresh_simt_kernel(int m, int n_ld, int z, int z_ld, const double* __restrict__
   if (tid == 0) atomicMax(drift_key, f64_key(red[0]));
 }
 
-// Mixed mode with equalities: x <- x - A_E^T (A_E A_E^T)^{-1} (A_E x - b_E),
+// Mixed mode with equalities: x <- x - A_E^T (A_E A_E^T)^{-1} (A_E x - b_E)
+// = x - Q^T (Q x - w) (Section 3.2),
 // in FP64 on the FP32-pair points (removes drift of the equality residual).
-__global__ void reproject_kernel(int z, int n, int n_ld, int mE, const double* AE,
-                                 const double* bE, const double* L, float* Xhi, float* Xlo) {
-  __shared__ double cbuf[kThreads / 32][32];
+__global__ void reproject_kernel(int z, int n, int n_ld, int mE, const double* Q,
+                                 const double* w, float* Xhi, float* Xlo) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (kThreads / 32) + warp;
   if (k >= z) return;
   const size_t row = static_cast<size_t>(k) * n_ld;
-  double* c = cbuf[warp];
+  // x <- x - (q_e . x - w_e) q_e, one orthonormal row at a time (the same
+  // as x - Q^T (Q x - w)), on the FP64 value of the hi + lo pair.
   for (int e = 0; e < mE; ++e) {
+    const double* q = Q + static_cast<size_t>(e) * n_ld;
     double acc = 0.0;
     for (int i = lane; i < n; i += 32)
-      acc += AE[static_cast<size_t>(e) * n_ld + i] *
-             (static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]));
+      acc += q[i] * (static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) c[e] = acc - bE[e];
-  }
-  __syncwarp();
-  if (lane == 0) {
-    for (int r = 0; r < mE; ++r) {
-      double s = c[r];
-      for (int q = 0; q < r; ++q) s -= L[r * mE + q] * c[q];
-      c[r] = s / L[r * mE + r];
+    const double r = acc - w[e];
+    for (int i = lane; i < n; i += 32) {
+      const double v = static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]) -
+                       r * q[i];
+      const float hv = static_cast<float>(v);
+      Xhi[row + i] = hv;
+      Xlo[row + i] = static_cast<float>(v - static_cast<double>(hv));
     }
-    for (int r = mE - 1; r >= 0; --r) {
-      double s = c[r];
-      for (int q = r + 1; q < mE; ++q) s -= L[q * mE + r] * c[q];
-      c[r] = s / L[r * mE + r];
-    }
-  }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) {
-    double v = static_cast<double>(Xhi[row + i]) + static_cast<double>(Xlo[row + i]);
-    for (int e = 0; e < mE; ++e) v -= AE[static_cast<size_t>(e) * n_ld + i] * c[e];
-    const float h = static_cast<float>(v);
-    Xhi[row + i] = h;
-    Xlo[row + i] = static_cast<float>(v - static_cast<double>(h));
   }
 }
 
@@ -1092,17 +1057,36 @@ cudaError_t launch_directions(mhar_ctx* c, int j) {
   return cudaGetLastError();
 }
 
+// Walkers (warps) per block of the projection: eight, fewer when their
+// coefficient vectors (mE doubles each) would pass 200 KB of shared memory.
+int projection_warps(int mE) {
+  const int w = static_cast<int>((200u << 10) / (sizeof(double) * (mE > 0 ? mE : 1)));
+  return w < 1 ? 1 : (w > kThreads / 32 ? kThreads / 32 : w);
+}
+
+cudaError_t projection_smem_attr(int mE) {
+  const int bytes = static_cast<int>(sizeof(double)) * projection_warps(mE) * mE;
+  cudaError_t e = cudaFuncSetAttribute(projection_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(projection_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 cudaError_t launch_projection(mhar_ctx* c, int j) {
-  const int grid = blocks_for(c->z, kThreads / 32);
+  const int warps = projection_warps(c->mE);
+  const int grid = blocks_for(c->z, warps);
+  const size_t smem = sizeof(double) * static_cast<size_t>(warps) * c->mE;
   if (c->opts.precision == MHAR_FP64) {
-    projection_kernel<double><<<grid, kThreads, 0, c->stream>>>(
-        c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.AE64, c->d.Lchol, c->d.D64, 0, 0, nullptr,
+    projection_kernel<double><<<grid, warps * 32, smem, c->stream>>>(
+        c->z, c->n, c->n_ld, c->mE, c->d.Q64, c->d.Q32, c->d.D64, 0, 0, nullptr,
         nullptr, nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr, c->d.status);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
-    projection_kernel<float><<<grid, kThreads, 0, c->stream>>>(
-        c->z, c->n, c->n_ld, c->mE, c->d.AE32, c->d.AE64, c->d.Lchol, c->d.D32, split, c->k_pad,
+    projection_kernel<float><<<grid, warps * 32, smem, c->stream>>>(
+        c->z, c->n, c->n_ld, c->mE, c->d.Q64, c->d.Q32, c->d.D32, split, c->k_pad,
         c->d.Dh, c->d.Dl, c->d.corr, c->d.corrn, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0,
         c->d.sigma, c->d.step, j, c->d.Dh2, c->d.Dl2, c->d.status);
   }
@@ -1147,7 +1131,7 @@ cudaError_t launch_chord_update_warp(mhar_ctx* c, int j) {
         c->d.A32, c->d.b32, c->d.kr32, c->d.sigma, c->d.corrn, c->d.Xhi, c->d.D32, c->m, c->n, c->n_ld, c->z, c->d.key_lo,
         c->d.key_hi, c->d.status, 1, c->opts.seed, c->d.step, j, c->opts.walker0, c->d.lmin,
         c->d.lmax, c->d.theta, c->d.counters, nullptr, nullptr, c->d.Xhi, c->d.Xlo, c->d.D32,
-        c->mE, c->d.AE32, c->d.corr);
+        c->mE, c->d.Q32, c->d.corr);
   return cudaGetLastError();
 }
 
@@ -1172,7 +1156,7 @@ cudaError_t launch_update_simt(mhar_ctx* c, int j) {
   update_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
       mode, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->d.key_lo,
       c->d.key_hi, c->d.lmin, c->d.lmax, c->d.theta, c->d.status, c->d.counters, c->d.X64,
-      c->d.D64, c->d.Xhi, c->d.Xlo, c->d.D32, c->mE, c->d.AE32, c->d.corr);
+      c->d.D64, c->d.Xhi, c->d.Xlo, c->d.D32, c->mE, c->d.Q32, c->d.corr);
   return cudaGetLastError();
 }
 
@@ -1246,7 +1230,7 @@ cudaError_t launch_refresh_simt(mhar_ctx* c) {
 
 cudaError_t launch_reproject(mhar_ctx* c) {
   reproject_kernel<<<blocks_for(c->z, kThreads / 32), kThreads, 0, c->stream>>>(
-      c->z, c->n, c->n_ld, c->mE, c->d.AE64, c->d.bE64, c->d.Lchol, c->d.Xhi, c->d.Xlo);
+      c->z, c->n, c->n_ld, c->mE, c->d.Q64, c->d.wE64, c->d.Xhi, c->d.Xlo);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ struct TcParams {
   float* Xlo;
   const float* rowk;        // 4 m_pad: Ks_2, Kg_2, Ks_1, Kg_1 of every row (prepare_tc_kernel)
   const __half* Xh;         // z_ld x k_pad: FP16 hi of the points split at the last refresh
-  const float* corrn;       // z or null: ||A_E^T corr / sigma||_2 (see add_correction)
+  const float* corrn;       // z or null: ||Q^T corr / sigma||_2 (see add_correction)
   // The tracked slack's error since the last refresh, per walker: bounded by
   // Ks_i E_k + k 2^-24 |b_i / scale_i| after k updates, with
   //   E_k = (||x_r / sigma|| + sum_t |theta_t| ||d_hat_t||) (1 + k / (4 T + 4)),
@@ -74,7 +74,7 @@ struct TcParams {
   const __half* Dh;         // z_ld x k_pad
   const __half* Dl;
   const float* sigma;       // n_ld: coordinate scales (operands hold x / sigma, d / sigma)
-  const float* AE32;        // mE x n_ld (equality rows) or null
+  const float* Q32;         // mE x n_ld (orthonormal rows of the equalities) or null
   const float* corr;        // z x mE residual corrections or null
   double* lmin;
   double* lmax;
@@ -433,7 +433,7 @@ walker_tc_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constan
         // Exact null-space correction of the rounded direction (see projection).
         float dlt = 0.0f;
         for (int q2 = 0; q2 < p.mE; ++q2)
-          dlt = fmaf(p.AE32[static_cast<size_t>(q2) * p.n_ld + i],
+          dlt = fmaf(p.Q32[static_cast<size_t>(q2) * p.n_ld + i],
                      p.corr[static_cast<size_t>(kk) * p.mE + q2], dlt);
         p.Xlo[xr] = fmaf(-tw, dlt, p.Xlo[xr]);
       }
@@ -501,7 +501,7 @@ TcParams make_params(const mhar_ctx* c, const TcPlan* plan, int mode, int j, boo
   p.Dh = c->d.Dh;
   p.Dl = c->d.Dl;
   p.sigma = c->d.sigma;
-  p.AE32 = c->d.AE32;
+  p.Q32 = c->d.Q32;
   p.corr = c->d.corr;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;

@@ -30,8 +30,6 @@ void set_null_error(const char* msg) {
 
 namespace {
 
-constexpr int kMaxEqualities = 32;
-
 void remember_create_error(const char* msg) { mhar::set_null_error(msg); }
 
 void set_err(mhar_ctx* c, const char* fmt, ...) {
@@ -94,8 +92,8 @@ bool recompute(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_RECOM
 
 void free_all(mhar_ctx* c) {
   mhar::DeviceBuffers& d = c->d;
-  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.kr32, d.AE64, d.AE32, d.bE64,
-                  d.Lchol, d.Ah, d.Al, d.row_scale, d.bS, d.rows, d.rowk, d.nx_ref, d.theta_acc,
+  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.kr32, d.AE64, d.Q64, d.Q32, d.bE64,
+                  d.wE64, d.Lchol, d.Ah, d.Al, d.row_scale, d.bS, d.rows, d.rowk, d.nx_ref, d.theta_acc,
                   d.refresh_step, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.corrn, d.Xh, d.Xl, d.wscale, d.Dh2, d.Dl2,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
                   d.emit, d.check, d.pc_delta64, d.pc_U64, d.pc_delta32, d.pc_U32, d.sigma};
@@ -104,36 +102,93 @@ void free_all(mhar_ctx* c) {
   d = mhar::DeviceBuffers();
 }
 
-// Projector set-up on the device (Section 3.2): G = A_E A_E^T in FP64, then
-// its Cholesky factor L (lower, row-major).  ok[0] = 0 if G is not positive
-// definite.
-__global__ void proj_setup_kernel(int mE, int n, int n_ld, const double* AE, double* L, int* ok) {
-  __shared__ double G[kMaxEqualities * kMaxEqualities];
-  for (int e = threadIdx.x; e < mE * mE; e += blockDim.x) {
-    const int r = e / mE, q = e % mE;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += AE[static_cast<size_t>(r) * n_ld + i] * AE[static_cast<size_t>(q) * n_ld + i];
-    G[e] = s;
-  }
+// Projector set-up on the device (Section 3.2).  With L the Cholesky factor
+// of A_E A_E^T and Q = L^{-1} A_E (orthonormal rows spanning the row space of
+// A_E), P = I - A_E^T (A_E A_E^T)^{-1} A_E = I - Q^T Q, and the re-projection
+// onto A_E x = b_E is x - Q^T (Q x - w) with w = L^{-1} b_E.  The walkers then
+// need no triangular solves.  Q is taken by CholeskyQR2 (Fukaya, Nakatsukasa,
+// Yanagisawa and Yamamoto, "CholeskyQR2: a simple and communication-avoiding
+// algorithm for computing a tall-skinny QR factorization", 2014): the Cholesky
+// QR step twice, the second on the first's Q, which leaves the rows of Q
+// orthonormal to FP64 rounding while cond(A_E) stays below about 1e7.  All of
+// it in FP64 on the device, in global memory, for any mE < n.
+
+constexpr int kSetupThreads = 256;
+
+// G[r][q] = M_r . M_q for q <= r (lower triangle), one block per entry.
+__global__ void gram_kernel(int mE, int n, int n_ld, const double* M, double* G) {
+  const int r = blockIdx.x, q = blockIdx.y;
+  if (q > r) return;
+  __shared__ double part[kSetupThreads / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    s += M[static_cast<size_t>(r) * n_ld + i] * M[static_cast<size_t>(q) * n_ld + i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int good = 1;
-    for (int jc = 0; jc < mE && good; ++jc) {
-      double dsum = G[jc * mE + jc];
-      for (int k = 0; k < jc; ++k) dsum -= G[jc * mE + k] * G[jc * mE + k];
-      if (!(dsum > 0.0)) { good = 0; break; }
-      const double ljj = sqrt(dsum);
-      G[jc * mE + jc] = ljj;
-      for (int i = jc + 1; i < mE; ++i) {
-        double s = G[i * mE + jc];
-        for (int k = 0; k < jc; ++k) s -= G[i * mE + k] * G[jc * mE + k];
-        G[i * mE + jc] = s / ljj;
-      }
-    }
-    for (int i = 0; i < mE; ++i)
-      for (int q = 0; q < mE; ++q) L[i * mE + q] = q <= i ? G[i * mE + q] : 0.0;
-    ok[0] = good;
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+    G[static_cast<size_t>(r) * mE + q] = t;
   }
+}
+
+// In-place Cholesky factor of the lower triangle of G (one block, column by
+// column: the pivot by a block reduction, the column below it in parallel).
+// ok[0] = 0 when a pivot falls to rel times its diagonal entry or below: A_E
+// is rank-deficient, or too ill-conditioned for the factor to mean anything.
+__global__ void cholesky_kernel(int mE, double* G, double rel, int* ok) {
+  __shared__ double part[kSetupThreads / 32];
+  __shared__ double piv;
+  for (int j = 0; j < mE; ++j) {
+    double* Gj = G + static_cast<size_t>(j) * mE;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) s += Gj[k] * Gj[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+      const double dsum = Gj[j] - t;
+      piv = (dsum > rel * Gj[j]) ? sqrt(dsum) : 0.0;
+      Gj[j] = piv;
+    }
+    __syncthreads();
+    const double ljj = piv;
+    if (!(ljj > 0.0)) {
+      if (threadIdx.x == 0) ok[0] = 0;
+      return;
+    }
+    for (int i = j + 1 + threadIdx.x; i < mE; i += blockDim.x) {
+      double* Gi = G + static_cast<size_t>(i) * mE;
+      double t = Gi[j];
+      for (int k = 0; k < j; ++k) t -= Gi[k] * Gj[k];
+      Gi[j] = t / ljj;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ok[0] = 1;
+}
+
+// M <- L^{-1} M in place (forward substitution), one thread per column of M
+// (mE rows, ncol columns, leading dimension ld); L lower, mE x mE.
+__global__ void trsm_kernel(int mE, int ncol, int ld, const double* L, double* M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncol) return;
+  for (int r = 0; r < mE; ++r) {
+    const double* Lr = L + static_cast<size_t>(r) * mE;
+    double t = M[static_cast<size_t>(r) * ld + i];
+    for (int k = 0; k < r; ++k) t -= Lr[k] * M[static_cast<size_t>(k) * ld + i];
+    M[static_cast<size_t>(r) * ld + i] = t / Lr[r];
+  }
+}
+
+__global__ void to_f32_kernel(size_t count, const double* src, float* dst) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i < count) dst[i] = static_cast<float>(src[i]);
 }
 
 __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const double* x0,
@@ -660,14 +715,12 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
     for (int e = 0; e < mE; ++e)
       std::memcpy(&AEp[static_cast<size_t>(e) * c->n_ld], AE + static_cast<size_t>(e) * n,
                   sizeof(double) * n);
-    std::vector<float> AEf(AEp.begin(), AEp.end());
-    if ((rc = dmalloc(c, &d.AE64, AEp.size())) || (rc = dmalloc(c, &d.AE32, AEf.size())) ||
-        (rc = dmalloc(c, &d.bE64, mE)) || (rc = dmalloc(c, &d.Lchol, static_cast<size_t>(mE) * mE)))
+    if ((rc = dmalloc(c, &d.AE64, AEp.size())) || (rc = dmalloc(c, &d.Q64, AEp.size())) ||
+        (rc = dmalloc(c, &d.Q32, AEp.size())) || (rc = dmalloc(c, &d.bE64, mE)) ||
+        (rc = dmalloc(c, &d.wE64, mE)) || (rc = dmalloc(c, &d.Lchol, static_cast<size_t>(mE) * mE)))
       return rc;
     MHAR_CUDA(cudaMemcpyAsync(d.AE64, AEp.data(), sizeof(double) * AEp.size(),
                               cudaMemcpyHostToDevice, c->stream), "copy AE");
-    MHAR_CUDA(cudaMemcpyAsync(d.AE32, AEf.data(), sizeof(float) * AEf.size(),
-                              cudaMemcpyHostToDevice, c->stream), "copy AE32");
     MHAR_CUDA(cudaMemcpyAsync(d.bE64, bE, sizeof(double) * mE, cudaMemcpyHostToDevice, c->stream),
               "copy bE");
     MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
@@ -716,19 +769,37 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       return rc;
   }
 
-  // Projector factor on the device.
+  // Projector on the device: Q and w by CholeskyQR2.
   if (mE > 0) {
     int* ok = d.status + 1;
-    proj_setup_kernel<<<1, 256, 0, c->stream>>>(mE, n, c->n_ld, d.AE64, d.Lchol, ok);
-    MHAR_CUDA(cudaGetLastError(), "projector set-up kernel");
-    int okh = 0;
-    MHAR_CUDA(cudaMemcpyAsync(&okh, ok, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy");
-    MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
-    MHAR_CUDA(cudaMemsetAsync(ok, 0, sizeof(int), c->stream), "memset");
-    if (!okh) {
-      set_err(c, "A_E A_E^T is not positive definite (rank-deficient equalities)");
-      return MHAR_E_RANK;
+    const size_t qn = static_cast<size_t>(mE) * c->n_ld;
+    MHAR_CUDA(cudaMemcpyAsync(d.Q64, d.AE64, sizeof(double) * qn, cudaMemcpyDeviceToDevice,
+                              c->stream), "copy Q");
+    MHAR_CUDA(cudaMemcpyAsync(d.wE64, d.bE64, sizeof(double) * mE, cudaMemcpyDeviceToDevice,
+                              c->stream), "copy w");
+    for (int pass = 0; pass < 2; ++pass) {
+      gram_kernel<<<dim3(mE, mE), kSetupThreads, 0, c->stream>>>(mE, n, c->n_ld, d.Q64, d.Lchol);
+      MHAR_CUDA(cudaGetLastError(), "projector Gram kernel");
+      // A pivot below 1e-14 of its diagonal entry: cond(A_E) beyond about 1e7.
+      cholesky_kernel<<<1, kSetupThreads, 0, c->stream>>>(mE, d.Lchol, 1e-14, ok);
+      MHAR_CUDA(cudaGetLastError(), "projector Cholesky kernel");
+      int okh = 0;
+      MHAR_CUDA(cudaMemcpyAsync(&okh, ok, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy");
+      MHAR_CUDA(cudaStreamSynchronize(c->stream), "sync");
+      MHAR_CUDA(cudaMemsetAsync(ok, 0, sizeof(int), c->stream), "memset");
+      if (!okh) {
+        set_err(c, "A_E A_E^T is not positive definite (rank-deficient or ill-conditioned "
+                   "equalities, cond(A_E) > ~1e7)");
+        return MHAR_E_RANK;
+      }
+      trsm_kernel<<<(c->n_ld + 127) / 128, 128, 0, c->stream>>>(mE, c->n_ld, c->n_ld, d.Lchol,
+                                                                 d.Q64);
+      trsm_kernel<<<1, 32, 0, c->stream>>>(mE, 1, 1, d.Lchol, d.wE64);
+      MHAR_CUDA(cudaGetLastError(), "projector solve kernel");
     }
+    to_f32_kernel<<<static_cast<unsigned>((qn + 255) / 256), 256, 0, c->stream>>>(qn, d.Q64, d.Q32);
+    MHAR_CUDA(cudaGetLastError(), "projector conversion kernel");
+    MHAR_CUDA(mhar::projection_smem_attr(mE), "projection kernel attributes");
   }
 
   // Algorithm 2: every column of X starts at x0.
@@ -779,9 +850,8 @@ int mhar_create(const double* A, const double* b, int m, int n, const double* AE
   if (!A || !b || !x0 || m < 1 || n < 1 || mE < 0 || (mE > 0 && (!AE || !bE))) {
     set_err(c, "bad pointer or size (m=%d n=%d mE=%d)", m, n, mE);
     rc = MHAR_E_ARG;
-  } else if (mE > kMaxEqualities || mE >= n) {
-    set_err(c, "the library handles 0 <= mE <= %d and mE < n (got mE=%d, n=%d)", kMaxEqualities,
-            mE, n);
+  } else if (mE >= n || mE > 25600) {
+    set_err(c, "the library handles 0 <= mE < n and mE <= 25600 (got mE=%d, n=%d)", mE, n);
     rc = MHAR_E_UNSUPPORTED;
   } else if (c->opts.precision < MHAR_FP64 || c->opts.precision > MHAR_MIXED_RECOMPUTE ||
              c->opts.refresh_k < 0 || c->opts.graph_chunk < 0 || c->opts.emit_walkers < 0 ||

@@ -23,9 +23,11 @@ struct DeviceBuffers {
   float* b32 = nullptr;    // m (FP32 mode: lowered by 3 u |b_i|, see kernels_simt.cu)
   float* kr32 = nullptr;   // 2 m (FP32 mode: the row bounds of chord_simt_kernel)
   double* AE64 = nullptr;  // mE x n_ld
-  float* AE32 = nullptr;   // mE x n_ld
   double* bE64 = nullptr;  // mE
-  double* Lchol = nullptr; // mE x mE, lower Cholesky factor of A_E A_E^T
+  double* Q64 = nullptr;   // mE x n_ld, orthonormal rows: Q = L^{-1} A_E, P = I - Q^T Q
+  float* Q32 = nullptr;    // mE x n_ld, Q in FP32
+  double* wE64 = nullptr;  // mE, w = L^{-1} b_E (Q x = w on the affine subspace)
+  double* Lchol = nullptr; // mE x mE, set-up scratch: Cholesky factors of the Gram matrices
   // Tensor-core operands: A split into FP16 hi/lo after a per-row power-of-two
   // scale; rows padded to m_pad, columns to k_pad.
   __half* Ah = nullptr;    // m_pad x k_pad
@@ -52,8 +54,8 @@ struct DeviceBuffers {
   __half* Dl2 = nullptr;
   float* S = nullptr;      // m_pad x z_ld      (mixed: tracked slack / row_scale, blocked:
                            //  element (i, k) at ((i / 4) z_ld + k) 4 + i % 4)
-  float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix)
-  float* corrn = nullptr;  // z                 (the same: ||A_E^T corr / sigma||_2 bound)
+  float* corr = nullptr;   // z x mE            (FP32 / mixed with equalities: residual fix, Q d)
+  float* corrn = nullptr;  // z                 (the same: ||Q^T corr / sigma||_2 bound)
   __half* Xh = nullptr;    // z_ld x k_pad      (mixed: refresh operand, FP16 hi of scaled X)
   __half* Xl = nullptr;    // z_ld x k_pad      (mixed: FP16 lo)
   float* wscale = nullptr; // z_ld              (mixed: power-of-two scale of each walker)
@@ -150,6 +152,9 @@ inline int mma_chain(const mhar_ctx* c) { return mma_per_step(c) * (c->kdim / kT
 // `j` is the iteration offset added to the device counter *d.step.
 cudaError_t launch_directions(mhar_ctx* ctx, int j);
 cudaError_t launch_projection(mhar_ctx* ctx, int j);
+// Opens the projection kernels' dynamic shared memory to mE coefficient
+// vectors per block (call once per context before the first launch).
+cudaError_t projection_smem_attr(int mE);
 cudaError_t launch_chord_simt(mhar_ctx* ctx);
 // Small bodies in the FP64 / FP32 modes: one warp per walker does the chord,
 // theta and the move (Sections 4.4-4.5) in a single launch.

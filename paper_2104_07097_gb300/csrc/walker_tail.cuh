@@ -10,8 +10,9 @@
 //      the pair being written.
 // After the cluster barrier, when every CTA holds the strip's 128 chords and
 // theta (computed identically in each CTA):
-//  (1) move the point, x += theta (d - A_E^T c')  (Section 4.5; c' is the
-//      exact null-space correction of the rounded direction, when m_E > 0),
+//  (1) move the point, x += theta (d - Q^T c')  (Section 4.5; c' is the
+//      exact row-space part of the rounded direction, Q the orthonormal rows
+//      of A_E, when m_E > 0),
 //      in double-float arithmetic;
 //  (2) split the moved point into the FP16 operand pair of the next
 //      iteration: x_i / (sigma_i 2^e), 2^e the per-walker power of two with
@@ -38,9 +39,9 @@ struct WalkerTail {
   __half* Xl;
   float* wscale;         // z_ld
   const float* sigma;    // n_ld
-  const float* AE32;     // mE x n_ld or null
+  const float* Q32;      // mE x n_ld or null: orthonormal rows Q = L^{-1} A_E
   const float* corr;     // z x mE or null
-  const float* corrn;    // z or null: ||A_E^T corr / sigma||_2 of each walker's direction
+  const float* corrn;    // z or null: ||Q^T corr / sigma||_2 of each walker's direction
   int mE, n, n_ld, k_pad, z_ld, inter, draw;
   int unit_sigma;        // 1: every sigma_i is 1, skip them
   // Preconditioned draw d = delta .* h + U g (pc_rank >= 0; only kernels that
@@ -65,7 +66,7 @@ inline WalkerTail make_walker_tail(const mhar_ctx* c, int inter, bool pc_draw = 
   t.Xl = c->d.Xl;
   t.wscale = c->d.wscale;
   t.sigma = c->d.sigma;
-  t.AE32 = c->d.AE32;
+  t.Q32 = c->d.Q32;
   t.corr = c->d.corr;
   t.corrn = c->d.corrn;
   t.mE = c->mE;
@@ -162,9 +163,9 @@ __device__ __forceinline__ tc::WalkerNorms operand_norms(const __half* Dh, const
   return r;
 }
 
-// With equalities the point moves along d - A_E^T c' (walker_tail (1)) while
-// the chord is found along d: |a_i . A_E^T c'| <= |a_hat_i|_p ||A_E^T c' /
-// sigma||_2 and Kg_p >= 2^-22 |a_hat_i|_p, so 2^22 ||A_E^T c' / sigma||_2 added
+// With equalities the point moves along d - Q^T c' (walker_tail (1)) while
+// the chord is found along d: |a_i . Q^T c'| <= |a_hat_i|_p ||Q^T c' /
+// sigma||_2 and Kg_p >= 2^-22 |a_hat_i|_p, so 2^22 ||Q^T c' / sigma||_2 added
 // to both direction norms covers it in the margin of a_i . d.
 __device__ __forceinline__ void add_correction(const WalkerTail& t, int k, tc::WalkerNorms& wn) {
   if (t.corrn == nullptr) return;
@@ -403,7 +404,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
           if (i >= t.n) continue;
           float dlt = 0.0f;
           for (int q = 0; q < t.mE; ++q)
-            dlt = fmaf(t.AE32[static_cast<size_t>(q) * t.n_ld + i],
+            dlt = fmaf(t.Q32[static_cast<size_t>(q) * t.n_ld + i],
                        t.corr[static_cast<size_t>(k) * t.mE + q], dlt);
           lo[e] = fmaf(-th, dlt, lo[e]);
         }
