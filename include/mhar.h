@@ -326,8 +326,12 @@ int mhar_fit_preconditioner(mhar_ctx* ctx, int64_t warmup, int32_t snapshots, in
  * sampler of its own (Algorithm 2, Lemma 4.2 on the tensor cores) with z
  * walkers, no equalities, and Philox key opts.seed + p for problem p, so
  * problem p's walk is the one a single context with that seed would take.
- * The launch covers every (problem, strip of 128 walkers) unit, largest
- * first, each on a cluster of C CTAs along its rows; mhar_batch_tune picks C. */
+ * Two launch shapes, over the (problem, strip of 128 walkers) units,
+ * largest first: each unit on a cluster of C CTAs along its rows (C = 1, 2,
+ * 4, 8); or a persistent launch of one CTA per SM in which every CTA pulls
+ * whole units from a device queue, so that one unit's walker-side work
+ * overlaps the next unit's loads and MMAs (shape 0).  mhar_batch_tune picks
+ * the shape. */
 typedef struct {
   const double* A;   /* m x n, row-major (copied)                 */
   const double* b;   /* m                                         */
@@ -345,10 +349,16 @@ int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
                       const mhar_opts* opts, mhar_batch** out);
 
 /* Autotuner: times `iters` (1..1024) real iterations of the batch for every
- * cluster size C in {1, 2, 4, 8} (up to the largest problem's row tiles) and
- * keeps the fastest; *cluster (may be NULL) receives it.  The timed
- * iterations advance every walk.  Results do not depend on C. */
+ * shape -- the persistent launch (0) and cluster sizes C in {1, 2, 4, 8} up
+ * to the largest problem's row tiles -- and keeps the fastest; *cluster (may
+ * be NULL) receives it (0 for the persistent launch).  The timed
+ * iterations advance every walk.  Results do not depend on the shape. */
 int mhar_batch_tune(mhar_batch* batch, int32_t iters, int32_t* cluster);
+
+/* Sets the launch shape without timing: 0 the persistent launch,
+ * 1, 2, 4 or 8 clusters of that many CTAs (MHAR_E_ARG otherwise, or when C
+ * exceeds every problem's row tiles).  Results do not depend on it. */
+int mhar_batch_set_shape(mhar_batch* batch, int32_t shape);
 
 /* Advances every problem `steps` iterations; out[p] receives problem p's
  * floor(steps / thin) samples, laid out as for mhar_run (out[p] may be NULL

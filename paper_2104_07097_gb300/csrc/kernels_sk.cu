@@ -351,6 +351,307 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   }
 }
 
+// ---- batched persistent launch --------------------------------------------------
+// Many polytopes in one persistent launch: one CTA per SM pulls whole
+// (problem, walker strip) units from a device queue (an atomic counter over
+// the unit table, largest units first) until the table is exhausted, with
+// the same pipelines as above carried across units.  The producer fetches
+// the next unit as soon as it has issued the current one's loads and hands
+// its index to the MMA issuer and the epilogue through a small ring in
+// shared memory, so one unit's walker-side work (on the epilogue warps)
+// overlaps the next unit's loads and first MMAs, and no CTA is launched or
+// torn down between units.  A unit names its problem, whose tensor maps and
+// parameters the CTA reads from a table in global memory, and whose K chunk
+// count is taken at run time.  Walker operands of a body with n <= 128 (at
+// most two K chunks) stay in shared memory for the whole unit; wider bodies
+// stream them per tile like the single-body kernel.
+struct alignas(128) BskProblem {
+  CUtensorMap ah, al, dh, dl, dh2, dl2, xh, xl;
+  const float* rows;
+  const __half* Xh;
+  const float* wscale;
+  double* lmin;
+  double* lmax;
+  double* theta;
+  int* status;
+  unsigned long long* counters;
+  int* err;
+  const uint64_t* step_ptr;
+  uint64_t seed;
+  uint32_t walker0;
+  int z, kdim, k_chunks, k_pad, m_tiles;
+  WalkerTail wt;
+};
+
+struct BskUnit {
+  int prob;      // problem
+  int strip;     // walker strip within the problem
+};
+
+struct BskParams {
+  const BskProblem* probs;
+  const BskUnit* units;     // largest first
+  int n_units;
+  int* queue;               // two counters, used by alternate iterations
+};
+
+constexpr int kRing = 4;    // unit indices in flight between the producer and the consumers
+
+struct BskRing {
+  uint64_t full[kRing];
+  uint64_t empty[kRing];    // the MMA thread and every epilogue warp release a slot
+  int unit[kRing];
+};
+
+constexpr size_t kSmemBsk = kSmemSk + sizeof(BskRing);
+static_assert(kSmemBsk <= 232448, "recompute_batch_sk_kernel exceeds the shared memory of a CTA");
+
+__global__ void __launch_bounds__(kThreadsSk, 1)
+recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* wslot = base;
+  uint8_t* aslot = base + kWSlots * kWBytes;
+  SkTail* tail = reinterpret_cast<SkTail*>(aslot + kASlots * kABytes);
+  BskRing* ring = reinterpret_cast<BskRing*>(tail + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
+    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    for (int r = 0; r < kRing; ++r) { mbar_init(&ring->full[r], 1); mbar_init(&ring->empty[r], 1 + kEpiWarps); }
+    tail->timed_out = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tail->tmem_base)), "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tail->tmem_base;
+  volatile int* timed_out = &tail->timed_out;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // The problems of a batch advance together.  Iteration s (problem 0's
+  // count) takes units from counter s % 2 and clears the other for
+  // iteration s + 1, which waits for this grid to complete before it reads it.
+  int* err0 = bp.probs[0].err;
+  const uint64_t bstep = *bp.probs[0].step_ptr + static_cast<uint64_t>(j);
+  int* queue = bp.queue + (bstep & 1ull);
+  if (blockIdx.x == 0 && threadIdx.x == 0) bp.queue[(bstep + 1ull) & 1ull] = 0;
+
+  if (warp == 0) {
+    // ---- TMA producer, and the unit fetch --------------------------------------------
+    if (lane == 0) {
+      int w_it = 0, a_it = 0;
+      for (int r = 0;; ++r) {
+        const int rs = r % kRing;
+        if (r >= kRing) mbar_wait(&ring->empty[rs], ((r / kRing) - 1) & 1, timed_out, err0);
+        int u = *timed_out ? bp.n_units : atomicAdd(queue, 1);
+        u = u < bp.n_units ? u : -1;
+        ring->unit[rs] = u;
+        mbar_arrive_sk(&ring->full[rs]);
+        if (u < 0) break;
+        const BskUnit un = bp.units[u];
+        const BskProblem& P = bp.probs[un.prob];
+        const int kch = P.k_chunks;
+        const bool resident = kch <= kWSlots;
+        const int cur = static_cast<int>((*P.step_ptr + static_cast<uint64_t>(j)) & 1ull);
+        const int yw = un.strip * kWalkers;
+        auto load_w = [&](int kc) {
+          const int s = w_it % kWSlots;
+          if (w_it >= kWSlots) mbar_wait(&tail->w_empty[s], ((w_it / kWSlots) - 1) & 1, timed_out, P.err);
+          uint8_t* dst = wslot + s * kWBytes;
+          const int x = kc * kTcKChunk;
+          mbar_expect_tx(&tail->w_full[s], kWBytes);
+          tma_load_2d(dst, cur ? &P.dh2 : &P.dh, &tail->w_full[s], x, yw);
+          tma_load_2d(dst + kOperandBytes, cur ? &P.dl2 : &P.dl, &tail->w_full[s], x, yw);
+          tma_load_2d(dst + 2 * kOperandBytes, &P.xh, &tail->w_full[s], x, yw);
+          tma_load_2d(dst + 3 * kOperandBytes, &P.xl, &tail->w_full[s], x, yw);
+          ++w_it;
+        };
+        if (resident)
+          for (int kc = 0; kc < kch; ++kc) load_w(kc);
+        for (int nt = 0; nt < P.m_tiles; ++nt) {
+          for (int kc = 0; kc < kch; ++kc) {
+            if (!resident) load_w(kc);
+            const int yr = nt * kRowsTile;
+            for (int half = 0; half < 2; ++half, ++a_it) {
+              const int s = a_it % kASlots;
+              if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, P.err);
+              mbar_expect_tx(&tail->a_full[s], kABytes);
+              tma_load_2d(aslot + s * kABytes, half == 0 ? &P.ah : &P.al, &tail->a_full[s],
+                          kc * kTcKChunk, yr);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      int w_it = 0, a_it = 0, gt = 0;
+      for (int r = 0;; ++r) {
+        const int rs = r % kRing;
+        const bool ok = mbar_wait(&ring->full[rs], (r / kRing) & 1, timed_out, err0);
+        const int u = ok ? ring->unit[rs] : -1;
+        mbar_arrive_sk(&ring->empty[rs]);
+        if (u < 0) break;
+        const BskProblem& P = bp.probs[bp.units[u].prob];
+        const int kch = P.k_chunks, kdim = P.kdim;
+        const bool resident = kch <= kWSlots;
+        const int wbase = w_it;
+        for (int nt = 0; nt < P.m_tiles; ++nt, ++gt) {
+          const int b = gt & 1;
+          if (gt >= 2) mbar_wait(&tail->t_empty[b], ((gt >> 1) - 1) & 1, timed_out, P.err);
+          tc_fence_after();
+          const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
+          const uint32_t p_tmem = g_tmem + 128u;
+          for (int kc = 0; kc < kch; ++kc) {
+            const int use = resident ? wbase + kc : w_it;
+            const int ws = use % kWSlots;
+            if (!resident || nt == 0)
+              mbar_wait(&tail->w_full[ws], (use / kWSlots) & 1, timed_out, P.err);
+            const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
+            const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
+            const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
+            const int ks_n = min(kTcKChunk / kTcK, (kdim - kc * kTcKChunk) / kTcK);
+            int as = a_it % kASlots;
+            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, P.err);
+            tc_fence_after();
+            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl,
+                        sw128_desc(smem_u32(aslot + as * kABytes)), idesc, kc > 0 ? 1u : 0u);
+            mma_commit(&tail->a_empty[as]);
+            ++a_it;
+            as = a_it % kASlots;
+            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, P.err);
+            tc_fence_after();
+            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)),
+                        idesc);
+            mma_commit(&tail->a_empty[as]);
+            ++a_it;
+            if (!resident) {
+              mma_commit(&tail->w_empty[ws]);
+              ++w_it;
+            }
+          }
+          mma_commit(&tail->t_full[b]);
+        }
+        if (resident) {
+          // The unit's operand chunks are free once its last MMAs are done.
+          for (int kc = 0; kc < kch; ++kc) mma_commit(&tail->w_empty[(wbase + kc) % kWSlots]);
+          w_it = wbase + kch;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue --------------------------------------------------------------------
+    const int tid = static_cast<int>(threadIdx.x) - 64;
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int cg = e >> 2;
+    const int wl = q * 32 + lane;
+    TailItem none;
+    none.valid = 0;
+    int gt = 0;
+    for (int r = 0;; ++r) {
+      const int rs = r % kRing;
+      const bool ok = mbar_wait(&ring->full[rs], (r / kRing) & 1, timed_out, err0, true);
+      const int u = ok ? ring->unit[rs] : -1;
+      __syncwarp();
+      if (lane == 0) mbar_arrive_sk(&ring->empty[rs]);
+      if (u < 0) break;
+      const BskUnit un = bp.units[u];
+      const BskProblem& P = bp.probs[un.prob];
+      const uint64_t step = *P.step_ptr + static_cast<uint64_t>(j);
+      const int cur = static_cast<int>(step & 1ull);
+      const int strip = un.strip;
+      const int row0 = cg * 32;
+      if (lane == 0) prefetch_l1(row_block(P.rows, row0));
+      if (P.wt.draw)
+        walker_draw_next<kEpiWarps * 32>(P.wt, cur, P.seed, step + 1ull, P.walker0, strip, P.z,
+                                         0, kWalkers, tid);
+      const int k = strip * kWalkers + wl;
+      const float ws = P.wscale[k];
+      WalkerNorms wn =
+          operand_norms<kEpiWarps * 32>(P.wt.Dh[cur], P.Xh, P.k_pad, k, wl, cg, ws, tail->nrm);
+      if (k < P.z) add_correction(P.wt, k, wn);
+      ChordAcc acc;
+      acc.init();
+      for (int nt = 0; nt < P.m_tiles; ++nt, ++gt) {
+        const int b = gt & 1;
+        if (lane == 0 && nt + 1 < P.m_tiles) prefetch_l1(row_block(P.rows, row0 + (nt + 1) * kRowsTile));
+        mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, P.err, true);
+        tc_fence_after();
+        const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+        const uint32_t gcol = tmem + lane_off + static_cast<uint32_t>(b * 256 + cg * 32);
+        float sv[32], gv[32];
+        tmem_ld32(gcol + 128u, sv);
+        tmem_ld32(gcol, gv);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_sk(&tail->t_empty[b]);
+        float fx, fd;
+        wn.pick(P.rows, row0 + nt * kRowsTile, fx, fd);
+        slack32(sv, P.rows, row0 + nt * kRowsTile, ws, fx);
+        scan32(sv, gv, P.rows, row0 + nt * kRowsTile, fd, acc);
+      }
+      const float lo = acc.lo_all(), hi = acc.hi_all();
+      tail->part_lo[cg][wl] = lo;
+      tail->part_hi[cg][wl] = hi;
+      named_bar<kEpiWarps * 32>();
+      if (cg == 0) {
+        const float L = fmaxf(fmaxf(lo, tail->part_lo[1][wl]), fmaxf(tail->part_lo[2][wl], tail->part_lo[3][wl]));
+        const float H = fminf(fminf(hi, tail->part_hi[1][wl]), fminf(tail->part_hi[2][wl], tail->part_hi[3][wl]));
+        float t = 0.0f;
+        if (k < P.z) {
+          int flag = 0;
+          if (isinf(L) || isinf(H)) {
+            flag = MHAR_ST_UNBOUNDED;
+          } else if (L > H) {
+            flag = MHAR_ST_STALL;
+          } else {
+            const U4 w = philox_block(P.seed, step, P.walker0 + static_cast<uint32_t>(k), 0u,
+                                      kStreamChord);
+            const double uu = open_unit_f64(w.x);
+            t = static_cast<float>(static_cast<double>(L) +
+                                   uu * (static_cast<double>(H) - static_cast<double>(L)));
+          }
+          P.lmin[k] = L;
+          P.lmax[k] = H;
+          P.theta[k] = t;
+          if (flag) {
+            atomicOr(P.status, flag);
+            atomicAdd(&P.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
+          }
+        }
+        tail->theta_s[wl] = t;
+      }
+      named_bar<kEpiWarps * 32>();
+      walker_tail<kEpiWarps * 32>(P.wt, cur, strip, P.z, 0, kWalkers, tail->theta_s, tail->red,
+                                  tid, none);
+      named_bar<kEpiWarps * 32>();
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+  }
+}
+
 }  // namespace
 
 // ---- host side -------------------------------------------------------------------
@@ -477,6 +778,107 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   }
   return cudaLaunchKernelEx(&cfg, kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2, tp->dl2, tp->xh,
                             tp->xl, p, j);
+}
+
+// ---- batched persistent launch: host side ---------------------------------------
+struct BatchSkPlan {
+  BskProblem* probs = nullptr;
+  BskUnit* units = nullptr;
+  int* queue = nullptr;
+  int n_units = 0;
+  int grid = 0;
+};
+
+void batch_sk_destroy(void* plan_v) {
+  BatchSkPlan* plan = static_cast<BatchSkPlan*>(plan_v);
+  if (!plan) return;
+  void* ptrs[] = {plan->probs, plan->units, plan->queue};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete plan;
+}
+
+int batch_sk_build(mhar_ctx* const* ctx, int count, void** plan_out, char* err, size_t err_len) {
+  *plan_out = nullptr;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx[0]->device);
+  std::vector<BskProblem> probs(count);
+  std::vector<BskUnit> units;
+  std::vector<long long> size(count);
+  for (int q = 0; q < count; ++q) {
+    const mhar_ctx* c = ctx[q];
+    const TcPlan* tp = static_cast<const TcPlan*>(c->tc);
+    BskProblem& P = probs[q];
+    std::memset(&P, 0, sizeof(P));
+    P.ah = tp->ah; P.al = tp->al; P.dh = tp->dh; P.dl = tp->dl;
+    P.dh2 = tp->dh2; P.dl2 = tp->dl2; P.xh = tp->xh; P.xl = tp->xl;
+    P.rows = c->d.rows;
+    P.Xh = c->d.Xh;
+    P.wscale = c->d.wscale;
+    P.lmin = c->d.lmin;
+    P.lmax = c->d.lmax;
+    P.theta = c->d.theta;
+    P.status = c->d.status;
+    P.counters = c->d.counters;
+    P.err = c->d.status + 1;
+    P.step_ptr = c->d.step;
+    P.seed = c->opts.seed;
+    P.walker0 = c->opts.walker0;
+    P.z = c->z;
+    P.kdim = c->kdim;
+    P.k_chunks = c->k_pad / kTcKChunk;
+    P.k_pad = c->k_pad;
+    P.m_tiles = tc_plan_m_tiles(c);
+    P.wt = make_walker_tail(c, 0);
+    size[q] = static_cast<long long>(P.m_tiles) * P.k_chunks;
+    for (int st = 0; st < tc_plan_strips(c); ++st) units.push_back({q, st});
+  }
+  // Largest units first, so that the last units pulled are short ones.
+  std::stable_sort(units.begin(), units.end(), [&](const BskUnit& a, const BskUnit& b) {
+    return size[a.prob] > size[b.prob];
+  });
+  BatchSkPlan* plan = new BatchSkPlan();
+  plan->n_units = static_cast<int>(units.size());
+  plan->grid = std::min(sms, plan->n_units);
+  cudaError_t e = cudaFuncSetAttribute(recompute_batch_sk_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBsk));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->probs), sizeof(BskProblem) * probs.size());
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->units), sizeof(BskUnit) * units.size());
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->queue), 2 * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->probs, probs.data(), sizeof(BskProblem) * probs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->units, units.data(), sizeof(BskUnit) * units.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(plan->queue, 0, 2 * sizeof(int));
+  if (e != cudaSuccess) {
+    snprintf(err, err_len, "batched persistent plan: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    batch_sk_destroy(plan);
+    return MHAR_E_CUDA;
+  }
+  *plan_out = plan;
+  return MHAR_OK;
+}
+
+cudaError_t launch_recompute_batch_sk(const void* plan_v, int j, cudaStream_t stream) {
+  const BatchSkPlan* plan = static_cast<const BatchSkPlan*>(plan_v);
+  BskParams p;
+  p.probs = plan->probs;
+  p.units = plan->units;
+  p.n_units = plan->n_units;
+  p.queue = plan->queue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan->grid, 1, 1);
+  cfg.blockDim = dim3(kThreadsSk, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBsk;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, recompute_batch_sk_kernel, p, j);
 }
 
 }  // namespace mhar

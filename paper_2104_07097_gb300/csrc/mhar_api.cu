@@ -1267,9 +1267,10 @@ struct mhar_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int z = 0;
-  int C = 1;
+  int C = 1;                    // cluster size; 0: the persistent stream-K launch
   void* table = nullptr;
   int units = 0;
+  void* sk = nullptr;           // stream-K plan (C == 0)
   uint64_t** steps = nullptr;   // device array of every problem's step counter
   cudaGraphExec_t g_chunk = nullptr;
   cudaGraphExec_t g_one = nullptr;
@@ -1306,15 +1307,20 @@ int batch_set_shape(mhar_batch* b, int C) {
   batch_drop_graphs(b);
   if (b->table) cudaFree(b->table);
   b->table = nullptr;
-  int rc = mhar::batch_table_build(b->ctx.data(), static_cast<int>(b->ctx.size()), C, &b->table,
-                                   &b->units, b->err, sizeof(b->err));
+  mhar::batch_sk_destroy(b->sk);
+  b->sk = nullptr;
+  int rc = C == 0 ? mhar::batch_sk_build(b->ctx.data(), static_cast<int>(b->ctx.size()), &b->sk,
+                                         b->err, sizeof(b->err))
+                  : mhar::batch_table_build(b->ctx.data(), static_cast<int>(b->ctx.size()), C,
+                                            &b->table, &b->units, b->err, sizeof(b->err));
   if (rc == MHAR_OK) b->C = C;
   return rc;
 }
 
 cudaError_t batch_enqueue(mhar_batch* b, int count) {
   for (int j = 0; j < count; ++j) {
-    cudaError_t e = mhar::launch_recompute_batch(b->table, b->units, b->C, j, b->stream);
+    cudaError_t e = b->C == 0 ? mhar::launch_recompute_batch_sk(b->sk, j, b->stream)
+                              : mhar::launch_recompute_batch(b->table, b->units, b->C, j, b->stream);
     if (e != cudaSuccess) return e;
   }
   return mhar::launch_advance_many(b->steps, static_cast<int>(b->ctx.size()), count, b->stream);
@@ -1433,7 +1439,8 @@ int mhar_batch_tune(mhar_batch* b, int32_t iters, int32_t* cluster) {
     max_tiles = std::max(max_tiles, mhar::tc_plan_m_tiles(c));
   int best_C = b->C;
   float best = INFINITY;
-  for (int C = 1; C <= 8; C *= 2) {
+  // The persistent stream-K launch (C = 0), then clusters of 1, 2, 4, 8.
+  for (int C = 0; C <= 8; C = C == 0 ? 1 : 2 * C) {
     if (C > max_tiles) break;
     int rc = batch_set_shape(b, C);
     if (rc) return rc;
@@ -1463,6 +1470,19 @@ int mhar_batch_tune(mhar_batch* b, int32_t iters, int32_t* cluster) {
   if (rc) return rc;
   if (cluster) *cluster = best_C;
   return MHAR_OK;
+}
+
+int mhar_batch_set_shape(mhar_batch* b, int32_t shape) {
+  if (!b) return MHAR_E_ARG;
+  int max_tiles = 1;
+  for (mhar_ctx* c : b->ctx) max_tiles = std::max(max_tiles, mhar::tc_plan_m_tiles(c));
+  if (!(shape == 0 || shape == 1 || shape == 2 || shape == 4 || shape == 8) ||
+      (shape > 1 && shape > max_tiles)) {
+    batch_err(b, "shape %d: 0 (stream-K) or a cluster size 1, 2, 4, 8 up to %d row tiles",
+              shape, max_tiles);
+    return MHAR_E_ARG;
+  }
+  return batch_set_shape(b, shape);
 }
 
 int mhar_batch_run(mhar_batch* b, int64_t steps, int64_t thin, double* const* out) {
@@ -1569,6 +1589,7 @@ void mhar_batch_destroy(mhar_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_drop_graphs(b);
   if (b->table) cudaFree(b->table);
+  mhar::batch_sk_destroy(b->sk);
   if (b->steps) cudaFree(b->steps);
   for (mhar_ctx* c : b->ctx) mhar_destroy(c);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

@@ -222,6 +222,11 @@ int batch_table_build(mhar_ctx* const* ctx, int count, int C, void** table, int*
                       char* err, size_t err_len);
 cudaError_t launch_recompute_batch(const void* table, int units, int C, int j,
                                    cudaStream_t stream);
+// Batched persistent stream-K launch (kernels_sk.cu): one CTA per SM, the
+// batch's (problem, strip, row tile) work cut into cost-balanced ranges.
+int batch_sk_build(mhar_ctx* const* ctx, int count, void** plan, char* err, size_t err_len);
+void batch_sk_destroy(void* plan);
+cudaError_t launch_recompute_batch_sk(const void* plan, int j, cudaStream_t stream);
 cudaError_t launch_advance_many(uint64_t* const* steps, int count, int by, cudaStream_t stream);
 
 // Whether the stream-K schedule beats clusters along the rows for this shape.

@@ -41,7 +41,7 @@ ST_DRIFT = 8
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
            "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
            "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
-           "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_run",
+           "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_set_shape", "mhar_batch_run",
            "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
            "mhar_batch_destroy", "mhar_kernel_name", "mhar_last_error", "mhar_strerror",
            "mhar_status_code", "mhar_set_audit", "mhar_batch_set_audit", "mhar_destroy")
@@ -131,6 +131,8 @@ def load(path: str | None = None):
     lib.mhar_batch_create.restype = ctypes.c_int
     lib.mhar_batch_tune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     lib.mhar_batch_tune.restype = ctypes.c_int
+    lib.mhar_batch_set_shape.argtypes = [vp, ctypes.c_int32]
+    lib.mhar_batch_set_shape.restype = ctypes.c_int
     lib.mhar_batch_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(vp)]
     lib.mhar_batch_run.restype = ctypes.c_int
     lib.mhar_batch_get_state.argtypes = [vp, ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_uint64)]
@@ -471,6 +473,13 @@ class Batch:
         if rc != OK:
             self._err(rc)
         return int(c.value)
+
+    def set_shape(self, shape: int) -> None:
+        """0: the persistent launch (CTAs pull units from a device queue); 1, 2,
+        4, 8: clusters of that many CTAs per unit."""
+        rc = load().mhar_batch_set_shape(self._b, int(shape))
+        if rc != OK:
+            self._err(rc)
 
     def run(self, steps: int, thin: int = 0, outs=None):
         """Advances every problem; with thin > 0 returns (or fills) one

@@ -33,9 +33,10 @@ def bodies():
 
 
 def _tuned_iterations(bodies, iters):
-    """Iterations the tuner runs: 1 + iters per candidate cluster size."""
+    """Iterations the tuner runs: 1 + iters per candidate shape (the persistent
+    launch and the cluster sizes)."""
     max_tiles = max((p.m + 127) // 128 for p in bodies)
-    return sum(1 + iters for c in (1, 2, 4, 8) if c <= max_tiles)
+    return sum(1 + iters for c in (0, 1, 2, 4, 8) if c <= max_tiles)
 
 
 def _problems(bodies):
@@ -47,7 +48,7 @@ def test_batch_equals_single_contexts(bodies):
     with mhar.Batch(_problems(bodies), z, seed=seed) as bt:
         got = bt.run(20, thin=5)
         C = bt.tune(4)
-        assert C in (1, 2, 4, 8)
+        assert C in (0, 1, 2, 4, 8)
         got2 = bt.run(12, thin=12)
     for q, p in enumerate(bodies):
         with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=seed + q,
@@ -70,6 +71,45 @@ def test_batch_against_oracle(bodies):
         err = np.abs(got[q] - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
         assert err <= 1e-4, (q, err)
         assert stats[q].max_violation <= 1e-6
+
+
+@pytest.mark.parametrize("z", [256, 4096])
+def test_batch_shapes_bit_equal(bodies, z):
+    # z = 256: 12 units, fewer than the SMs (one unit per CTA of the
+    # persistent launch); z = 4096: 192 units of n from 12 to 150 on 152
+    # SMs, so CTAs pull several units and the shared-memory rings and the
+    # unit ring wrap, switching between resident (n <= 128) and streamed
+    # walker operands.
+    out = {}
+    for shape in (0, 1, 2, 4):
+        with mhar.Batch(_problems(bodies), z, seed=11) as bt:
+            bt.set_shape(shape)
+            out[shape] = bt.run(15, thin=5)
+            stats = [bt.check(q) for q in range(len(bodies))]
+        assert all(st.max_violation <= 1e-10 for st in stats), shape
+    for shape in (0, 2, 4):
+        for q in range(len(bodies)):
+            np.testing.assert_array_equal(out[shape][q], out[1][q], err_msg=f"shape {shape} problem {q}")
+
+
+def test_batch_persistent_against_oracle(bodies):
+    z, seed, steps = 200, 9, 8
+    with mhar.Batch(_problems(bodies), z, seed=seed) as bt:
+        bt.set_shape(0)
+        got = bt.run(steps, thin=1)
+    for q, p in enumerate(bodies):
+        ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, "mixed_rs", thin=1,
+                              seed=seed + q)
+        err = np.abs(got[q] - ref["samples"]).max() / max(1.0, np.abs(ref["samples"]).max())
+        assert err <= 1e-4, (q, err)
+
+
+def test_batch_shape_rejected(bodies):
+    with mhar.Batch(_problems(bodies[:1]), 64) as bt:    # one row tile
+        for bad in (3, -1, 2, 16):
+            with pytest.raises(mhar.MharError) as e:
+                bt.set_shape(bad)
+            assert e.value.code == mhar.E_ARG
 
 
 def test_batch_feasible_over_many_iterations(bodies):
