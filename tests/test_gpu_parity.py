@@ -117,12 +117,16 @@ def test_step_for_step_parity_50(body, z, prec):
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "mixed_rs"])
 @pytest.mark.parametrize("body,z", CASES)
 def test_free_running_parity(body, z, prec):
-    """Free-running chains against the reduced-precision oracle's: within 1e-4
-    over the first 10 iterations.  Over 50 iterations the chain amplifies the
-    kernels' own FP32 rounding of the chord (the reference computes its chord
-    in FP64) about 1000-fold, so the 50-iteration bound is 5e-3.  (Against the
-    pure oracle the margins themselves, about 1e-5 of a chord, are amplified
-    the same way: no bound is asserted on that distance.)"""
+    """Free-running chains against the reduced-precision oracle's for 50
+    iterations.  The kernels' own arithmetic (FP32 slack, the approximate
+    reciprocal of the ratio) differs from the reference's FP64 chord by about
+    1e-6 of a point at the first step; the chain carries that forward, and on
+    the random bodies a few walkers (at most 14 of 256 measured) reach a chord
+    whose binding facet flips, past 1e-4 late in the run.  So: every walker
+    within 1e-4 over the first 10 iterations; 90 % of the walkers within 1e-4
+    at every one of the 50; all within 5e-3.  (Against the pure oracle the
+    margins themselves, about 1e-5 of a chord, are carried the same way: no
+    bound is asserted on that distance.)"""
     p = BODIES[body]()
     X0 = np.tile(p.x0, (z, 1))
     ref = reduced_ref(p, X0, 50, prec, seed=5)
@@ -131,6 +135,10 @@ def test_free_running_parity(body, z, prec):
         st = s.check()
     err = [normwise(got[i], ref["samples"][i]) for i in range(50)]
     assert max(err[:10]) <= TOL[prec], err[:10]
+    for i in range(50):
+        scale = max(1.0, np.abs(ref["samples"][i]).max())
+        per_walker = np.abs(got[i] - ref["samples"][i]).max(axis=1) / scale
+        assert np.quantile(per_walker, 0.9) <= TOL[prec], (i, np.quantile(per_walker, 0.9))
     assert max(err) <= 5e-3, max(err)
     assert st.max_violation <= 1e-6 * np.abs(p.b).max()
     if p.mE:
