@@ -410,6 +410,28 @@ def _ratio(arms, key):
     return a / b if a is not None and b else None
 
 
+FEAS_TOL = 1e-6   # max(A x - b) <= FEAS_TOL |b|_inf; |b|_inf = 1 on every workload here
+
+
+def mark_feasibility(node) -> bool:
+    """Flags every leg (a dict carrying max_violation or run_max_violation)
+    with "feasible": its measured and audited violations within FEAS_TOL;
+    returns whether all legs are."""
+    ok = True
+    if isinstance(node, dict):
+        for v in node.values():
+            ok = mark_feasibility(v) and ok
+        worst = [node[k] for k in ("max_violation", "run_max_violation")
+                 if isinstance(node.get(k), (int, float))]
+        audit = node.get("audit")
+        if isinstance(audit, dict) and isinstance(audit.get("run_max_violation"), (int, float)):
+            worst.append(audit["run_max_violation"])
+        if worst and "max_violation" in node:
+            node["feasible"] = bool(max(worst) <= FEAS_TOL)
+            ok = ok and node["feasible"]
+    return ok
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,6 +598,10 @@ def main() -> None:
             line["ess_moderate"] = ess_leg(stream, torch, mhar, peaks, ESS_MODERATE)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)
+        line["feasibility_ok"] = mark_feasibility(line)
+        if not line["feasibility_ok"]:
+            print("bench: a leg broke max(A x - b) <= 1e-6 |b|_inf (see its 'feasible' flag)",
+                  file=sys.stderr)
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:

@@ -40,3 +40,17 @@ def test_other_ranks_are_silent():
     r = _run({"RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_feasibility_flags():
+    # Every leg carrying max_violation gets a "feasible" flag from its measured
+    # and audited violations (bound 1e-6 |b|_inf, |b|_inf = 1 here).
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"feasibility": {"max_violation": -3e-5, "audit": {"run_max_violation": -1e-5}},
+            "batched": {"max_violation": -2e-5, "audit": {"run_max_violation": 2e-6}},
+            "other": {"x": {"max_violation": 5e-7, "run_max_violation": -1.0}}}
+    assert bench.mark_feasibility(line) is False
+    assert line["feasibility"]["feasible"] is True
+    assert line["batched"]["feasible"] is False
+    assert line["other"]["x"]["feasible"] is True
