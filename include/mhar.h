@@ -318,6 +318,31 @@ int mhar_get_preconditioner(const mhar_ctx* ctx, double* delta, double* U, int32
 int mhar_fit_preconditioner(mhar_ctx* ctx, int64_t warmup, int32_t snapshots, int32_t rank,
                             int32_t power_iters);
 
+/* The same fit in two halves, so that the shards of one ensemble on several
+ * GPUs (disjoint walker0 ranges; walkers are independent chains, Section 4.1)
+ * can pool their warm-up points into one fit: every shard calls
+ * mhar_fit_moments with the same `shift`, the caller sums s1, s2 and count
+ * over the shards (an all-reduce), and every shard calls
+ * mhar_fit_from_moments with the sums, so all of them adopt the same
+ * preconditioner -- the one a single context holding all the walkers fits.
+ *
+ * mhar_fit_moments: runs the warm-up of mhar_fit_preconditioner (same
+ * iterations and snapshots) and returns, about `shift` (n, host; NULL =
+ * walker 0's point at the first snapshot, which differs between shards),
+ *   s1 = sum (x - shift)                 (n, host, caller-allocated)
+ *   s2 = sum (x - shift)(x - shift)^T    (n x n row-major, symmetric)
+ *   *count = z * snapshots
+ * Requires warmup >= 1, 1 <= snapshots <= warmup, z * snapshots >= 2 (else
+ * MHAR_E_ARG); MHAR_E_NONFINITE for a non-finite shift.
+ * mhar_fit_from_moments: Sigma = (s2 - s1 s1^T / count) / (count - 1), then
+ * the rank-`rank` + diagonal fit and its adoption exactly as in
+ * mhar_fit_preconditioner.  Requires count >= 2 and the rank / power_iters
+ * bounds above (else MHAR_E_ARG); MHAR_E_NONFINITE for non-finite moments. */
+int mhar_fit_moments(mhar_ctx* ctx, int64_t warmup, int32_t snapshots, const double* shift,
+                     double* s1, double* s2, int64_t* count);
+int mhar_fit_from_moments(mhar_ctx* ctx, const double* s1, const double* s2, int64_t count,
+                          int32_t rank, int32_t power_iters);
+
 /* ---- batches of polytopes ------------------------------------------------- */
 /* Many independent problems advanced together, one kernel launch per
  * iteration for all of them (the paper runs one polytope at a time; its

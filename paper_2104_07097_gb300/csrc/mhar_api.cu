@@ -564,6 +564,105 @@ int audit(mhar_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// ---- the preconditioner fit, in parts (mhar_fit_preconditioner, and the
+// moments / factor halves used to pool a fit over several shards) ------------
+bool fit_args_ok(mhar_ctx* c, int64_t warmup, int32_t snapshots) {
+  if (warmup < 1 || snapshots < 1 || snapshots > warmup ||
+      static_cast<int64_t>(c->z) * snapshots < 2) {
+    set_err(c, "bad fit arguments (warmup=%lld snapshots=%d, z=%d)",
+            static_cast<long long>(warmup), snapshots, c->z);
+    return false;
+  }
+  return true;
+}
+
+bool factor_args_ok(mhar_ctx* c, int32_t rank, int32_t power_iters) {
+  if (rank < 0 || rank > std::min(mhar::kMaxPcRank, c->n) || power_iters < 0 || power_iters > 64) {
+    set_err(c, "bad fit arguments (rank=%d power_iters=%d, n=%d)", rank, power_iters, c->n);
+    return false;
+  }
+  return true;
+}
+
+void fit_release(mhar_ctx* c, mhar::FitScratch* f) {
+  cudaStreamSynchronize(c->stream);
+  void* ptrs[] = {f->shift, f->s1, f->s2, f->sigma, f->Y, f->Q, f->flag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  *f = mhar::FitScratch();
+}
+
+int fit_alloc(mhar_ctx* c, mhar::FitScratch* f) {
+  const size_t n = static_cast<size_t>(c->n), nn = n * n;
+  int rc;
+  if ((rc = dmalloc(c, &f->shift, n)) || (rc = dmalloc(c, &f->s1, n)) || (rc = dmalloc(c, &f->s2, nn)) ||
+      (rc = dmalloc(c, &f->sigma, nn)) || (rc = dmalloc(c, &f->Y, n * mhar::kMaxPcRank)) ||
+      (rc = dmalloc(c, &f->Q, n * mhar::kMaxPcRank)) || (rc = dmalloc(c, &f->flag, 1)) ||
+      (rc = alloc_preconditioner(c))) {
+    fit_release(c, f);
+    return rc;
+  }
+  return MHAR_OK;
+}
+
+// Warm-up and moments on the device: `snapshots` snapshots spread over the
+// last half of `warmup` iterations; the moments are taken about `shift`
+// (host, n) or, when it is NULL, about walker 0's point at the first snapshot.
+int fit_moments_device(mhar_ctx* c, int64_t warmup, int32_t snapshots, const double* shift,
+                       mhar::FitScratch* f) {
+  const int64_t gap = std::max<int64_t>(1, warmup / (2 * static_cast<int64_t>(snapshots)));
+  const int64_t first = warmup - (snapshots - 1) * gap;
+  if (shift)
+    MHAR_CUDA(cudaMemcpyAsync(f->shift, shift, sizeof(double) * c->n, cudaMemcpyHostToDevice,
+                              c->stream), "copy shift");
+  int rc = MHAR_OK;
+  for (int s = 0; s < snapshots && rc == MHAR_OK; ++s) {
+    rc = mhar_run(c, s == 0 ? first : gap, 0, nullptr);
+    if (rc != MHAR_OK) break;
+    cudaError_t e = cudaSuccess;
+    if (s == 0 && !shift) e = mhar::launch_fit_shift(c, f);
+    if (e == cudaSuccess) e = mhar::launch_fit_accumulate(c, f);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "covariance kernel");
+    c->launches += (s == 0 && !shift) ? 2 : 1;
+  }
+  return rc;
+}
+
+// Sigma from the moments of `samples` points, then (delta, U) into the
+// context's preconditioner buffers.
+int fit_factor_device(mhar_ctx* c, mhar::FitScratch* f, long long samples, int rank,
+                      int power_iters) {
+  cudaError_t e = mhar::launch_fit_factor(c, f, samples, rank, power_iters);
+  if (e != cudaSuccess) return cuda_fail(c, e, "preconditioner fit kernels");
+  c->launches += rank > 0 ? 5 + 2 * power_iters : 2;
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, f->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fit sync");
+  if (flag) {
+    set_err(c, "the warm-up covariance is not finite");
+    return MHAR_E_NONFINITE;
+  }
+  return MHAR_OK;
+}
+
+// The coordinate scales follow the fitted (delta, U) by the rule of
+// mhar_set_preconditioner; then the walk adopts it.
+int fit_adopt(mhar_ctx* c, int rank) {
+  std::vector<double> d64(c->n_ld), u64(static_cast<size_t>(c->n_ld) * mhar::kMaxPcRank);
+  MHAR_CUDA(cudaMemcpy(d64.data(), c->d.pc_delta64, sizeof(double) * d64.size(),
+                       cudaMemcpyDeviceToHost), "copy delta");
+  MHAR_CUDA(cudaMemcpy(u64.data(), c->d.pc_U64, sizeof(double) * u64.size(),
+                       cudaMemcpyDeviceToHost), "copy U");
+  int rc = precond_scales(c, d64.data(), u64.data());
+  if (rc) return rc;
+  return adopt_preconditioner(c, rank);
+}
+
+}  // namespace
+
 extern "C" {
 
 int mhar_status_code(int32_t status_bits, int32_t wait_expired) {
@@ -1052,68 +1151,76 @@ int mhar_get_preconditioner(const mhar_ctx* cc, double* delta, double* U, int32_
 int mhar_fit_preconditioner(mhar_ctx* c, int64_t warmup, int32_t snapshots, int32_t rank,
                             int32_t power_iters) {
   if (!c) return MHAR_E_ARG;
-  if (warmup < 1 || snapshots < 1 || snapshots > warmup ||
-      static_cast<int64_t>(c->z) * snapshots < 2 || rank < 0 ||
-      rank > std::min(mhar::kMaxPcRank, c->n) || power_iters < 0 || power_iters > 64) {
-    set_err(c, "bad fit arguments (warmup=%lld snapshots=%d rank=%d power_iters=%d, z=%d n=%d)",
-            static_cast<long long>(warmup), snapshots, rank, power_iters, c->z, c->n);
+  if (!fit_args_ok(c, warmup, snapshots) || !factor_args_ok(c, rank, power_iters)) return MHAR_E_ARG;
+  mhar::FitScratch f;
+  int rc = fit_alloc(c, &f);
+  if (rc == MHAR_OK) rc = fit_moments_device(c, warmup, snapshots, nullptr, &f);
+  if (rc == MHAR_OK)
+    rc = fit_factor_device(c, &f, static_cast<long long>(c->z) * snapshots, rank, power_iters);
+  fit_release(c, &f);
+  if (rc != MHAR_OK) return rc;
+  return fit_adopt(c, rank);
+}
+
+int mhar_fit_moments(mhar_ctx* c, int64_t warmup, int32_t snapshots, const double* shift,
+                     double* s1, double* s2, int64_t* count) {
+  if (!c) return MHAR_E_ARG;
+  if (!s1 || !s2 || !count) {
+    set_err(c, "s1, s2 and count must not be NULL");
     return MHAR_E_ARG;
   }
-  const int n = c->n;
-  mhar::FitScratch f;
-  int rc = MHAR_OK;
-  auto release = [&]() {
-    cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {f.shift, f.s1, f.s2, f.sigma, f.Y, f.Q, f.flag};
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
-  };
-  const size_t nn = static_cast<size_t>(n) * n;
-  if ((rc = dmalloc(c, &f.shift, n)) || (rc = dmalloc(c, &f.s1, n)) || (rc = dmalloc(c, &f.s2, nn)) ||
-      (rc = dmalloc(c, &f.sigma, nn)) || (rc = dmalloc(c, &f.Y, static_cast<size_t>(n) * mhar::kMaxPcRank)) ||
-      (rc = dmalloc(c, &f.Q, static_cast<size_t>(n) * mhar::kMaxPcRank)) || (rc = dmalloc(c, &f.flag, 1)) ||
-      (rc = alloc_preconditioner(c))) {
-    release();
-    return rc;
-  }
-  const int64_t gap = std::max<int64_t>(1, warmup / (2 * static_cast<int64_t>(snapshots)));
-  const int64_t first = warmup - (snapshots - 1) * gap;
-  for (int s = 0; s < snapshots && rc == MHAR_OK; ++s) {
-    rc = mhar_run(c, s == 0 ? first : gap, 0, nullptr);
-    if (rc != MHAR_OK) break;
-    cudaError_t e = cudaSuccess;
-    if (s == 0) e = mhar::launch_fit_shift(c, &f);
-    if (e == cudaSuccess) e = mhar::launch_fit_accumulate(c, &f);
-    if (e != cudaSuccess) rc = cuda_fail(c, e, "covariance kernel");
-    c->launches += s == 0 ? 2 : 1;
-  }
-  if (rc == MHAR_OK) {
-    cudaError_t e = mhar::launch_fit_factor(c, &f, static_cast<long long>(c->z) * snapshots, rank,
-                                            power_iters);
-    if (e != cudaSuccess) rc = cuda_fail(c, e, "preconditioner fit kernels");
-    c->launches += rank > 0 ? 5 + 2 * power_iters : 2;
-  }
-  int flag = 0;
-  if (rc == MHAR_OK) {
-    cudaError_t e = cudaMemcpyAsync(&flag, f.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) rc = cuda_fail(c, e, "fit sync");
-  }
-  release();
-  if (rc != MHAR_OK) return rc;
-  if (flag) {
-    set_err(c, "the warm-up covariance is not finite");
+  if (!fit_args_ok(c, warmup, snapshots)) return MHAR_E_ARG;
+  if (shift && !all_finite(shift, static_cast<size_t>(c->n))) {
+    set_err(c, "shift is not finite");
     return MHAR_E_NONFINITE;
   }
-  // The coordinate scales follow the fitted (delta, U) by the rule of
-  // mhar_set_preconditioner.
-  std::vector<double> d64(c->n_ld), u64(static_cast<size_t>(c->n_ld) * mhar::kMaxPcRank);
-  MHAR_CUDA(cudaMemcpy(d64.data(), c->d.pc_delta64, sizeof(double) * d64.size(),
-                       cudaMemcpyDeviceToHost), "copy delta");
-  MHAR_CUDA(cudaMemcpy(u64.data(), c->d.pc_U64, sizeof(double) * u64.size(),
-                       cudaMemcpyDeviceToHost), "copy U");
-  if ((rc = precond_scales(c, d64.data(), u64.data()))) return rc;
-  return adopt_preconditioner(c, rank);
+  mhar::FitScratch f;
+  int rc = fit_alloc(c, &f);
+  if (rc == MHAR_OK) rc = fit_moments_device(c, warmup, snapshots, shift, &f);
+  const size_t n = static_cast<size_t>(c->n);
+  if (rc == MHAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(s1, f.s1, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s2, f.s2, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "copy moments");
+  }
+  fit_release(c, &f);
+  if (rc != MHAR_OK) return rc;
+  // Only the upper triangle (j >= i) is accumulated; the rest is returned as
+  // its mirror so that s2 is the full symmetric sum.
+  for (size_t i = 0; i < n; ++i)
+    for (size_t j = 0; j < i; ++j) s2[i * n + j] = s2[j * n + i];
+  *count = static_cast<int64_t>(c->z) * snapshots;
+  return MHAR_OK;
+}
+
+int mhar_fit_from_moments(mhar_ctx* c, const double* s1, const double* s2, int64_t count,
+                          int32_t rank, int32_t power_iters) {
+  if (!c) return MHAR_E_ARG;
+  if (!s1 || !s2 || count < 2) {
+    set_err(c, "s1 and s2 must not be NULL and count must be at least 2 (got %lld)",
+            static_cast<long long>(count));
+    return MHAR_E_ARG;
+  }
+  if (!factor_args_ok(c, rank, power_iters)) return MHAR_E_ARG;
+  const size_t n = static_cast<size_t>(c->n);
+  if (!all_finite(s1, n) || !all_finite(s2, n * n)) {
+    set_err(c, "the moments are not finite");
+    return MHAR_E_NONFINITE;
+  }
+  mhar::FitScratch f;
+  int rc = fit_alloc(c, &f);
+  if (rc == MHAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(f.s1, s1, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f.s2, s2, sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "copy moments");
+  }
+  if (rc == MHAR_OK) rc = fit_factor_device(c, &f, static_cast<long long>(count), rank, power_iters);
+  fit_release(c, &f);
+  if (rc != MHAR_OK) return rc;
+  return fit_adopt(c, rank);
 }
 
 int mhar_get_stats(const mhar_ctx* c, mhar_stats* s) {

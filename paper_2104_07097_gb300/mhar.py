@@ -41,7 +41,8 @@ ST_DRIFT = 8
 EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mhar_set_state",
            "mhar_get_chord", "mhar_check", "mhar_get_stats", "mhar_time_kernels",
            "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
-           "mhar_fit_preconditioner", "mhar_batch_create", "mhar_batch_tune", "mhar_batch_set_shape", "mhar_batch_run",
+           "mhar_fit_preconditioner", "mhar_fit_moments", "mhar_fit_from_moments",
+           "mhar_batch_create", "mhar_batch_tune", "mhar_batch_set_shape", "mhar_batch_run",
            "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
            "mhar_batch_destroy", "mhar_kernel_name", "mhar_last_error", "mhar_strerror",
            "mhar_status_code", "mhar_set_audit", "mhar_batch_set_audit", "mhar_destroy")
@@ -126,6 +127,12 @@ def load(path: str | None = None):
     lib.mhar_fit_preconditioner.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32]
     lib.mhar_fit_preconditioner.restype = ctypes.c_int
+    lib.mhar_fit_moments.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, dp, dp, dp,
+                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.mhar_fit_moments.restype = ctypes.c_int
+    lib.mhar_fit_from_moments.argtypes = [vp, dp, dp, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_int32]
+    lib.mhar_fit_from_moments.restype = ctypes.c_int
     lib.mhar_batch_create.argtypes = [ctypes.POINTER(MharProblem), ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(MharOpts), ctypes.POINTER(vp)]
     lib.mhar_batch_create.restype = ctypes.c_int
@@ -299,6 +306,27 @@ def mhar_fit_preconditioner(ctx, warmup: int, snapshots: int, rank: int, power_i
         raise MharError(rc, mhar_last_error(ctx))
 
 
+def mhar_fit_moments(ctx, n: int, warmup: int, snapshots: int, shift=None):
+    """(s1, s2, count) of the warm-up points about `shift` (see mhar.h)."""
+    s1 = np.zeros(n)
+    s2 = np.zeros((n, n))
+    count = ctypes.c_int64()
+    sh = None if shift is None else _f64(shift)
+    rc = load().mhar_fit_moments(ctx, int(warmup), int(snapshots), _dp(sh), _dp(s1), _dp(s2),
+                                 ctypes.byref(count))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+    return s1, s2, int(count.value)
+
+
+def mhar_fit_from_moments(ctx, s1, s2, count: int, rank: int, power_iters: int) -> None:
+    s1, s2 = _f64(s1), _f64(s2)
+    rc = load().mhar_fit_from_moments(ctx, _dp(s1), _dp(s2), int(count), int(rank),
+                                      int(power_iters))
+    if rc != OK:
+        raise MharError(rc, mhar_last_error(ctx))
+
+
 def mhar_chord_noalloc(A_ptr, b_ptr, m: int, n: int, X_ptr, D_ptr, z: int, lmin_ptr, lmax_ptr,
                        stream=None) -> int:
     """Allocation-free chord of every walker; all array arguments are device
@@ -402,6 +430,15 @@ class Sampler:
                            power_iters: int = 4) -> None:
         """Learns (delta, U) from `warmup` iterations of the chain and freezes it."""
         mhar_fit_preconditioner(self._ctx, warmup, snapshots, min(rank, self.n), power_iters)
+
+    def fit_moments(self, warmup: int, snapshots: int = 10, shift=None):
+        """The warm-up half of the fit: (s1, s2, count) about `shift`, to be
+        summed over the shards of one ensemble and passed to fit_from_moments."""
+        return mhar_fit_moments(self._ctx, self.n, warmup, snapshots, shift)
+
+    def fit_from_moments(self, s1, s2, count: int, rank: int = 32, power_iters: int = 4) -> None:
+        """The factor half of the fit, from (pooled) moments; then frozen."""
+        mhar_fit_from_moments(self._ctx, s1, s2, count, min(rank, self.n), power_iters)
 
     def kernel_name(self) -> str:
         """The kernel that runs each iteration's chord on this sampler."""

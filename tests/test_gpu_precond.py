@@ -167,6 +167,73 @@ def test_fit_parity_on_the_same_points(prec):
     _compare_fit(got, want)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_rs"])
+def test_fit_pooled_over_shards(prec):
+    # Two shards of one ensemble (walker0 = 0 and z) pool their warm-up moments
+    # about a common shift (x0) and both adopt the fit of the pooled moments:
+    # the same moments, the same fit as one context holding all 2 z walkers,
+    # and the oracle's fit of the pooled covariance.
+    p = _fit_body()
+    z, W, S, r, q = 256, 90, 5, 4, 8
+    parts = []
+    for w0 in (0, z):
+        with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=7, walker0=w0) as smp:
+            parts.append(smp.fit_moments(W, S, shift=p.x0))
+    s1 = parts[0][0] + parts[1][0]
+    s2 = parts[0][1] + parts[1][1]
+    count = parts[0][2] + parts[1][2]
+    assert count == 2 * z * S
+    np.testing.assert_allclose(s2, s2.T, rtol=0, atol=0)
+    with mhar.Sampler(p.A, p.b, p.x0, 2 * z, precision=prec, seed=7) as whole:
+        w1, w2, wc = whole.fit_moments(W, S, shift=p.x0)
+        whole.fit_from_moments(w1, w2, wc, r, q)
+        want_whole = whole.preconditioner()
+        X_whole = whole.run(6, thin=6)[0]
+    assert wc == count
+    scale = np.abs(w2).max()
+    np.testing.assert_allclose(s1, w1, rtol=0, atol=1e-12 * max(1.0, np.abs(w1).max()))
+    np.testing.assert_allclose(s2, w2, rtol=0, atol=1e-12 * scale)
+    got, walks = [], []
+    for w0 in (0, z):
+        with mhar.Sampler(p.A, p.b, p.x0, z, precision=prec, seed=7, walker0=w0) as smp:
+            smp.run(W)   # the same warm-up the moments came from
+            smp.fit_from_moments(s1, s2, count, r, q)
+            got.append(smp.preconditioner())
+            walks.append(smp.run(6, thin=6)[0])
+    _compare_fit(got[0], want_whole)
+    np.testing.assert_array_equal(got[0][0], got[1][0])
+    np.testing.assert_array_equal(got[0][1], got[1][1])
+    Sigma = (s2 - np.outer(s1, s1) / count) / (count - 1)
+    _compare_fit(got[0], opc.fit(Sigma, r, q, seed=7))
+    if prec == "fp64":
+        # The shards then walk as the whole ensemble does, walker for walker.
+        err = np.abs(np.vstack(walks) - X_whole).max() / max(1.0, np.abs(X_whole).max())
+        assert err <= 1e-9, err
+
+
+def test_fit_moments_errors():
+    p = _fit_body()
+    with mhar.Sampler(p.A, p.b, p.x0, 64, precision="fp64") as smp:
+        with pytest.raises(mhar.MharError) as e:
+            smp.fit_moments(10, 11)
+        assert e.value.code == mhar.E_ARG
+        with pytest.raises(mhar.MharError) as e:
+            smp.fit_moments(10, 2, shift=np.full(p.n, np.nan))
+        assert e.value.code == mhar.E_NONFINITE
+        s1, s2, c = smp.fit_moments(10, 2)
+        with pytest.raises(mhar.MharError) as e:
+            smp.fit_from_moments(s1, s2, 1, 4, 2)
+        assert e.value.code == mhar.E_ARG
+        bad = s2.copy()
+        bad[0, 0] = np.inf
+        with pytest.raises(mhar.MharError) as e:
+            smp.fit_from_moments(s1, bad, c, 4, 2)
+        assert e.value.code == mhar.E_NONFINITE
+        smp.fit_from_moments(s1, s2, c, 4, 2)
+        assert smp.preconditioner() is not None
+        smp.run(3)
+
+
 def test_fit_rank_zero_and_full_rank():
     p = _fit_body()
     with mhar.Sampler(p.A, p.b, p.x0, 256, precision="fp64", seed=1) as smp:
