@@ -2,8 +2,8 @@
 //
 // Section 4.3 (Generating D): Philox4x32-10 words -> Box-Muller N(0,1) entries
 //   of H, one thread per (walker, quad of coordinates); D = P H through the
-//   factored projector (Section 3.2): d = h - A_E^T (L L^T)^{-1} (A_E h),
-//   with L the Cholesky factor of A_E A_E^T.
+//   projector of Section 3.2 in the form P = I - Q^T Q, Q = L^{-1} A_E with
+//   orthonormal rows (L the Cholesky factor of A_E A_E^T).
 // Section 4.4 (Finding the line sets) in the recompute formulation of
 //   Lemma 4.2: A X and A D are tiled over (64 rows x 64 walkers) blocks, the
 //   slack b - A X and the ratios are formed in registers, and every block
