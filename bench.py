@@ -463,6 +463,12 @@ def main() -> None:
 
     from paper_2104_07097_gb300 import build as libbuild
     from paper_2104_07097_gb300 import mhar
+    # One rank per node compiles (if the library is stale); the others wait,
+    # so no two processes write the same object files.
+    if local == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
     libbuild.build()
     mhar.load()
 
