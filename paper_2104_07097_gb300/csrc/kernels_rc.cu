@@ -23,10 +23,10 @@
 // 4 x 128 columns), so the epilogue of tile t overlaps the MMAs of tile t+1.
 // The walker operands (D and X pairs) stay in shared memory for the whole
 // launch when n <= 128 and are streamed per tile otherwise; the A pairs stream
-// through five 16 KB slots (hi and lo staged separately) so loads run about a
-// tile ahead of the MMAs.  Each CTA pushes its partial chords into every
-// peer's shared memory before one cluster barrier, after which CTAs finish
-// independently.
+// through two pairs of 16 KB half-slots (hi and lo of one K chunk behind one
+// barrier) so loads run a K chunk ahead of the MMAs.  Each CTA pushes its
+// partial chords into every peer's shared memory before one cluster barrier,
+// after which CTAs finish independently.
 //
 // Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM
 // owner, warps 2..17 epilogue (four per TMEM lane quarter, each taking 32 of
@@ -52,7 +52,8 @@ namespace {
 using namespace tc;
 
 constexpr int kWSlots = 2;                           // walker-operand slots
-constexpr int kASlots = 5;                           // A half-slots (Ah or Al of one chunk)
+constexpr int kASlots = 4;                           // A half-slots (Ah or Al of one chunk)
+constexpr int kAPairs = kASlots / 2;                 // A slots: Ah and Al of one chunk
 constexpr int kWBytes = 4 * kOperandBytes;           // Dh, Dl, Xh, Xl chunk
 constexpr int kABytes = kOperandBytes;               // Ah or Al chunk
 constexpr int kEpiWarps = 16;
@@ -134,7 +135,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* wslot = base;                                   // kWSlots x 64 KB
-  uint8_t* aslot = base + kWSlots * kWBytes;               // kASlots x 32 KB
+  uint8_t* aslot = base + kWSlots * kWBytes;               // kASlots x 16 KB
   RcTail* tail = reinterpret_cast<RcTail*>(aslot + kASlots * kABytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -196,13 +197,16 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
             tma_load_2d(dst + 3 * kOperandBytes, &tm_xl, &tail->w_full[s], x, yw);
             ++w_it;
           }
+          // A's hi and lo chunk in one pair of half-slots behind one barrier
+          // (every wait, fence and commit on the MMA thread's path costs issue
+          // time).
           const int yr = row_base + nt * kRowsTile;
-          for (int half = 0; half < 2; ++half, ++a_it) {
-            const int s = a_it % kASlots;
-            if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, p.err);
-            mbar_expect_tx(&tail->a_full[s], kABytes);
-            tma_load_2d(aslot + s * kABytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s], x, yr);
-          }
+          const int s = a_it % kAPairs;
+          if (a_it >= kAPairs) mbar_wait(&tail->a_empty[s], ((a_it / kAPairs) - 1) & 1, timed_out, p.err);
+          mbar_expect_tx(&tail->a_full[s], 2 * kABytes);
+          tma_load_2d(aslot + (2 * s) * kABytes, &tm_ah, &tail->a_full[s], x, yr);
+          tma_load_2d(aslot + (2 * s + 1) * kABytes, &tm_al, &tail->a_full[s], x, yr);
+          ++a_it;
         }
       }
     }
@@ -233,28 +237,21 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
           const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
           const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
           const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-          // A hi: the four products that read it; then release its slot.
-          int as = a_it % kASlots;
-          mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
+          // A hi: the four products that read it; A lo: the hi parts of the
+          // walker operands times it; then release the pair of half-slots.
+          const int as = a_it % kAPairs;
+          mbar_wait(&tail->a_full[as], (a_it / kAPairs) & 1, timed_out, p.err);
           tc_fence_after();
+          const uint64_t ah = sw128_desc(smem_u32(aslot + (2 * as) * kABytes));
+          const uint64_t al = sw128_desc(smem_u32(aslot + (2 * as + 1) * kABytes));
           const int ks_n = KS > 0 ? KS : min(kTcKChunk / kTcK, (p.kdim - kc * kTcKChunk) / kTcK);
-          if constexpr (KS > 0)
-            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, sw128_desc(smem_u32(aslot + as * kABytes)),
-                          idesc, kc > 0 ? 1u : 0u);
-          else
-            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl,
-                        sw128_desc(smem_u32(aslot + as * kABytes)), idesc, kc > 0 ? 1u : 0u);
-          mma_commit(&tail->a_empty[as]);
-          ++a_it;
-          // A lo: hi parts of the walker operands times it.
-          as = a_it % kASlots;
-          mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
-          tc_fence_after();
-          if constexpr (KS > 0)
-            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)), idesc);
-          else
-            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)),
-                        idesc);
+          if constexpr (KS > 0) {
+            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, ah, idesc, kc > 0 ? 1u : 0u);
+            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, al, idesc);
+          } else {
+            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl, ah, idesc, kc > 0 ? 1u : 0u);
+            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, al, idesc);
+          }
           mma_commit(&tail->a_empty[as]);
           ++a_it;
           if (!resident) {

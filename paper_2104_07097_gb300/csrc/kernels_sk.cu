@@ -38,7 +38,9 @@ namespace {
 using namespace tc;
 
 constexpr int kWSlots = 2;                           // walker-operand slots (Dh, Dl, Xh, Xl chunk)
-constexpr int kASlots = 5;                           // A half-slots
+constexpr int kASlots = 4;                           // A half-slots (hi and lo of two chunks)
+constexpr int kAPairs = kASlots / 2;                 // the batched kernel's A slots: hi + lo of a chunk
+static_assert(kASlots >= 2 * kWSlots, "the stream-K kernel pairs A half-slots with walker slots");
 constexpr int kWBytes = 4 * kOperandBytes;
 constexpr int kABytes = kOperandBytes;
 constexpr int kEpiWarps = 16;
@@ -146,31 +148,28 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   const int sb = p.seg_begin[blockIdx.x], se = p.seg_begin[blockIdx.x + 1];
 
   if (warp == 0) {
-    // ---- TMA producer: walker operand chunk and A hi / lo per (tile, k chunk) --
+    // ---- TMA producer: per (tile, k chunk) one slot holds the walker operand
+    // chunk and A's hi / lo chunk, behind one barrier (every barrier wait,
+    // fence and commit on the MMA thread's path costs issue time) ------------
     if (lane == 0) {
-      int w_it = 0, a_it = 0;
+      int w_it = 0;
       for (int sg = sb; sg < se; ++sg) {
         const SkSeg seg = p.segs[sg];
         const int yw = seg.strip * kWalkers;
         for (int nt = seg.t0; nt < seg.t1; ++nt) {
-          for (int kc = 0; kc < p.k_chunks; ++kc) {
+          const int yr = nt * kRowsTile;
+          for (int kc = 0; kc < p.k_chunks; ++kc, ++w_it) {
             const int x = kc * kTcKChunk;
-            int s = w_it % kWSlots;
+            const int s = w_it % kWSlots;
             if (w_it >= kWSlots) mbar_wait(&tail->w_empty[s], ((w_it / kWSlots) - 1) & 1, timed_out, p.err);
             uint8_t* dst = wslot + s * kWBytes;
-            mbar_expect_tx(&tail->w_full[s], kWBytes);
+            mbar_expect_tx(&tail->w_full[s], kWBytes + 2 * kABytes);
             tma_load_2d(dst, cur ? &tm_dh2 : &tm_dh, &tail->w_full[s], x, yw);
             tma_load_2d(dst + kOperandBytes, cur ? &tm_dl2 : &tm_dl, &tail->w_full[s], x, yw);
             tma_load_2d(dst + 2 * kOperandBytes, &tm_xh, &tail->w_full[s], x, yw);
             tma_load_2d(dst + 3 * kOperandBytes, &tm_xl, &tail->w_full[s], x, yw);
-            ++w_it;
-            const int yr = nt * kRowsTile;
-            for (int half = 0; half < 2; ++half, ++a_it) {
-              s = a_it % kASlots;
-              if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, p.err);
-              mbar_expect_tx(&tail->a_full[s], kABytes);
-              tma_load_2d(aslot + s * kABytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s], x, yr);
-            }
+            tma_load_2d(aslot + (2 * s) * kABytes, &tm_ah, &tail->w_full[s], x, yr);
+            tma_load_2d(aslot + (2 * s + 1) * kABytes, &tm_al, &tail->w_full[s], x, yr);
           }
         }
       }
@@ -180,7 +179,7 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     // ---- MMA issuer: G = (Dh + Dl) A^T and P = (Xh + Xl) A^T, 3 products each --
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
-      int w_it = 0, a_it = 0, gt = 0;
+      int w_it = 0, gt = 0;
       for (int sg = sb; sg < se; ++sg) {
         const SkSeg seg = p.segs[sg];
         for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
@@ -189,28 +188,21 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
           tc_fence_after();
           const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
           const uint32_t p_tmem = g_tmem + 128u;
-          // One K chunk; KS (its K steps) is a compile-time constant so that the
-          // MMA runs carry no branches.
+          // One K chunk: one wait, then the A hi run and the A lo run, then one
+          // commit that frees the slot; KS (its K steps) is a compile-time
+          // constant so that the MMA runs carry no branches.
           auto chunk = [&](int kc, auto ks_c) {
             constexpr int KS = decltype(ks_c)::value;
             const int ws = w_it % kWSlots;
             mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
+            tc_fence_after();
             const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
             const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
             const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-            int as = a_it % kASlots;
-            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
-            tc_fence_after();
-            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, sw128_desc(smem_u32(aslot + as * kABytes)),
-                          idesc, kc > 0 ? 1u : 0u);
-            mma_commit(&tail->a_empty[as]);
-            ++a_it;
-            as = a_it % kASlots;
-            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, p.err);
-            tc_fence_after();
-            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)), idesc);
-            mma_commit(&tail->a_empty[as]);
-            ++a_it;
+            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl,
+                          sw128_desc(smem_u32(aslot + (2 * ws) * kABytes)), idesc, kc > 0 ? 1u : 0u);
+            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + (2 * ws + 1) * kABytes)),
+                          idesc);
             mma_commit(&tail->w_empty[ws]);
             ++w_it;
           };
@@ -479,16 +471,16 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
         if (resident)
           for (int kc = 0; kc < kch; ++kc) load_w(kc);
         for (int nt = 0; nt < P.m_tiles; ++nt) {
-          for (int kc = 0; kc < kch; ++kc) {
+          for (int kc = 0; kc < kch; ++kc, ++a_it) {
             if (!resident) load_w(kc);
-            const int yr = nt * kRowsTile;
-            for (int half = 0; half < 2; ++half, ++a_it) {
-              const int s = a_it % kASlots;
-              if (a_it >= kASlots) mbar_wait(&tail->a_empty[s], ((a_it / kASlots) - 1) & 1, timed_out, P.err);
-              mbar_expect_tx(&tail->a_full[s], kABytes);
-              tma_load_2d(aslot + s * kABytes, half == 0 ? &P.ah : &P.al, &tail->a_full[s],
-                          kc * kTcKChunk, yr);
-            }
+            // A's hi and lo chunk in one pair of half-slots behind one barrier.
+            const int s = a_it % kAPairs;
+            if (a_it >= kAPairs) mbar_wait(&tail->a_empty[s], ((a_it / kAPairs) - 1) & 1, timed_out, P.err);
+            mbar_expect_tx(&tail->a_full[s], 2 * kABytes);
+            tma_load_2d(aslot + (2 * s) * kABytes, &P.ah, &tail->a_full[s], kc * kTcKChunk,
+                        nt * kRowsTile);
+            tma_load_2d(aslot + (2 * s + 1) * kABytes, &P.al, &tail->a_full[s], kc * kTcKChunk,
+                        nt * kRowsTile);
           }
         }
       }
@@ -524,18 +516,13 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
             const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
             const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
             const int ks_n = min(kTcKChunk / kTcK, (kdim - kc * kTcKChunk) / kTcK);
-            int as = a_it % kASlots;
-            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, P.err);
+            const int as = a_it % kAPairs;
+            mbar_wait(&tail->a_full[as], (a_it / kAPairs) & 1, timed_out, P.err);
             tc_fence_after();
             mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl,
-                        sw128_desc(smem_u32(aslot + as * kABytes)), idesc, kc > 0 ? 1u : 0u);
-            mma_commit(&tail->a_empty[as]);
-            ++a_it;
-            as = a_it % kASlots;
-            mbar_wait(&tail->a_full[as], (a_it / kASlots) & 1, timed_out, P.err);
-            tc_fence_after();
-            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + as * kABytes)),
-                        idesc);
+                        sw128_desc(smem_u32(aslot + (2 * as) * kABytes)), idesc, kc > 0 ? 1u : 0u);
+            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh,
+                        sw128_desc(smem_u32(aslot + (2 * as + 1) * kABytes)), idesc);
             mma_commit(&tail->a_empty[as]);
             ++a_it;
             if (!resident) {

@@ -12,7 +12,8 @@
 //     only feeds the rows of A -- half the operand bytes per MMA of the
 //     shared-memory form, which is what limited that form;
 //   * the rows of A stream in 128-row tiles (MMA N = 128) through eight
-//     16 KB slots (hi and lo staged separately), up to two tiles ahead;
+//     16 KB slots, the hi and lo halves of one K chunk behind one barrier, up
+//     to two tiles ahead;
 //   * the G and P accumulators of a tile (128 + 128 columns) take the other
 //     256 TMEM columns.  A tile's MMAs run as two passes, P first, then G,
 //     each with its own full / empty barrier pair: the epilogue copies P to
@@ -51,6 +52,7 @@ using namespace tc;
 constexpr int kTile = 128;                           // MMA N: rows of A per tile
 constexpr int kSlotBytes = kTile * kTcKChunk * 2;    // 128 x 64 FP16 = 16 KB
 constexpr int kSlots = 8;                            // two tiles of A (hi, lo) ahead
+constexpr int kPairs = kSlots / 2;                   // hi + lo of one K chunk per barrier
 constexpr int kEpiWarps = 16;
 constexpr int kThreadsTs = (2 + kEpiWarps) * 32;
 constexpr int kMaxCluster = 8;
@@ -110,38 +112,37 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
 }
 
 // One 64-column K chunk of a tile's P pass (X hi, X lo times A hi; X hi
-// times A lo) with KS K steps; slot uses ih = it0 + 2 kc (A hi), ih + 1 (A lo).
+// times A lo) with KS K steps; pair use pu = p0 + kc holds A hi in half-slot
+// 2 (pu % kPairs) and A lo in the next, behind one barrier (every wait, fence
+// and commit on the issuing thread's path costs issue time).
 template <int KS>
-__device__ __forceinline__ void ts_p_chunk(TsTail* tail, uint8_t* base, int it0, int kc,
+__device__ __forceinline__ void ts_p_chunk(TsTail* tail, uint8_t* base, int p0, int kc,
                                            uint32_t p_tmem, uint32_t op_xh, uint32_t op_xl,
                                            uint32_t idesc, volatile int* timed_out, int* err) {
-  const int ih = it0 + 2 * kc, il = ih + 1;
+  const int pu = p0 + kc, ps = pu % kPairs;
   const uint32_t ac0 = static_cast<uint32_t>(kc * 32);   // 2 FP16 per column
-  mbar_wait(&tail->a_full[ih % kSlots], (ih / kSlots) & 1, timed_out, err);
+  mbar_wait(&tail->a_full[ps], (pu / kPairs) & 1, timed_out, err);
   tc_fence_after();
   // A slot's descriptor is built once; a K step of 16 FP16 adds 2 to it (32 bytes).
-  const uint64_t bh = sw128_desc(smem_u32(base + (ih % kSlots) * kSlotBytes));
+  const uint64_t bh = sw128_desc(smem_u32(base + (2 * ps) * kSlotBytes));
+  const uint64_t bl = sw128_desc(smem_u32(base + (2 * ps + 1) * kSlotBytes));
   mma_ts_run2<KS>(p_tmem, op_xh + ac0, op_xl + ac0, bh, idesc, kc > 0 ? 1u : 0u);
-  mbar_wait(&tail->a_full[il % kSlots], (il / kSlots) & 1, timed_out, err);
-  tc_fence_after();
-  const uint64_t bl = sw128_desc(smem_u32(base + (il % kSlots) * kSlotBytes));
   mma_ts_run1<KS>(p_tmem, op_xh + ac0, bl, idesc);
 }
 
 // The same chunk of the G pass (D hi, D lo times A hi; D hi times A lo); the
-// slots were waited for by the P pass and are released here.
+// pair was waited for by the P pass and is released here.
 template <int KS>
-__device__ __forceinline__ void ts_g_chunk(TsTail* tail, uint8_t* base, int it0, int kc,
+__device__ __forceinline__ void ts_g_chunk(TsTail* tail, uint8_t* base, int p0, int kc,
                                            uint32_t g_tmem, uint32_t op_dh, uint32_t op_dl,
                                            uint32_t idesc) {
-  const int ih = it0 + 2 * kc, il = ih + 1;
+  const int pu = p0 + kc, ps = pu % kPairs;
   const uint32_t ac0 = static_cast<uint32_t>(kc * 32);
-  const uint64_t bh = sw128_desc(smem_u32(base + (ih % kSlots) * kSlotBytes));
+  const uint64_t bh = sw128_desc(smem_u32(base + (2 * ps) * kSlotBytes));
+  const uint64_t bl = sw128_desc(smem_u32(base + (2 * ps + 1) * kSlotBytes));
   mma_ts_run2<KS>(g_tmem, op_dh + ac0, op_dl + ac0, bh, idesc, kc > 0 ? 1u : 0u);
-  mma_commit(&tail->a_empty[ih % kSlots]);
-  const uint64_t bl = sw128_desc(smem_u32(base + (il % kSlots) * kSlotBytes));
   mma_ts_run1<KS>(g_tmem, op_dh + ac0, bl, idesc);
-  mma_commit(&tail->a_empty[il % kSlots]);
+  mma_commit(&tail->a_empty[ps]);
 }
 
 // KCH: 64-column K chunks of A's rows (1 or 2: n <= 128); LAST: K steps (16
@@ -264,18 +265,16 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   if (warp == 0) {
     // ---- TMA producer: A rows, 64-row tiles, hi and lo in separate slots ------
     if (lane == 0) {
-      int it = 0;
+      int pu = 0;
       for (int nt = 0; nt < ntiles; ++nt) {
         const int yr = row_base + nt * kTile;
 #pragma unroll
-        for (int kc = 0; kc < KCH; ++kc) {
-          for (int half = 0; half < 2; ++half, ++it) {
-            const int s = it % kSlots;
-            if (it >= kSlots) mbar_wait(&tail->a_empty[s], ((it / kSlots) - 1) & 1, timed_out, p.err);
-            mbar_expect_tx(&tail->a_full[s], kSlotBytes);
-            tma_load_2d(base + s * kSlotBytes, half == 0 ? &tm_ah : &tm_al, &tail->a_full[s],
-                        kc * kTcKChunk, yr);
-          }
+        for (int kc = 0; kc < KCH; ++kc, ++pu) {
+          const int s = pu % kPairs;
+          if (pu >= kPairs) mbar_wait(&tail->a_empty[s], ((pu / kPairs) - 1) & 1, timed_out, p.err);
+          mbar_expect_tx(&tail->a_full[s], 2 * kSlotBytes);
+          tma_load_2d(base + (2 * s) * kSlotBytes, &tm_ah, &tail->a_full[s], kc * kTcKChunk, yr);
+          tma_load_2d(base + (2 * s + 1) * kSlotBytes, &tm_al, &tail->a_full[s], kc * kTcKChunk, yr);
         }
       }
     }
@@ -290,22 +289,22 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
                      op_xl = op_dh + 192u;
       const uint32_t g_tmem = tmem;
       const uint32_t p_tmem = tmem + 128u;
-      int it0 = 0;   // first slot use of the tile
-      for (int nt = 0; nt < ntiles; ++nt, it0 += 2 * KCH) {
+      int p0 = 0;    // first pair use of the tile
+      for (int nt = 0; nt < ntiles; ++nt, p0 += KCH) {
         // P pass: X hi, X lo times A hi; X hi times A lo.  The accumulator is
         // free once the epilogue has copied the previous tile's P out.
         if (nt >= 1) mbar_wait(&tail->p_empty, (nt - 1) & 1, timed_out, p.err);
         tc_fence_after();
         if constexpr (KCH == 2)
-          ts_p_chunk<4>(tail, base, it0, 0, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
-        ts_p_chunk<LAST>(tail, base, it0, KCH - 1, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
+          ts_p_chunk<4>(tail, base, p0, 0, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
+        ts_p_chunk<LAST>(tail, base, p0, KCH - 1, p_tmem, op_xh, op_xl, idesc, timed_out, p.err);
         mma_commit(&tail->p_full);
         // G pass: D hi, D lo times A hi; D hi times A lo.  Each slot is
         // released after its last use here.
         if (nt >= 1) mbar_wait(&tail->g_empty, (nt - 1) & 1, timed_out, p.err);
         tc_fence_after();
-        if constexpr (KCH == 2) ts_g_chunk<4>(tail, base, it0, 0, g_tmem, op_dh, op_dl, idesc);
-        ts_g_chunk<LAST>(tail, base, it0, KCH - 1, g_tmem, op_dh, op_dl, idesc);
+        if constexpr (KCH == 2) ts_g_chunk<4>(tail, base, p0, 0, g_tmem, op_dh, op_dl, idesc);
+        ts_g_chunk<LAST>(tail, base, p0, KCH - 1, g_tmem, op_dh, op_dl, idesc);
         mma_commit(&tail->g_full);
       }
     }
