@@ -226,7 +226,8 @@ def run_reference(args) -> None:
 
 def batch_leg(stream, torch, mhar, peaks) -> dict:
     """256 random polytopes (n ~ U{20..400}, m ~ U{2n..20n}), z = 512 each, one
-    kernel launch per iteration for all of them, cluster size autotuned."""
+    kernel launch per iteration for all of them (or one per bucket of similar
+    n), launch shapes autotuned."""
     B = BATCH_WORKLOAD
     bodies = wl.batch(B["count"], seed=B["seed"])
     z, iters = B["z"], B["iterations"]
@@ -235,6 +236,7 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
     create_s = time.perf_counter() - t0
     try:
         C = bt.tune(B["tune_iters"])
+        per_bucket, bucket_shapes, _ = bt.get_shapes()
         bt.run(16)  # warm-up with the chosen shape (graph capture)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -256,7 +258,9 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
     return {"workload": f"{B['name']}: {B['count']} random polytopes, n ~ U{{20..400}}, "
                         f"m ~ U{{2n..20n}}, z={z} each, {iters} iterations",
             "value": B["count"] * z * iters / secs, "unit": METRIC,
-            "seconds": secs, "cluster": C, "launches_per_iteration": 1,
+            "seconds": secs,
+            "shape": ({"per_bucket": [c for c in bucket_shapes]} if per_bucket else C),
+            "launches_per_iteration": (sum(1 for c in bucket_shapes if c >= 0) if per_bucket else 1),
             "create_seconds": create_s,
             "roofline": {"bound": "tensor", "achieved": flops / secs / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": flops / secs / 1e12 / peak,

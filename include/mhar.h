@@ -356,7 +356,7 @@ int mhar_fit_from_moments(mhar_ctx* ctx, const double* s1, const double* s2, int
  * 4, 8); or a persistent launch of one CTA per SM in which every CTA pulls
  * whole units from a device queue, so that one unit's walker-side work
  * overlaps the next unit's loads and MMAs (shape 0).  mhar_batch_tune picks
- * the shape. */
+ * the shape, for the whole batch or per bucket (below). */
 typedef struct {
   const double* A;   /* m x n, row-major (copied)                 */
   const double* b;   /* m                                         */
@@ -373,17 +373,48 @@ typedef struct mhar_batch mhar_batch;
 int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
                       const mhar_opts* opts, mhar_batch** out);
 
-/* Autotuner: times `iters` (1..1024) real iterations of the batch for every
- * shape -- the persistent launch (0) and cluster sizes C in {1, 2, 4, 8} up
- * to the largest problem's row tiles -- and keeps the fastest; *cluster (may
- * be NULL) receives it (0 for the persistent launch).  The timed
- * iterations advance every walk.  Results do not depend on the shape. */
+/* Autotuner (no counterpart in the paper; its padding study, Section 6.2,
+ * times throughput against the number of walkers).  Times `iters` (1..1024)
+ * real iterations of the whole batch for every single shape -- the
+ * persistent launch (0) and cluster sizes C in {1, 2, 4, 8} up to the
+ * largest problem's row tiles.  Then, when the batch spans two or more
+ * buckets, it tries a shape per bucket by coordinate descent from the best
+ * single shape: one bucket at a time, most work first, takes every other
+ * shape allowed for its problems, the whole batch timed each time; a change
+ * stays only if the batch runs more than 1 % faster.  Per-bucket shapes are
+ * kept if they beat the best single shape by more than 1 %.  *cluster (may
+ * be NULL) receives the single shape kept (0 for the persistent launch), or
+ * -1 for per-bucket shapes (mhar_batch_get_shapes tells them).  Every timed
+ * iteration advances every walk (1 + iters per candidate).  Results do not
+ * depend on the shapes. */
 int mhar_batch_tune(mhar_batch* batch, int32_t iters, int32_t* cluster);
 
-/* Sets the launch shape without timing: 0 the persistent launch,
- * 1, 2, 4 or 8 clusters of that many CTAs (MHAR_E_ARG otherwise, or when C
- * exceeds every problem's row tiles).  Results do not depend on it. */
+/* Sets one launch shape for the whole batch without timing: 0 the
+ * persistent launch, 1, 2, 4 or 8 clusters of that many CTAs (MHAR_E_ARG
+ * otherwise, or when C exceeds every problem's row tiles).  Results do not
+ * depend on it. */
 int mhar_batch_set_shape(mhar_batch* batch, int32_t shape);
+
+/* Buckets: the problems of a batch fall into buckets by the 64-column K
+ * chunks of their operands (n rounded up to a multiple of 64): bucket 0 one
+ * chunk (n <= 64), 1 two, 2 three or four, 3 five to eight, 4 more.  In
+ * per-bucket mode every non-empty bucket's units are launched with the
+ * bucket's own shape, each bucket on a stream of its own forked from and
+ * joined back into the batch's stream, so that the buckets run side by side;
+ * the step counters advance after all of them (one launch per bucket and
+ * iteration).  mhar_batch_set_bucket_shape switches to per-bucket mode (on
+ * the first switch every bucket takes the batch's current shape, clamped to
+ * its problems' row tiles) and sets bucket `bucket`'s shape; MHAR_E_ARG for
+ * an empty bucket or a shape mhar_batch_set_shape would reject for that
+ * bucket's problems.  mhar_batch_set_shape returns to one shape. */
+int mhar_batch_set_bucket_shape(mhar_batch* batch, int32_t bucket, int32_t shape);
+
+/* Current shapes: *per_bucket (may be NULL) is 1 in per-bucket mode, else 0;
+ * shape[5] (may be NULL) receives every bucket's shape (-1 for an empty
+ * bucket; with one shape for the batch, that shape); bucket_of (may be NULL,
+ * one entry per problem) the bucket of every problem. */
+int mhar_batch_get_shapes(const mhar_batch* batch, int32_t* per_bucket, int32_t* shape,
+                          int32_t* bucket_of);
 
 /* Advances every problem `steps` iterations; out[p] receives problem p's
  * floor(steps / thin) samples, laid out as for mhar_run (out[p] may be NULL

@@ -1369,6 +1369,33 @@ int mhar_check(mhar_ctx* c, mhar_stats* s) {
 }  // extern "C"
 
 // ---- batches of problems ----------------------------------------------------------
+// Buckets of a batch's problems by the 64-column K chunks of their operands:
+// 1, 2, 3-4, 5-8, more.  The walker operands stay in shared memory for the
+// first two, and the MMA run of a row tile grows with the chunks, so the
+// balance between a unit's set-up and walker-side work and its MMAs, and
+// with it the best launch shape, changes from bucket to bucket.
+constexpr int kBatchBuckets = 5;
+
+int batch_bucket_of(const mhar_ctx* c) {
+  const int kc = c->k_pad / mhar::kTcKChunk;
+  return kc <= 1 ? 0 : kc == 2 ? 1 : kc <= 4 ? 2 : kc <= 8 ? 3 : 4;
+}
+
+// One bucket in per-bucket mode: its problems, its launch shape and unit
+// table (or persistent plan), and a stream of its own.
+struct BatchBucket {
+  int cls = 0;                      // bucket index (batch_bucket_of)
+  std::vector<mhar_ctx*> ctx;
+  int max_tiles = 1;                // largest row-tile count of its problems
+  int64_t work = 0;                 // sum of m_tiles x k_chunks x strips
+  int C = -1;                       // shape; -1: tables not built
+  void* table = nullptr;
+  int units = 0;
+  void* sk = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
 struct mhar_batch {
   std::vector<mhar_ctx*> ctx;
   cudaStream_t stream = nullptr;
@@ -1385,6 +1412,10 @@ struct mhar_batch {
   int64_t launches = 0;
   int64_t walker_steps = 0;
   int64_t since_audit = 0;
+  bool per_bucket = false;          // every bucket launched with its own shape
+  std::vector<BatchBucket> buckets; // the non-empty buckets
+  std::vector<int> bucket_of;       // bucket index of every problem
+  cudaEvent_t fork = nullptr;
   mhar_opts opts{};
   char err[512] = {0};
 };
@@ -1410,8 +1441,66 @@ void batch_drop_graphs(mhar_batch* b) {
   b->g_chunk = b->g_one = nullptr;
 }
 
-int batch_set_shape(mhar_batch* b, int C) {
+void bucket_release(BatchBucket& k) {
+  if (k.table) cudaFree(k.table);
+  k.table = nullptr;
+  k.units = 0;
+  mhar::batch_sk_destroy(k.sk);
+  k.sk = nullptr;
+  k.C = -1;
+}
+
+// The bucket's launch with shape C (C as for the whole batch).
+int bucket_build(mhar_batch* b, BatchBucket& k, int C) {
   batch_drop_graphs(b);
+  bucket_release(k);
+  const int n = static_cast<int>(k.ctx.size());
+  const int rc = C == 0 ? mhar::batch_sk_build(k.ctx.data(), n, &k.sk, b->err, sizeof(b->err))
+                        : mhar::batch_table_build(k.ctx.data(), n, C, &k.table, &k.units, b->err,
+                                                  sizeof(b->err));
+  if (rc == MHAR_OK) k.C = C;
+  return rc;
+}
+
+// Problems into their buckets, with a stream and an event per bucket.
+int batch_buckets_init(mhar_batch* b) {
+  int index[kBatchBuckets];
+  for (int& i : index) i = -1;
+  b->bucket_of.resize(b->ctx.size());
+  for (size_t q = 0; q < b->ctx.size(); ++q) {
+    mhar_ctx* c = b->ctx[q];
+    const int cls = batch_bucket_of(c);
+    if (index[cls] < 0) {
+      index[cls] = static_cast<int>(b->buckets.size());
+      b->buckets.emplace_back();
+      b->buckets.back().cls = cls;
+    }
+    BatchBucket& k = b->buckets[index[cls]];
+    k.ctx.push_back(c);
+    const int tiles = mhar::tc_plan_m_tiles(c);
+    k.max_tiles = std::max(k.max_tiles, tiles);
+    k.work += static_cast<int64_t>(tiles) * (c->k_pad / mhar::kTcKChunk) * mhar::tc_plan_strips(c);
+    b->bucket_of[q] = cls;
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (BatchBucket& k : b->buckets) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming);
+  }
+  return e == cudaSuccess ? MHAR_OK : batch_cuda(b, e, "bucket streams");
+}
+
+// The largest shape allowed for a bucket at or below C (cluster sizes may
+// not exceed its problems' row tiles).
+int bucket_clamp(const BatchBucket& k, int C) {
+  while (C > 1 && C > k.max_tiles) C /= 2;
+  return C;
+}
+
+int batch_set_shape(mhar_batch* b, int C) {
+  b->per_bucket = false;
+  batch_drop_graphs(b);
+  for (BatchBucket& k : b->buckets) bucket_release(k);
   if (b->table) cudaFree(b->table);
   b->table = nullptr;
   mhar::batch_sk_destroy(b->sk);
@@ -1425,6 +1514,22 @@ int batch_set_shape(mhar_batch* b, int C) {
 }
 
 cudaError_t batch_enqueue(mhar_batch* b, int count) {
+  if (b->per_bucket) {
+    // Every bucket on its own stream, forked from and joined back into the
+    // batch's stream: the buckets run concurrently, each bucket's iterations
+    // in order, and the step counters advance after all of them.
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (BatchBucket& k : b->buckets) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(k.stream, b->fork, 0);
+      for (int j = 0; j < count && e == cudaSuccess; ++j)
+        e = k.C == 0 ? mhar::launch_recompute_batch_sk(k.sk, j, k.stream)
+                     : mhar::launch_recompute_batch(k.table, k.units, k.C, j, k.stream);
+      if (e == cudaSuccess) e = cudaEventRecord(k.done, k.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, k.done, 0);
+    }
+    if (e != cudaSuccess) return e;
+    return mhar::launch_advance_many(b->steps, static_cast<int>(b->ctx.size()), count, b->stream);
+  }
   for (int j = 0; j < count; ++j) {
     cudaError_t e = b->C == 0 ? mhar::launch_recompute_batch_sk(b->sk, j, b->stream)
                               : mhar::launch_recompute_batch(b->table, b->units, b->C, j, b->stream);
@@ -1459,19 +1564,58 @@ int batch_advance(mhar_batch* b, int64_t count) {
     if (rc) return rc;
   }
   const int64_t n = count;
+  const int64_t per_iter = b->per_bucket ? static_cast<int64_t>(b->buckets.size()) : 1;
   while (count >= b->graph_len) {
     cudaError_t e = cudaGraphLaunch(b->g_chunk, b->stream);
     if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
     count -= b->graph_len;
-    b->launches += b->graph_len + 1;
+    b->launches += b->graph_len * per_iter + 1;
   }
   while (count-- > 0) {
     cudaError_t e = cudaGraphLaunch(b->g_one, b->stream);
     if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
-    b->launches += 2;
+    b->launches += per_iter + 1;
   }
   for (mhar_ctx* c : b->ctx) c->step += static_cast<uint64_t>(n);
   b->walker_steps += n * b->z * static_cast<int64_t>(b->ctx.size());
+  return MHAR_OK;
+}
+
+// Device time of `iters` iterations with the current shape(s), after one
+// untimed iteration that captures the graphs.  The iterations are real:
+// every walk advances.
+int batch_time(mhar_batch* b, int iters, float* ms) {
+  int rc = batch_advance(b, 1);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+  if (e == cudaSuccess) {
+    rc = batch_advance(b, iters);
+    if (rc == MHAR_OK) e = cudaEventRecord(e1, b->stream);
+  }
+  if (rc == MHAR_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (rc == MHAR_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  return e == cudaSuccess ? MHAR_OK : batch_cuda(b, e, "tuning");
+}
+
+// Per-bucket mode; buckets without a table yet take shape C0 (clamped).
+int batch_enter_buckets(mhar_batch* b, int C0) {
+  if (b->table) cudaFree(b->table);
+  b->table = nullptr;
+  mhar::batch_sk_destroy(b->sk);
+  b->sk = nullptr;
+  batch_drop_graphs(b);
+  for (BatchBucket& k : b->buckets) {
+    if (k.C >= 0) continue;
+    const int rc = bucket_build(b, k, bucket_clamp(k, C0));
+    if (rc) return rc;
+  }
+  b->per_bucket = true;
   return MHAR_OK;
 }
 
@@ -1520,6 +1664,7 @@ int mhar_batch_create(const mhar_problem* problems, int32_t count, int32_t z,
       e = cudaMemcpy(b->steps, steps.data(), sizeof(uint64_t*) * steps.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) rc = batch_cuda(b, e, "step table");
   }
+  if (rc == MHAR_OK) rc = batch_buckets_init(b);
   if (rc == MHAR_OK) {
     // Default shape: one CTA per unit when the units alone fill the GPU.
     int sms = 148;
@@ -1546,36 +1691,59 @@ int mhar_batch_tune(mhar_batch* b, int32_t iters, int32_t* cluster) {
     max_tiles = std::max(max_tiles, mhar::tc_plan_m_tiles(c));
   int best_C = b->C;
   float best = INFINITY;
-  // The persistent stream-K launch (C = 0), then clusters of 1, 2, 4, 8.
+  // (1) One shape for the whole batch: the persistent launch (C = 0), then
+  // clusters of 1, 2, 4, 8.
   for (int C = 0; C <= 8; C = C == 0 ? 1 : 2 * C) {
     if (C > max_tiles) break;
     int rc = batch_set_shape(b, C);
     if (rc) return rc;
-    rc = batch_advance(b, 1);  // warm-up and graph capture
-    if (rc) return rc;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-    if (e == cudaSuccess) {
-      rc = batch_advance(b, iters);
-      if (rc) return rc;
-      e = cudaEventRecord(e1, b->stream);
-    }
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (e != cudaSuccess) return batch_cuda(b, e, "tuning");
+    rc = batch_time(b, iters, &ms);
+    if (rc) return rc;
     if (ms < best) {
       best = ms;
       best_C = C;
     }
   }
-  int rc = batch_set_shape(b, best_C);
-  if (rc) return rc;
-  if (cluster) *cluster = best_C;
+  // (2) A shape per bucket, by coordinate descent from the best single
+  // shape: one bucket at a time (most work first) tries every other shape
+  // with the whole batch timed; a change stays only if the batch runs more
+  // than 1 % faster.  The mix is kept if it beats the best single shape by
+  // more than 1 %.
+  bool mix = false;
+  if (b->buckets.size() >= 2) {
+    for (BatchBucket& k : b->buckets) bucket_release(k);
+    int rc = batch_enter_buckets(b, best_C);
+    float cur = 0.f;
+    if (rc == MHAR_OK) rc = batch_time(b, iters, &cur);
+    if (rc) return rc;
+    std::vector<BatchBucket*> order;
+    for (BatchBucket& k : b->buckets) order.push_back(&k);
+    std::stable_sort(order.begin(), order.end(),
+                     [](const BatchBucket* x, const BatchBucket* y) { return x->work > y->work; });
+    for (BatchBucket* k : order) {
+      for (int C = 0; C <= 8; C = C == 0 ? 1 : 2 * C) {
+        if (C > k->max_tiles) break;
+        const int prev = k->C;
+        if (C == prev) continue;
+        rc = bucket_build(b, *k, C);
+        float ms = 0.f;
+        if (rc == MHAR_OK) rc = batch_time(b, iters, &ms);
+        if (rc) return rc;
+        if (ms < 0.99f * cur) {
+          cur = ms;
+        } else if ((rc = bucket_build(b, *k, prev))) {
+          return rc;
+        }
+      }
+    }
+    mix = cur < 0.99f * best;
+  }
+  if (!mix) {
+    const int rc = batch_set_shape(b, best_C);
+    if (rc) return rc;
+  }
+  if (cluster) *cluster = mix ? -1 : best_C;
   return MHAR_OK;
 }
 
@@ -1590,6 +1758,39 @@ int mhar_batch_set_shape(mhar_batch* b, int32_t shape) {
     return MHAR_E_ARG;
   }
   return batch_set_shape(b, shape);
+}
+
+int mhar_batch_set_bucket_shape(mhar_batch* b, int32_t bucket, int32_t shape) {
+  if (!b) return MHAR_E_ARG;
+  BatchBucket* k = nullptr;
+  for (BatchBucket& x : b->buckets)
+    if (x.cls == bucket) k = &x;
+  if (!k || !(shape == 0 || shape == 1 || shape == 2 || shape == 4 || shape == 8) ||
+      (shape > 1 && shape > k->max_tiles)) {
+    batch_err(b, "bucket %d shape %d: a non-empty bucket 0..%d and 0 (persistent) or a cluster "
+              "size 1, 2, 4, 8 up to %d row tiles", bucket, shape, kBatchBuckets - 1,
+              k ? k->max_tiles : 0);
+    return MHAR_E_ARG;
+  }
+  if (!b->per_bucket) {
+    for (BatchBucket& x : b->buckets) bucket_release(x);
+    const int rc = batch_enter_buckets(b, b->C);
+    if (rc) return rc;
+  }
+  return bucket_build(b, *k, shape);
+}
+
+int mhar_batch_get_shapes(const mhar_batch* b, int32_t* per_bucket, int32_t* shape,
+                          int32_t* bucket_of) {
+  if (!b) return MHAR_E_ARG;
+  if (per_bucket) *per_bucket = b->per_bucket ? 1 : 0;
+  if (shape) {
+    for (int i = 0; i < kBatchBuckets; ++i) shape[i] = -1;
+    for (const BatchBucket& k : b->buckets) shape[k.cls] = b->per_bucket ? k.C : b->C;
+  }
+  if (bucket_of)
+    for (size_t q = 0; q < b->bucket_of.size(); ++q) bucket_of[q] = b->bucket_of[q];
+  return MHAR_OK;
 }
 
 int mhar_batch_run(mhar_batch* b, int64_t steps, int64_t thin, double* const* out) {
@@ -1697,6 +1898,12 @@ void mhar_batch_destroy(mhar_batch* b) {
   batch_drop_graphs(b);
   if (b->table) cudaFree(b->table);
   mhar::batch_sk_destroy(b->sk);
+  for (BatchBucket& k : b->buckets) {
+    bucket_release(k);
+    if (k.done) cudaEventDestroy(k.done);
+    if (k.stream) cudaStreamDestroy(k.stream);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->steps) cudaFree(b->steps);
   for (mhar_ctx* c : b->ctx) mhar_destroy(c);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

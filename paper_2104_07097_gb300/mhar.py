@@ -43,6 +43,7 @@ EXPORTS = ("mhar_default_opts", "mhar_create", "mhar_run", "mhar_get_state", "mh
            "mhar_chord_noalloc", "mhar_set_preconditioner", "mhar_get_preconditioner",
            "mhar_fit_preconditioner", "mhar_fit_moments", "mhar_fit_from_moments",
            "mhar_batch_create", "mhar_batch_tune", "mhar_batch_set_shape", "mhar_batch_run",
+           "mhar_batch_set_bucket_shape", "mhar_batch_get_shapes",
            "mhar_batch_get_state", "mhar_batch_check", "mhar_batch_last_error",
            "mhar_batch_destroy", "mhar_kernel_name", "mhar_last_error", "mhar_strerror",
            "mhar_status_code", "mhar_set_audit", "mhar_batch_set_audit", "mhar_destroy")
@@ -140,6 +141,11 @@ def load(path: str | None = None):
     lib.mhar_batch_tune.restype = ctypes.c_int
     lib.mhar_batch_set_shape.argtypes = [vp, ctypes.c_int32]
     lib.mhar_batch_set_shape.restype = ctypes.c_int
+    lib.mhar_batch_set_bucket_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.mhar_batch_set_bucket_shape.restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.mhar_batch_get_shapes.argtypes = [vp, i32p, i32p, i32p]
+    lib.mhar_batch_get_shapes.restype = ctypes.c_int
     lib.mhar_batch_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(vp)]
     lib.mhar_batch_run.restype = ctypes.c_int
     lib.mhar_batch_get_state.argtypes = [vp, ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_uint64)]
@@ -505,6 +511,8 @@ class Batch:
         raise MharError(rc, load().mhar_batch_last_error(self._b).decode())
 
     def tune(self, iters: int = 8) -> int:
+        """The autotuner: returns the single shape kept (0, 1, 2, 4, 8) or -1
+        for per-bucket shapes (see ``get_shapes``)."""
         c = ctypes.c_int32()
         rc = load().mhar_batch_tune(self._b, int(iters), ctypes.byref(c))
         if rc != OK:
@@ -517,6 +525,24 @@ class Batch:
         rc = load().mhar_batch_set_shape(self._b, int(shape))
         if rc != OK:
             self._err(rc)
+
+    def set_bucket_shape(self, bucket: int, shape: int) -> None:
+        """Per-bucket mode; bucket 0..4 by the 64-column K chunks of n (1, 2,
+        3-4, 5-8, more) gets launch shape ``shape``."""
+        rc = load().mhar_batch_set_bucket_shape(self._b, int(bucket), int(shape))
+        if rc != OK:
+            self._err(rc)
+
+    def get_shapes(self):
+        """(per_bucket, shape of each of the 5 buckets (-1: empty), bucket of
+        every problem)."""
+        per = ctypes.c_int32()
+        shapes = (ctypes.c_int32 * 5)()
+        of = (ctypes.c_int32 * len(self.shapes))()
+        rc = load().mhar_batch_get_shapes(self._b, ctypes.byref(per), shapes, of)
+        if rc != OK:
+            self._err(rc)
+        return bool(per.value), list(shapes), list(of)
 
     def run(self, steps: int, thin: int = 0, outs=None):
         """Advances every problem; with thin > 0 returns (or fills) one

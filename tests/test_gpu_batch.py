@@ -32,13 +32,6 @@ def bodies():
     return [wl.random_polytope(n, m, seed=s) for (n, m, s) in SHAPES]
 
 
-def _tuned_iterations(bodies, iters):
-    """Iterations the tuner runs: 1 + iters per candidate shape (the persistent
-    launch and the cluster sizes)."""
-    max_tiles = max((p.m + 127) // 128 for p in bodies)
-    return sum(1 + iters for c in (0, 1, 2, 4, 8) if c <= max_tiles)
-
-
 def _problems(bodies):
     return [(p.A, p.b, p.x0) for p in bodies]
 
@@ -48,13 +41,18 @@ def test_batch_equals_single_contexts(bodies):
     with mhar.Batch(_problems(bodies), z, seed=seed) as bt:
         got = bt.run(20, thin=5)
         C = bt.tune(4)
-        assert C in (0, 1, 2, 4, 8)
+        assert C in (-1, 0, 1, 2, 4, 8)
+        # The tuner's timed iterations are real ones and advance every problem
+        # alike, whatever shapes it tries.
+        steps = [bt.state(q)[1] for q in range(len(bodies))]
+        assert len(set(steps)) == 1 and steps[0] > 20
+        tuned = steps[0] - 20
         got2 = bt.run(12, thin=12)
     for q, p in enumerate(bodies):
         with mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", seed=seed + q,
                           smem_operands=True) as s:
             want = s.run(20, thin=5)
-            s.run(_tuned_iterations(bodies, 4))
+            s.run(tuned)
             want2 = s.run(12, thin=12)
         np.testing.assert_array_equal(got[q], want, err_msg=f"problem {q}")
         np.testing.assert_array_equal(got2[q], want2, err_msg=f"problem {q} after tuning")
@@ -92,6 +90,48 @@ def test_batch_shapes_bit_equal(bodies, z):
             np.testing.assert_array_equal(out[shape][q], out[1][q], err_msg=f"shape {shape} problem {q}")
 
 
+def test_batch_per_bucket_shapes_bit_equal(bodies):
+    # Buckets by the 64-column K chunks of n: n = 12, 37, 20, 64 -> bucket 0;
+    # n = 100 -> bucket 1; n = 150 -> bucket 2.  Each bucket on its own
+    # stream with its own shape gives the bits of one shape for the batch.
+    z = 256
+    with mhar.Batch(_problems(bodies), z, seed=21) as bt:
+        bt.set_shape(1)
+        ref = bt.run(15, thin=5)
+        per, shapes, of = bt.get_shapes()
+        assert not per and shapes == [1, 1, 1, -1, -1] and of == [0, 0, 1, 2, 0, 0]
+    for mix in ((2, 0, 4), (0, 1, 0), (4, 2, 1)):
+        with mhar.Batch(_problems(bodies), z, seed=21) as bt:
+            for k, c in enumerate(mix):
+                bt.set_bucket_shape(k, c)
+            per, shapes, _ = bt.get_shapes()
+            assert per and shapes == list(mix) + [-1, -1]
+            got = bt.run(15, thin=5)
+            stats = [bt.check(q) for q in range(len(bodies))]
+            steps = {bt.state(q)[1] for q in range(len(bodies))}
+        assert steps == {15}
+        assert all(st.max_violation <= 1e-10 for st in stats), mix
+        for q in range(len(bodies)):
+            np.testing.assert_array_equal(got[q], ref[q], err_msg=f"shapes {mix} problem {q}")
+    # Back to one shape after per-bucket mode.
+    with mhar.Batch(_problems(bodies), z, seed=21) as bt:
+        bt.set_bucket_shape(2, 0)
+        bt.run(5)
+        bt.set_shape(1)
+        got = bt.run(10, thin=5)
+        assert not bt.get_shapes()[0]
+    for q in range(len(bodies)):
+        np.testing.assert_array_equal(got[q], ref[q][1:], err_msg=f"problem {q}")
+
+
+def test_batch_bucket_shape_rejected(bodies):
+    with mhar.Batch(_problems(bodies), 64) as bt:
+        for bucket, shape in ((3, 1), (4, 0), (-1, 1), (5, 1), (1, 3), (1, 16), (2, -1)):
+            with pytest.raises(mhar.MharError) as e:
+                bt.set_bucket_shape(bucket, shape)
+            assert e.value.code == mhar.E_ARG, (bucket, shape)
+
+
 def test_batch_persistent_against_oracle(bodies):
     z, seed, steps = 200, 9, 8
     with mhar.Batch(_problems(bodies), z, seed=seed) as bt:
@@ -115,10 +155,11 @@ def test_batch_shape_rejected(bodies):
 def test_batch_feasible_over_many_iterations(bodies):
     with mhar.Batch(_problems(bodies), 384, seed=3) as bt:
         bt.tune(2)
+        tuned = bt.state(0)[1]
         bt.run(300)
         for q, p in enumerate(bodies):
             X, step = bt.state(q)
-            assert step == 300 + _tuned_iterations(bodies, 2)
+            assert step == 300 + tuned
             assert (X @ p.A.T - p.b).max() <= 1e-6
             assert bt.check(q).max_violation <= 1e-6
 
