@@ -277,7 +277,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
     const int q = warp & 3;
     const int cg = e >> 2;
     const int row0 = row_base + cg * 32;
-    if (lane == 0 && ntiles > 0) prefetch_l1(row_block(p.rows, row0));
+    if (lane < 4 && ntiles > 0) prefetch_l1(row_block(p.rows, row0) + 32 * lane);
     if (p.wt.draw)
       walker_draw_next<kEpiWarps * 32>(p.wt, cur, p.seed, step + 1ull, p.walker0, strip, p.z,
                                        w_begin, w_count, static_cast<int>(threadIdx.x) - 64);
@@ -291,7 +291,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
     acc.init();
     for (int nt = 0; nt < ntiles; ++nt) {
       const int b = nt & 1;
-      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile));
+      if (lane < 4 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile) + 32 * lane);
       mbar_wait(&tail->t_full[b], (nt >> 1) & 1, timed_out, p.err, true);
       tc_fence_after();
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;

@@ -45,6 +45,12 @@ constexpr int kWBytes = 4 * kOperandBytes;
 constexpr int kABytes = kOperandBytes;
 constexpr int kEpiWarps = 16;
 constexpr int kThreadsSk = (2 + kEpiWarps) * 32;
+// The single-body kernel issues its MMAs from two threads: warp 1 the G
+// products, warp kPWarp the P products (a single thread issuing all of them
+// keeps the tensor pipe near 80 cycles per 128 x 128 x 16 MMA on GB300,
+// against 64 when two threads share the stream).
+constexpr int kPWarp = 2 + kEpiWarps;
+constexpr int kThreadsSk1 = (3 + kEpiWarps) * 32;
 
 // One contiguous range of row tiles of one strip, processed by one CTA.
 struct SkSeg {
@@ -103,7 +109,7 @@ __device__ __forceinline__ void mbar_arrive_sk(uint64_t* bar) {
 
 // LAST: K steps in the operands' last 64-column chunk (1..4).
 template <int LAST>
-__global__ void __launch_bounds__(kThreadsSk, 1)
+__global__ void __launch_bounds__(kThreadsSk1, 1)
 recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
                     const __grid_constant__ CUtensorMap tm_dh2, const __grid_constant__ CUtensorMap tm_dl2,
@@ -118,9 +124,11 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
+    // A walker slot is free once both MMA threads have committed it; a tile's
+    // accumulators are full once both have.
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 2); }
     for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 2); mbar_init(&tail->t_empty[b], kEpiWarps); }
     tail->timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -175,10 +183,13 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // ---- MMA issuer: G = (Dh + Dl) A^T and P = (Xh + Xl) A^T, 3 products each --
+  } else if (warp == 1 || warp == kPWarp) {
+    // ---- MMA issuers: warp 1 G = (Dh + Dl) A^T, warp kPWarp P = (Xh + Xl) A^T,
+    // three products each, in the same order per accumulator as one issuer --
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      const bool g_side = warp == 1;
+      const uint32_t op0 = g_side ? 0u : 2u * kOperandBytes;   // Dh or Xh, then Dl or Xl
       int w_it = 0, gt = 0;
       for (int sg = sb; sg < se; ++sg) {
         const SkSeg seg = p.segs[sg];
@@ -186,8 +197,7 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
           const int b = gt & 1;
           if (gt >= 2) mbar_wait(&tail->t_empty[b], ((gt >> 1) - 1) & 1, timed_out, p.err);
           tc_fence_after();
-          const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
-          const uint32_t p_tmem = g_tmem + 128u;
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>(b * 256) + (g_side ? 0u : 128u);
           // One K chunk: one wait, then the A hi run and the A lo run, then one
           // commit that frees the slot; KS (its K steps) is a compile-time
           // constant so that the MMA runs carry no branches.
@@ -196,13 +206,11 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
             const int ws = w_it % kWSlots;
             mbar_wait(&tail->w_full[ws], (w_it / kWSlots) & 1, timed_out, p.err);
             tc_fence_after();
-            const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
-            const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
-            const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl,
-                          sw128_desc(smem_u32(aslot + (2 * ws) * kABytes)), idesc, kc > 0 ? 1u : 0u);
-            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, sw128_desc(smem_u32(aslot + (2 * ws + 1) * kABytes)),
-                          idesc);
+            const uint32_t w0 = smem_u32(wslot + ws * kWBytes) + op0;
+            const uint64_t o_h = sw128_desc(w0), o_l = sw128_desc(w0 + kOperandBytes);
+            ss_run2<KS>(d_tmem, o_h, o_l, sw128_desc(smem_u32(aslot + (2 * ws) * kABytes)), idesc,
+                        kc > 0 ? 1u : 0u);
+            ss_run1<KS>(d_tmem, o_h, sw128_desc(smem_u32(aslot + (2 * ws + 1) * kABytes)), idesc);
             mma_commit(&tail->w_empty[ws]);
             ++w_it;
           };
@@ -228,7 +236,7 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       const SkSeg seg = p.segs[sg];
       const int strip = seg.strip;
       const int row0 = cg * 32;
-      if (lane == 0 && seg.t1 > seg.t0) prefetch_l1(row_block(p.rows, row0 + seg.t0 * kRowsTile));
+      if (lane < 4 && seg.t1 > seg.t0) prefetch_l1(row_block(p.rows, row0 + seg.t0 * kRowsTile) + 32 * lane);
       // Iteration s+1's directions for this segment's share of the strip's
       // walkers, into the other pair (while the segment's first tile loads).
       if (p.wt.draw) {
@@ -246,7 +254,7 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
       acc.init();
       for (int nt = seg.t0; nt < seg.t1; ++nt, ++gt) {
         const int b = gt & 1;
-        if (lane == 0 && nt + 1 < seg.t1) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile));
+        if (lane < 4 && nt + 1 < seg.t1) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kRowsTile) + 32 * lane);
         mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, p.err, true);
         tc_fence_after();
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -563,7 +571,7 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
       const int cur = static_cast<int>(step & 1ull);
       const int strip = un.strip;
       const int row0 = cg * 32;
-      if (lane == 0) prefetch_l1(row_block(P.rows, row0));
+      if (lane < 4) prefetch_l1(row_block(P.rows, row0) + 32 * lane);
       if (P.wt.draw)
         walker_draw_next<kEpiWarps * 32>(P.wt, cur, P.seed, step + 1ull, P.walker0, strip, P.z,
                                          0, kWalkers, tid);
@@ -576,7 +584,7 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
       acc.init();
       for (int nt = 0; nt < P.m_tiles; ++nt, ++gt) {
         const int b = gt & 1;
-        if (lane == 0 && nt + 1 < P.m_tiles) prefetch_l1(row_block(P.rows, row0 + (nt + 1) * kRowsTile));
+        if (lane < 4 && nt + 1 < P.m_tiles) prefetch_l1(row_block(P.rows, row0 + (nt + 1) * kRowsTile) + 32 * lane);
         mbar_wait(&tail->t_full[b], (gt >> 1) & 1, timed_out, P.err, true);
         tc_fence_after();
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -748,7 +756,7 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   p.wt = make_walker_tail(c, 0);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan->grid, 1, 1);
-  cfg.blockDim = dim3(kThreadsSk, 1, 1);
+  cfg.blockDim = dim3(kThreadsSk1, 1, 1);
   cfg.dynamicSmemBytes = kSmemSk;
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];

@@ -317,7 +317,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int q = warp & 3;
     const int cg = e >> 2;              // 32-column group of each 128-column tile
     const int row0 = row_base + cg * 32;
-    if (lane == 0 && ntiles > 0) prefetch_l1(row_block(p.rows, row0));
+    if (lane < 4 && ntiles > 0) prefetch_l1(row_block(p.rows, row0) + 32 * lane);
     // This thread's walker-side item, copied to shared memory in the background.
     walker_tail_stage<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
                                       static_cast<int>(threadIdx.x) - 64,
@@ -352,7 +352,7 @@ recompute_ts_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     for (int nt = 0; nt < ntiles; ++nt) {
       // P first (its pass ends first), then G; each accumulator is released
       // as soon as it is in registers.
-      if (lane == 0 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kTile));
+      if (lane < 4 && nt + 1 < ntiles) prefetch_l1(row_block(p.rows, row0 + (nt + 1) * kTile) + 32 * lane);
       float sv[32], gv[32];
       mbar_wait(&tail->p_full, nt & 1, timed_out, p.err);
       tc_fence_after();

@@ -179,6 +179,30 @@ __device__ __forceinline__ void mma_ss_lo(uint32_t g, uint32_t p, uint64_t dh, u
   }
 }
 
+// One accumulator's share of those runs, for kernels that issue the G and the
+// P products from two threads: D += A0[ks] B[ks], D += A1[ks] B[ks] per K step
+// (B = the A hi slot), and D += A0[ks] B[ks] (B = the A lo slot), shared-memory
+// descriptors advancing by 2 per K step; the first MMA overwrites when
+// acc_first == 0.
+template <int KS>
+__device__ __forceinline__ void ss_run2(uint32_t d, uint64_t a0, uint64_t a1, uint64_t b,
+                                        uint32_t idesc, uint32_t acc_first) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = static_cast<uint64_t>(2 * ks);
+    mma_f16(d, a0 + o, b + o, idesc, ks > 0 ? 1u : acc_first);
+    mma_f16(d, a1 + o, b + o, idesc, 1u);
+  }
+}
+template <int KS>
+__device__ __forceinline__ void ss_run1(uint32_t d, uint64_t a0, uint64_t b, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const uint64_t o = static_cast<uint64_t>(2 * ks);
+    mma_f16(d, a0 + o, b + o, idesc, 1u);
+  }
+}
+
 // Runtime K-step count (1..4) to the runs above, for kernels that serve
 // bodies of different n in one launch.
 __device__ __forceinline__ void mma_ss_hi_n(int ks_n, uint32_t g, uint32_t p, uint64_t dh,
@@ -324,8 +348,11 @@ struct ChordAcc {
   __device__ __forceinline__ float hi_all() const { return __uint_as_float(hib); }
 };
 
-// Brings one 128-byte line into L1 ahead of its use (the b_i / scale_i of a
-// tile's 32 rows: L1 does not keep them from one launch to the next).
+// Brings one 128-byte line into L1 ahead of its use.  The chord epilogue
+// prefetches the four lines of a 32-row block (row_block below: b_i, Ks, Kg,
+// the form flag), one per lane of lanes 0..3: L1 does not keep them from one
+// launch to the next, and each line missed costs the epilogue -- which sets
+// the pace of a tile when the MMAs are short -- an L2 round trip.
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
