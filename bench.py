@@ -61,7 +61,7 @@ METRIC = "walker-steps/s"
 # entry must be dropped when its kernel changes.
 PROFILED_TRAFFIC = {
     ("rand100x2000", "recompute_ts_kernel"): 9.576e6 + 0.0,
-    ("illcond500x10000", "recompute_sk_kernel"): 208.182e6 + 88.601e6,
+    ("illcond500x10000", "recompute_sk_kernel"): 199.351e6 + 88.730e6,
 }
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
