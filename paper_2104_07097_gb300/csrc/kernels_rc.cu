@@ -28,9 +28,10 @@
 // partial chords into every peer's shared memory before one cluster barrier,
 // after which CTAs finish independently.
 //
-// Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM
-// owner, warps 2..17 epilogue (four per TMEM lane quarter, each taking 32 of
-// every tile's 128 columns).  Every mbarrier wait is bounded (~2 s); on expiry
+// Warp roles (608 threads): warp 0 TMA producer, warp 1 MMA issuer of the G
+// products and TMEM owner, warp 18 MMA issuer of the P products, warps 2..17
+// epilogue (four per TMEM lane quarter, each taking 32 of every tile's 128
+// columns).  Every mbarrier wait is bounded (~2 s); on expiry
 // the kernel flags the error word and still passes every cluster barrier.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -57,7 +58,11 @@ constexpr int kAPairs = kASlots / 2;                 // A slots: Ah and Al of on
 constexpr int kWBytes = 4 * kOperandBytes;           // Dh, Dl, Xh, Xl chunk
 constexpr int kABytes = kOperandBytes;               // Ah or Al chunk
 constexpr int kEpiWarps = 16;
-constexpr int kThreadsRc = (2 + kEpiWarps) * 32;
+// The MMAs are issued from two threads: warp 1 the G products, warp kPWarp
+// the P products (a single thread issuing all of them keeps the tensor pipe
+// near 80 cycles per 128 x 128 x 16 MMA on GB300).
+constexpr int kPWarp = 2 + kEpiWarps;
+constexpr int kThreadsRc = (3 + kEpiWarps) * 32;
 constexpr int kMaxTiles = 32;                        // rows per CTA <= 4096
 constexpr int kMaxCluster = 8;
 
@@ -154,9 +159,11 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
   const bool resident = p.k_chunks <= kWSlots;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
-    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    // Slots are free, and a tile's accumulators full, once both MMA threads
+    // have committed them.
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 2); }
+    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 2); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 2); mbar_init(&tail->t_empty[b], kEpiWarps); }
     tail->timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -211,17 +218,19 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // ---- MMA issuer: G = (Dh + Dl) A^T and P = (Xh + Xl) A^T, 3 products each --
+  } else if (warp == 1 || warp == kPWarp) {
+    // ---- MMA issuers: warp 1 G = (Dh + Dl) A^T, warp kPWarp P = (Xh + Xl) A^T,
+    // three products each, in the same order per accumulator as one issuer --
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      const bool g_side = warp == 1;
+      const uint32_t op0 = g_side ? 0u : 2u * kOperandBytes;   // Dh or Xh, then Dl or Xl
       int w_it = 0, a_it = 0;
       for (int nt = 0; nt < ntiles; ++nt) {
         const int b = nt & 1;
         if (nt >= 2) mbar_wait(&tail->t_empty[b], ((nt >> 1) - 1) & 1, timed_out, p.err);
         tc_fence_after();
-        const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
-        const uint32_t p_tmem = g_tmem + 128u;
+        const uint32_t d_tmem = tmem + static_cast<uint32_t>(b * 256) + (g_side ? 0u : 128u);
         auto chunk = [&](int kc, auto ks_c) {
           constexpr int KS = decltype(ks_c)::value;
           int ws;
@@ -234,23 +243,22 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
           }
           // Descriptors are built once per slot; one K step of 16 FP16 moves the
           // start address by 32 bytes, i.e. adds 2 to the descriptor.
-          const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
-          const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
-          const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
-          // A hi: the four products that read it; A lo: the hi parts of the
-          // walker operands times it; then release the pair of half-slots.
+          const uint32_t w0 = smem_u32(wslot + ws * kWBytes) + op0;
+          const uint64_t o_h = sw128_desc(w0), o_l = sw128_desc(w0 + kOperandBytes);
+          // A hi: the two products that read it; A lo: the hi part of the
+          // walker operand times it; then release the pair of half-slots.
           const int as = a_it % kAPairs;
           mbar_wait(&tail->a_full[as], (a_it / kAPairs) & 1, timed_out, p.err);
           tc_fence_after();
           const uint64_t ah = sw128_desc(smem_u32(aslot + (2 * as) * kABytes));
           const uint64_t al = sw128_desc(smem_u32(aslot + (2 * as + 1) * kABytes));
-          const int ks_n = KS > 0 ? KS : min(kTcKChunk / kTcK, (p.kdim - kc * kTcKChunk) / kTcK);
           if constexpr (KS > 0) {
-            mma_ss_hi<KS>(g_tmem, p_tmem, dh, dl, xh, xl, ah, idesc, kc > 0 ? 1u : 0u);
-            mma_ss_lo<KS>(g_tmem, p_tmem, dh, xh, al, idesc);
+            ss_run2<KS>(d_tmem, o_h, o_l, ah, idesc, kc > 0 ? 1u : 0u);
+            ss_run1<KS>(d_tmem, o_h, al, idesc);
           } else {
-            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl, ah, idesc, kc > 0 ? 1u : 0u);
-            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh, al, idesc);
+            const int ks_n = min(kTcKChunk / kTcK, (p.kdim - kc * kTcKChunk) / kTcK);
+            ss_run2_n(ks_n, d_tmem, o_h, o_l, ah, idesc, kc > 0 ? 1u : 0u);
+            ss_run1_n(ks_n, d_tmem, o_h, al, idesc);
           }
           mma_commit(&tail->a_empty[as]);
           ++a_it;
@@ -329,7 +337,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
   // (the loads do not depend on theta), so their latency overlaps the barrier.
   tc_fence_before();
   cluster_arrive();
-  if (warp >= 2)
+  if (warp >= 2 && warp < kPWarp)
     walker_tail_prefetch<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
                                          static_cast<int>(threadIdx.x) - 64, tail_item);
   cluster_wait();
@@ -339,7 +347,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
                  : "memory");
   }
 
-  if (warp >= 2 && ((warp - 2) >> 2) == 0) {
+  if (warp >= 2 && warp < kPWarp && ((warp - 2) >> 2) == 0) {
     const int q = warp & 3;
     const int wl = q * 32 + lane;
     const int k = strip * kWalkers + wl;
@@ -375,7 +383,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
       }
     }
   }
-  if (warp >= 2) {
+  if (warp >= 2 && warp < kPWarp) {
     named_bar<kEpiWarps * 32>();
     walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count, tail->theta_s,
                                 tail->red, static_cast<int>(threadIdx.x) - 64, tail_item);

@@ -203,6 +203,26 @@ __device__ __forceinline__ void ss_run1(uint32_t d, uint64_t a0, uint64_t b, uin
   }
 }
 
+// Runtime K-step count (1..4) to ss_run2 / ss_run1.
+__device__ __forceinline__ void ss_run2_n(int ks_n, uint32_t d, uint64_t a0, uint64_t a1, uint64_t b,
+                                          uint32_t idesc, uint32_t acc_first) {
+  switch (ks_n) {
+    case 4: ss_run2<4>(d, a0, a1, b, idesc, acc_first); break;
+    case 3: ss_run2<3>(d, a0, a1, b, idesc, acc_first); break;
+    case 2: ss_run2<2>(d, a0, a1, b, idesc, acc_first); break;
+    default: ss_run2<1>(d, a0, a1, b, idesc, acc_first); break;
+  }
+}
+__device__ __forceinline__ void ss_run1_n(int ks_n, uint32_t d, uint64_t a0, uint64_t b,
+                                          uint32_t idesc) {
+  switch (ks_n) {
+    case 4: ss_run1<4>(d, a0, b, idesc); break;
+    case 3: ss_run1<3>(d, a0, b, idesc); break;
+    case 2: ss_run1<2>(d, a0, b, idesc); break;
+    default: ss_run1<1>(d, a0, b, idesc); break;
+  }
+}
+
 // Runtime K-step count (1..4) to the runs above, for kernels that serve
 // bodies of different n in one launch.
 __device__ __forceinline__ void mma_ss_hi_n(int ks_n, uint32_t g, uint32_t p, uint64_t dh,
