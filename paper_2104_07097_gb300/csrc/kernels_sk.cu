@@ -16,7 +16,7 @@
 // depend on the cut), draws theta and does the walker-side work for the
 // whole strip.  Next iteration's directions are drawn early by the strip's
 // segments, each for its share of the walkers.
-// The pipelines (TMA producer, MMA issuer, 16 epilogue warps, double-buffered
+// The pipelines (TMA producer, two MMA issuers, 16 epilogue warps, double-buffered
 // accumulators) run across segment boundaries without re-initialisation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -44,13 +44,12 @@ static_assert(kASlots >= 2 * kWSlots, "the stream-K kernel pairs A half-slots wi
 constexpr int kWBytes = 4 * kOperandBytes;
 constexpr int kABytes = kOperandBytes;
 constexpr int kEpiWarps = 16;
-constexpr int kThreadsSk = (2 + kEpiWarps) * 32;
-// The single-body kernel issues its MMAs from two threads: warp 1 the G
-// products, warp kPWarp the P products (a single thread issuing all of them
-// keeps the tensor pipe near 80 cycles per 128 x 128 x 16 MMA on GB300,
-// against 64 when two threads share the stream).
+// Both kernels issue their MMAs from two threads: warp 1 the G products, warp
+// kPWarp the P products (a single thread issuing all of them keeps the tensor
+// pipe near 80 cycles per 128 x 128 x 16 MMA on GB300, against 64 when two
+// threads share the stream).
 constexpr int kPWarp = 2 + kEpiWarps;
-constexpr int kThreadsSk1 = (3 + kEpiWarps) * 32;
+constexpr int kThreadsSk = (3 + kEpiWarps) * 32;
 
 // One contiguous range of row tiles of one strip, processed by one CTA.
 struct SkSeg {
@@ -109,7 +108,7 @@ __device__ __forceinline__ void mbar_arrive_sk(uint64_t* bar) {
 
 // LAST: K steps in the operands' last 64-column chunk (1..4).
 template <int LAST>
-__global__ void __launch_bounds__(kThreadsSk1, 1)
+__global__ void __launch_bounds__(kThreadsSk, 1)
 recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                     const __grid_constant__ CUtensorMap tm_dh, const __grid_constant__ CUtensorMap tm_dl,
                     const __grid_constant__ CUtensorMap tm_dh2, const __grid_constant__ CUtensorMap tm_dl2,
@@ -399,7 +398,7 @@ constexpr int kRing = 4;    // unit indices in flight between the producer and t
 
 struct BskRing {
   uint64_t full[kRing];
-  uint64_t empty[kRing];    // the MMA thread and every epilogue warp release a slot
+  uint64_t empty[kRing];    // both MMA threads and every epilogue warp release a slot
   int unit[kRing];
 };
 
@@ -418,10 +417,12 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 1); }
-    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 1); mbar_init(&tail->t_empty[b], kEpiWarps); }
-    for (int r = 0; r < kRing; ++r) { mbar_init(&ring->full[r], 1); mbar_init(&ring->empty[r], 1 + kEpiWarps); }
+    // Two MMA threads (G and P): slots and accumulators are released, and
+    // ring entries consumed, by both.
+    for (int s = 0; s < kWSlots; ++s) { mbar_init(&tail->w_full[s], 1); mbar_init(&tail->w_empty[s], 2); }
+    for (int s = 0; s < kASlots; ++s) { mbar_init(&tail->a_full[s], 1); mbar_init(&tail->a_empty[s], 2); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tail->t_full[b], 2); mbar_init(&tail->t_empty[b], kEpiWarps); }
+    for (int r = 0; r < kRing; ++r) { mbar_init(&ring->full[r], 1); mbar_init(&ring->empty[r], 2 + kEpiWarps); }
     tail->timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -494,10 +495,12 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // ---- MMA issuer ------------------------------------------------------------------
+  } else if (warp == 1 || warp == kPWarp) {
+    // ---- MMA issuers: warp 1 the G products, warp kPWarp the P products ---------------
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc(kWalkers, kRowsTile);
+      const bool g_side = warp == 1;
+      const uint32_t op0 = g_side ? 0u : 2u * kOperandBytes;   // Dh or Xh, then Dl or Xl
       int w_it = 0, a_it = 0, gt = 0;
       for (int r = 0;; ++r) {
         const int rs = r % kRing;
@@ -513,24 +516,21 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
           const int b = gt & 1;
           if (gt >= 2) mbar_wait(&tail->t_empty[b], ((gt >> 1) - 1) & 1, timed_out, P.err);
           tc_fence_after();
-          const uint32_t g_tmem = tmem + static_cast<uint32_t>(b * 256);
-          const uint32_t p_tmem = g_tmem + 128u;
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>(b * 256) + (g_side ? 0u : 128u);
           for (int kc = 0; kc < kch; ++kc) {
             const int use = resident ? wbase + kc : w_it;
             const int ws = use % kWSlots;
             if (!resident || nt == 0)
               mbar_wait(&tail->w_full[ws], (use / kWSlots) & 1, timed_out, P.err);
-            const uint32_t w0 = smem_u32(wslot + ws * kWBytes);
-            const uint64_t dh = sw128_desc(w0), dl = sw128_desc(w0 + kOperandBytes);
-            const uint64_t xh = sw128_desc(w0 + 2 * kOperandBytes), xl = sw128_desc(w0 + 3 * kOperandBytes);
+            const uint32_t w0 = smem_u32(wslot + ws * kWBytes) + op0;
+            const uint64_t o_h = sw128_desc(w0), o_l = sw128_desc(w0 + kOperandBytes);
             const int ks_n = min(kTcKChunk / kTcK, (kdim - kc * kTcKChunk) / kTcK);
             const int as = a_it % kAPairs;
             mbar_wait(&tail->a_full[as], (a_it / kAPairs) & 1, timed_out, P.err);
             tc_fence_after();
-            mma_ss_hi_n(ks_n, g_tmem, p_tmem, dh, dl, xh, xl,
-                        sw128_desc(smem_u32(aslot + (2 * as) * kABytes)), idesc, kc > 0 ? 1u : 0u);
-            mma_ss_lo_n(ks_n, g_tmem, p_tmem, dh, xh,
-                        sw128_desc(smem_u32(aslot + (2 * as + 1) * kABytes)), idesc);
+            ss_run2_n(ks_n, d_tmem, o_h, o_l, sw128_desc(smem_u32(aslot + (2 * as) * kABytes)), idesc,
+                      kc > 0 ? 1u : 0u);
+            ss_run1_n(ks_n, d_tmem, o_h, sw128_desc(smem_u32(aslot + (2 * as + 1) * kABytes)), idesc);
             mma_commit(&tail->a_empty[as]);
             ++a_it;
             if (!resident) {
@@ -756,7 +756,7 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   p.wt = make_walker_tail(c, 0);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan->grid, 1, 1);
-  cfg.blockDim = dim3(kThreadsSk1, 1, 1);
+  cfg.blockDim = dim3(kThreadsSk, 1, 1);
   cfg.dynamicSmemBytes = kSmemSk;
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
