@@ -60,8 +60,8 @@ METRIC = "walker-steps/s"
 # commands are in profiles/); cold-cache per launch, as ncu replays it.  An
 # entry must be dropped when its kernel changes.
 PROFILED_TRAFFIC = {
-    ("rand100x2000", "recompute_ts_kernel"): 9.576e6 + 0.0,
-    ("illcond500x10000", "recompute_sk_kernel"): 199.351e6 + 88.730e6,
+    ("rand100x2000", "recompute_ts_kernel"): 9.575e6 + 0.0,
+    ("illcond500x10000", "recompute_sk_kernel"): 271.018e6 + 91.291e6,
 }
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
