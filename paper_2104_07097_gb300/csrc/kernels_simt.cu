@@ -84,87 +84,319 @@ __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint
   }
 }
 
-// ---- Section 3.2: d = P h with P = I - Q^T Q ------------------------------
+// ---- Section 3.2: d = P h with P = I - Q^T Q (FP64 mode) -------------------
 // One warp per walker.  Q (mE x n, orthonormal rows, Q = L^{-1} A_E): the
 // coefficients c = Q h in FP64 (warp reductions; every lane ends with the
 // sum), kept in shared memory (mE doubles per warp, dynamic), then
-// d_i = h_i - sum_e c_e q_ei in FP64, rounded once to the mode's type -- the
-// projection of the FP64 result, whatever mE is.
-// FP32 modes: the direction actually used (FP32, or the FP16 hi + lo pair of
-// the tensor-core mode) leaves a rounding residual A_E d of order 1e-7 |d|.
-// Its exact FP64 coordinates c' = Q d in the row space are stored per walker
-// (corr), and the point update moves along d - Q^T c', so A_E x = b_E holds
-// to FP64 rounding instead of drifting by theta * 1e-7 per iteration.
-template <typename T>
-__global__ void projection_kernel(int z, int n, int n_ld, int mE, const double* __restrict__ Q64,
-                                  const float* __restrict__ Q32,
-                                  T* D, int split, int k_pad, __half* Dh, __half* Dl,
-                                  float* corr, float* corrn, int z_ld, int inter,
-                                  const float* sigma, const uint64_t* step_ptr, int j,
-                                  __half* Dh1, __half* Dl1, int* status) {
-  if (Dh1 != nullptr && ((*step_ptr + static_cast<uint64_t>(j)) & 1ull)) {
-    Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
-    Dl = Dl1;
-  }
+// d_i = h_i - sum_e c_e q_ei in place.
+__global__ void projection_f64_kernel(int z, int n, int n_ld, int mE, const double* __restrict__ Q64,
+                                      double* D) {
   extern __shared__ double proj_c[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + warp;
   if (k >= z) return;
-  T* h = D + static_cast<size_t>(k) * n_ld;
+  double* h = D + static_cast<size_t>(k) * n_ld;
   double* c = proj_c + static_cast<size_t>(warp) * mE;
   for (int e = 0; e < mE; ++e) {
     const double* q = Q64 + static_cast<size_t>(e) * n_ld;
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc += q[i] * static_cast<double>(h[i]);
+    for (int i = lane; i < n; i += 32) acc += q[i] * h[i];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) c[e] = acc;
   }
   __syncwarp();
   for (int i = lane; i < n; i += 32) {
-    double v = static_cast<double>(h[i]);
+    double v = h[i];
     for (int e = 0; e < mE; ++e) v -= c[e] * Q64[static_cast<size_t>(e) * n_ld + i];
-    h[i] = static_cast<T>(v);
+    h[i] = v;
   }
-  if (split) {
-    for (int i = lane; i < n; i += 32) {
-      const float v = static_cast<float>(h[i]) / sigma[i];  // power of two: exact
-      const __half hh = __float2half_rn(v);
-      const size_t o = op_off(k, i, k_pad, z_ld, inter);
-      Dh[o] = hh;
-      Dl[o] = __float2half_rn(v - __half2float(hh));
-      if (!(fabsf(v) <= kHalfMax)) atomicOr(status, MHAR_ST_NONFINITE);
+}
+
+// ---- Section 3.2 in the FP32 and tensor-core modes -------------------------
+// The same projection in double-float arithmetic (unevaluated sums of two
+// FP32 numbers, about 2^-46 relative; mhar_device.cuh): the FP64 units of this
+// GPU run at a small fraction of the FP32 rate, and pairs of FP32 carry the
+// cancellation in h - Q^T Q h all the same.  Q = Qh + Ql, Qh = fl32(Q) and
+// Ql = fl32(Q - Qh).  One warp per walker; each lane takes quads of 4
+// consecutive coordinates (one Philox block of Section 4.3, one 16-byte load
+// of a row of Q).
+// d = h - Q^T c with c = Q h, rounded once to FP32: kept in D32 (FP32 mode) or
+// split into the FP16 operand pair d / sigma (tensor-core modes: split).
+// The direction actually used (FP32, or sigma (d_hi + d_lo)) leaves a
+// rounding residual A_E d of order 1e-7 |d|: its coordinates c' = Q d_used in
+// the row space are stored per walker (corr), and the point update moves
+// along d - Q^T c', so that A_E x = b_E does not drift by theta * 1e-7 per
+// iteration; ||Q^T c' / sigma||_2, rounded up (corrn), enters the chord's
+// error margins (walker_tail.cuh).
+// draw: h is the direction kernel's draw, made here (and made again in the
+// second pass rather than stored); otherwise h is read from D32 (the
+// preconditioned draw).
+constexpr int kProjRows = 4;   // rows of Q accumulated per pass over h
+
+// (s, r) += (ah + al) b
+__device__ __forceinline__ void ff_acc(float& s, float& r, float ah, float al, float b) {
+  const float p = ah * b;
+  const float pe = fmaf(al, b, fmaf(ah, b, -p));
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  r += err + pe;
+}
+// (s, r) -= (ch + cl)(qh + ql), the cl ql term dropped (2^-48 relative)
+__device__ __forceinline__ void ff_sub_prod(float& s, float& r, float ch, float cl, float qh,
+                                            float ql) {
+  const float p = ch * qh;
+  const float pe = fmaf(cl, qh, fmaf(ch, ql, fmaf(ch, qh, -p)));
+  float t, err;
+  two_sum(s, -p, t, err);
+  s = t;
+  r += err - pe;
+}
+// Sum over the warp.  Lanes may differ in the last bit of r (the order of
+// the low-part additions): the caller takes lane 0's.
+__device__ __forceinline__ void ff_warp_sum(float& s, float& r) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s, off);
+    const float orr = __shfl_xor_sync(0xffffffffu, r, off);
+    float t, err;
+    two_sum(s, os, t, err);
+    s = t;
+    r += orr + err;
+  }
+}
+__device__ __forceinline__ void draw_quad(uint64_t seed, uint64_t step, uint32_t walker, int q,
+                                          int n, float (&h)[4]) {
+  const U4 w = philox_block(seed, step, walker, static_cast<uint32_t>(q), kStreamDirection);
+  box_muller_f32(w.x, w.y, h[0], h[1]);
+  box_muller_f32(w.z, w.w, h[2], h[3]);
+  if (4 * q + 4 > n) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (4 * q + u >= n) h[u] = 0.0f;
+  }
+}
+// 1 / sigma for sigma = 2^e, -126 <= e <= 126 (every coordinate scale is a
+// power of two in that range, 1 past n; set_sigma checks it): the exponent
+// negated, exactly.
+__device__ __forceinline__ float pow2_recip(float sigma) {
+  return __int_as_float(0x7f000000 - __float_as_int(sigma));
+}
+__device__ __forceinline__ uint2 pack4h(const __half* h) {
+  return make_uint2(static_cast<uint32_t>(__half_as_ushort(h[0])) |
+                        (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16),
+                    static_cast<uint32_t>(__half_as_ushort(h[2])) |
+                        (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16));
+}
+
+__global__ void __launch_bounds__(kThreads)
+projection_ff_kernel(int draw, uint64_t seed, const uint64_t* step_ptr, int j, uint32_t walker0,
+                     int z, int n, int n_ld, int mE, const float* __restrict__ Qh,
+                     const float* __restrict__ Ql, float* D32, int split, int k_pad, int z_ld,
+                     int inter, const float* __restrict__ sigma, __half* Dh, __half* Dl,
+                     __half* Dh1, __half* Dl1, float* corr, float* corrn, int keep,
+                     int* status) {
+  extern __shared__ __align__(16) float proj_ff[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (k >= z) return;  // whole warps: k is the warp's
+  const uint64_t step = *step_ptr + static_cast<uint64_t>(j);
+  if (Dh1 != nullptr && (step & 1ull)) {
+    Dh = Dh1;  // recompute mode: iteration s's pair is s % 2
+    Dl = Dl1;
+  }
+  // keep: h is kept in shared memory (keep floats per warp, first) between
+  // the passes; otherwise it is drawn (or read) again.
+  float* hk = proj_ff + static_cast<size_t>(warp) * keep;
+  float* ch = proj_ff + static_cast<size_t>(blockDim.x >> 5) * keep +
+              static_cast<size_t>(warp) * 3 * mE;  // c (hi, lo), then c'
+  float* cl = ch + mE;
+  float* cp = cl + mE;
+  const int quads = (n + 3) >> 2;
+  float* Dk = D32 + static_cast<size_t>(k) * n_ld;
+  const uint32_t walker = walker0 + static_cast<uint32_t>(k);
+  auto normals = [&](int q, float (&h)[4]) {
+    if (draw) {
+      draw_quad(seed, step, walker, q, n, h);
+    } else {
+      const float4 v = *reinterpret_cast<const float4*>(Dk + 4 * q);
+      h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * q + u >= n) h[u] = 0.0f;
     }
-  }
-  if (corr == nullptr) return;
-  // Row-space coordinates of the rounded direction, in FP64.
-  float* ck = corr + static_cast<size_t>(k) * mE;
-  for (int e = 0; e < mE; ++e) {
-    double acc = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      double v;
-      if (split)
-        v = (static_cast<double>(__half2float(Dh[op_off(k, i, k_pad, z_ld, inter)])) +
-             static_cast<double>(__half2float(Dl[op_off(k, i, k_pad, z_ld, inter)]))) *
-            static_cast<double>(sigma[i]);
-      else
-        v = static_cast<double>(h[i]);
-      acc += Q64[static_cast<size_t>(e) * n_ld + i] * v;
+  };
+  auto qrow = [&](const float* Q, int e, int q) {
+    return __ldg(reinterpret_cast<const float4*>(Q + static_cast<size_t>(e) * n_ld + 4 * q));
+  };
+  // The direction actually used, read back (rows of c' past the first pass).
+  auto used = [&](int q, float (&du)[4]) {
+    const int i0 = 4 * q;
+    if (split) {
+      const size_t o = op_off(k, i0, k_pad, z_ld, inter);
+      const uint2 a = *reinterpret_cast<const uint2*>(Dh + o);
+      const uint2 b = *reinterpret_cast<const uint2*>(Dl + o);
+      const uint32_t aw[2] = {a.x, a.y}, bw[2] = {b.x, b.y};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float hh = __half2float(__ushort_as_half(static_cast<unsigned short>(aw[u >> 1] >> (16 * (u & 1)))));
+        const float ll = __half2float(__ushort_as_half(static_cast<unsigned short>(bw[u >> 1] >> (16 * (u & 1)))));
+        du[u] = i0 + u < n ? (hh + ll) * sigma[i0 + u] : 0.0f;
+      }
+    } else {
+      const float4 v = *reinterpret_cast<const float4*>(Dk + i0);
+      du[0] = v.x; du[1] = v.y; du[2] = v.z; du[3] = v.w;
+    }
+  };
+
+  // (1) c = Q h, kProjRows rows of Q per pass over h.
+  for (int e0 = 0; e0 < mE; e0 += kProjRows) {
+    float s[kProjRows], r[kProjRows];
+#pragma unroll
+    for (int u = 0; u < kProjRows; ++u) s[u] = r[u] = 0.0f;
+    for (int q = lane; q < quads; q += 32) {
+      float h[4];
+      if (keep && e0 > 0) {
+        const float4 v = *reinterpret_cast<const float4*>(hk + 4 * q);
+        h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+      } else {
+        normals(q, h);
+        if (keep) *reinterpret_cast<float4*>(hk + 4 * q) = make_float4(h[0], h[1], h[2], h[3]);
+      }
+#pragma unroll
+      for (int u = 0; u < kProjRows; ++u) {
+        if (e0 + u < mE) {
+          const float4 a = qrow(Qh, e0 + u, q), b = qrow(Ql, e0 + u, q);
+          ff_acc(s[u], r[u], a.x, b.x, h[0]);
+          ff_acc(s[u], r[u], a.y, b.y, h[1]);
+          ff_acc(s[u], r[u], a.z, b.z, h[2]);
+          ff_acc(s[u], r[u], a.w, b.w, h[3]);
+        }
+      }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) ck[e] = static_cast<float>(acc);
+    for (int u = 0; u < kProjRows; ++u) {
+      ff_warp_sum(s[u], r[u]);
+      if (lane == 0 && e0 + u < mE) fast_two_sum(s[u], r[u], ch[e0 + u], cl[e0 + u]);
+    }
   }
   __syncwarp();
-  // The point moves along d - Q^T c' (the update's FP32 arithmetic) while
-  // the chord is found along d: ||Q^T c' / sigma||_2, rounded up, enters
-  // the chord's error margins (tc_common.cuh, kernels_simt.cu).
+
+  // (2) d = h - Q^T c, rounded once; its FP16 pair or FP32 copy; c' of the
+  // first kProjRows rows on the way.
+  const bool want_corr = corr != nullptr;
+  float s2[kProjRows], r2[kProjRows];
+#pragma unroll
+  for (int u = 0; u < kProjRows; ++u) s2[u] = r2[u] = 0.0f;
+  for (int q = lane; q < quads; q += 32) {
+    const int i0 = 4 * q;
+    float ds[4], dr[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (keep) {  // each lane reads back the quads it stored
+      const float4 v = *reinterpret_cast<const float4*>(hk + i0);
+      ds[0] = v.x; ds[1] = v.y; ds[2] = v.z; ds[3] = v.w;
+    } else {
+      normals(q, ds);
+    }
+    for (int e = 0; e < mE; ++e) {
+      const float c_hi = ch[e], c_lo = cl[e];
+      const float4 a = qrow(Qh, e, q), b = qrow(Ql, e, q);
+      ff_sub_prod(ds[0], dr[0], c_hi, c_lo, a.x, b.x);
+      ff_sub_prod(ds[1], dr[1], c_hi, c_lo, a.y, b.y);
+      ff_sub_prod(ds[2], dr[2], c_hi, c_lo, a.z, b.z);
+      ff_sub_prod(ds[3], dr[3], c_hi, c_lo, a.w, b.w);
+    }
+    // Past n, h and the padded columns of Q are 0, and so is d: no
+    // per-coordinate test (sigma is 1 there).
+    float du[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) du[u] = ds[u] + dr[u];
+    if (split) {
+      __half hh[4], ll[4];
+      bool bad = false;
+      const float4 sg4 = __ldg(reinterpret_cast<const float4*>(sigma + i0));
+      const float sg[4] = {sg4.x, sg4.y, sg4.z, sg4.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = du[u] * pow2_recip(sg[u]);  // exact
+        hh[u] = __float2half_rn(v);
+        ll[u] = __float2half_rn(v - __half2float(hh[u]));
+        bad |= !(fabsf(v) <= kHalfMax);
+        // hi + lo is exact in FP32 (at most 24 significant bits), and so is
+        // the scaling by sigma.
+        du[u] = (__half2float(hh[u]) + __half2float(ll[u])) * sg[u];
+      }
+      const size_t o = op_off(k, i0, k_pad, z_ld, inter);
+      *reinterpret_cast<uint2*>(Dh + o) = pack4h(hh);
+      *reinterpret_cast<uint2*>(Dl + o) = pack4h(ll);
+      if (bad) atomicOr(status, MHAR_ST_NONFINITE);
+    } else {
+      *reinterpret_cast<float4*>(Dk + i0) = make_float4(du[0], du[1], du[2], du[3]);
+    }
+    if (want_corr) {
+#pragma unroll
+      for (int u = 0; u < kProjRows; ++u) {
+        if (u < mE) {
+          const float4 a = qrow(Qh, u, q), b = qrow(Ql, u, q);
+          ff_acc(s2[u], r2[u], a.x, b.x, du[0]);
+          ff_acc(s2[u], r2[u], a.y, b.y, du[1]);
+          ff_acc(s2[u], r2[u], a.z, b.z, du[2]);
+          ff_acc(s2[u], r2[u], a.w, b.w, du[3]);
+        }
+      }
+    }
+  }
+  if (!want_corr) return;
+  float* ck = corr + static_cast<size_t>(k) * mE;
+#pragma unroll
+  for (int u = 0; u < kProjRows; ++u) {
+    ff_warp_sum(s2[u], r2[u]);
+    if (lane == 0 && u < mE) ck[u] = cp[u] = s2[u] + r2[u];
+  }
+  // (3) c' of the remaining rows, from the stored direction (each lane reads
+  // back the quads it wrote).
+  for (int e0 = kProjRows; e0 < mE; e0 += kProjRows) {
+    float s[kProjRows], r[kProjRows];
+#pragma unroll
+    for (int u = 0; u < kProjRows; ++u) s[u] = r[u] = 0.0f;
+    for (int q = lane; q < quads; q += 32) {
+      float du[4];
+      used(q, du);
+#pragma unroll
+      for (int u = 0; u < kProjRows; ++u) {
+        if (e0 + u < mE) {
+          const float4 a = qrow(Qh, e0 + u, q), b = qrow(Ql, e0 + u, q);
+          ff_acc(s[u], r[u], a.x, b.x, du[0]);
+          ff_acc(s[u], r[u], a.y, b.y, du[1]);
+          ff_acc(s[u], r[u], a.z, b.z, du[2]);
+          ff_acc(s[u], r[u], a.w, b.w, du[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kProjRows; ++u) {
+      ff_warp_sum(s[u], r[u]);
+      if (lane == 0 && e0 + u < mE) ck[e0 + u] = cp[e0 + u] = s[u] + r[u];
+    }
+  }
+  __syncwarp();
+  // (4) ||Q^T c' / sigma||_2 in FP32, rounded up by 2^-10 (far above the
+  // FP32 rounding of these n mE products).
   float cn = 0.0f;
-  for (int i = lane; i < n; i += 32) {
-    float dlt = 0.0f;
-    for (int e = 0; e < mE; ++e) dlt = fmaf(Q32[static_cast<size_t>(e) * n_ld + i], ck[e], dlt);
-    const float v = dlt / sigma[i];
-    cn = fmaf(v, v, cn);
+  for (int q = lane; q < quads; q += 32) {
+    float dlt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int e = 0; e < mE; ++e) {
+      const float4 a = qrow(Qh, e, q);
+      const float ce = cp[e];
+      dlt[0] = fmaf(a.x, ce, dlt[0]);
+      dlt[1] = fmaf(a.y, ce, dlt[1]);
+      dlt[2] = fmaf(a.z, ce, dlt[2]);
+      dlt[3] = fmaf(a.w, ce, dlt[3]);
+    }
+    const float4 sg4 = __ldg(reinterpret_cast<const float4*>(sigma + 4 * q));
+    const float v0 = dlt[0] * pow2_recip(sg4.x), v1 = dlt[1] * pow2_recip(sg4.y);
+    const float v2 = dlt[2] * pow2_recip(sg4.z), v3 = dlt[3] * pow2_recip(sg4.w);
+    cn = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, fmaf(v3, v3, cn))));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, off);
@@ -1057,38 +1289,50 @@ cudaError_t launch_directions(mhar_ctx* c, int j) {
   return cudaGetLastError();
 }
 
-// Walkers (warps) per block of the projection: eight, fewer when their
-// coefficient vectors (mE doubles each) would pass 200 KB of shared memory.
+// Walkers (warps) per block of the projections: eight, fewer when their
+// shared coefficient vectors (mE doubles, or 3 mE floats, per walker) would
+// pass 150 KB (with the kept h below: 198 KB at most).
 int projection_warps(int mE) {
-  const int w = static_cast<int>((200u << 10) / (sizeof(double) * (mE > 0 ? mE : 1)));
+  const int w = static_cast<int>((150u << 10) / (3 * sizeof(float) * (mE > 0 ? mE : 1)));
   return w < 1 ? 1 : (w > kThreads / 32 ? kThreads / 32 : w);
 }
 
-cudaError_t projection_smem_attr(int mE) {
-  const int bytes = static_cast<int>(sizeof(double)) * projection_warps(mE) * mE;
-  cudaError_t e = cudaFuncSetAttribute(projection_kernel<double>,
+// Floats of h a walker keeps in shared memory between the passes of the
+// FP32 / tensor-core projection: all of it up to n = 1536 (6 KB a warp),
+// else none (drawn again).
+int projection_keep(int n) {
+  const int q = (n + 3) / 4;
+  return q <= 384 ? 4 * q : 0;
+}
+
+cudaError_t projection_smem_attr(int mE, int n) {
+  const int bytes = static_cast<int>(sizeof(float)) * projection_warps(mE) *
+                    (3 * mE + projection_keep(n));
+  cudaError_t e = cudaFuncSetAttribute(projection_f64_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(projection_kernel<float>,
+    e = cudaFuncSetAttribute(projection_ff_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
-cudaError_t launch_projection(mhar_ctx* c, int j) {
+cudaError_t launch_projection(mhar_ctx* c, int j, int draw) {
   const int warps = projection_warps(c->mE);
   const int grid = blocks_for(c->z, warps);
-  const size_t smem = sizeof(double) * static_cast<size_t>(warps) * c->mE;
   if (c->opts.precision == MHAR_FP64) {
-    projection_kernel<double><<<grid, warps * 32, smem, c->stream>>>(
-        c->z, c->n, c->n_ld, c->mE, c->d.Q64, c->d.Q32, c->d.D64, 0, 0, nullptr,
-        nullptr, nullptr, nullptr, 0, 0, nullptr, c->d.step, j, nullptr, nullptr, c->d.status);
+    const size_t smem = sizeof(double) * static_cast<size_t>(warps) * c->mE;
+    projection_f64_kernel<<<grid, warps * 32, smem, c->stream>>>(c->z, c->n, c->n_ld, c->mE,
+                                                                 c->d.Q64, c->d.D64);
   } else {
     const int split =
         (c->opts.precision == MHAR_MIXED_F16X3 || c->opts.precision == MHAR_MIXED_RECOMPUTE) ? 1 : 0;
-    projection_kernel<float><<<grid, warps * 32, smem, c->stream>>>(
-        c->z, c->n, c->n_ld, c->mE, c->d.Q64, c->d.Q32, c->d.D32, split, c->k_pad,
-        c->d.Dh, c->d.Dl, c->d.corr, c->d.corrn, (c->z + 127) / 128 * 128, c->use_ts ? 1 : 0,
-        c->d.sigma, c->d.step, j, c->d.Dh2, c->d.Dl2, c->d.status);
+    const int keep = projection_keep(c->n);
+    const size_t smem = sizeof(float) * static_cast<size_t>(warps) * (3 * c->mE + keep);
+    projection_ff_kernel<<<grid, warps * 32, smem, c->stream>>>(
+        draw, c->opts.seed, c->d.step, j, c->opts.walker0, c->z, c->n, c->n_ld, c->mE,
+        c->d.Q32, c->d.Q32lo, c->d.D32, split, c->k_pad, (c->z + 127) / 128 * 128,
+        c->use_ts ? 1 : 0, c->d.sigma, c->d.Dh, c->d.Dl, c->d.Dh2, c->d.Dl2, c->d.corr,
+        c->d.corrn, keep, c->d.status);
   }
   return cudaGetLastError();
 }

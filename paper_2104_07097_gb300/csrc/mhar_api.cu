@@ -92,7 +92,7 @@ bool recompute(const mhar_ctx* c) { return c->opts.precision == MHAR_MIXED_RECOM
 
 void free_all(mhar_ctx* c) {
   mhar::DeviceBuffers& d = c->d;
-  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.kr32, d.AE64, d.Q64, d.Q32, d.bE64,
+  void* ptrs[] = {d.A64, d.b64, d.A32, d.b32, d.kr32, d.AE64, d.Q64, d.Q32, d.Q32lo, d.bE64,
                   d.wE64, d.Lchol, d.Ah, d.Al, d.row_scale, d.bS, d.rows, d.rowk, d.nx_ref, d.theta_acc,
                   d.refresh_step, d.X64, d.Xhi, d.Xlo, d.D64, d.D32, d.Dh, d.Dl, d.S, d.corr, d.corrn, d.Xh, d.Xl, d.wscale, d.Dh2, d.Dl2,
                   d.key_lo, d.key_hi, d.lmin, d.lmax, d.theta, d.status, d.counters, d.step,
@@ -186,9 +186,14 @@ __global__ void trsm_kernel(int mE, int ncol, int ld, const double* L, double* M
   }
 }
 
-__global__ void to_f32_kernel(size_t count, const double* src, float* dst) {
+// hi = fl32(v), lo = fl32(v - hi).
+__global__ void to_f32_pair_kernel(size_t count, const double* src, float* hi, float* lo) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (i < count) dst[i] = static_cast<float>(src[i]);
+  if (i < count) {
+    const float h = static_cast<float>(src[i]);
+    hi[i] = h;
+    lo[i] = static_cast<float>(src[i] - static_cast<double>(h));
+  }
 }
 
 __global__ void broadcast_points_kernel(int mode, int z, int n, int n_ld, const double* x0,
@@ -214,9 +219,15 @@ bool tail_draws(const mhar_ctx* c) {
   return recompute(c) && c->mE == 0 && (c->pc_rank < 0 || c->use_ts);
 }
 
+// FP32 and tensor-core modes with equalities and no preconditioner: the
+// projection kernel draws the directions itself (one launch for both).
+bool projection_draws(const mhar_ctx* c) {
+  return c->mE > 0 && c->pc_rank < 0 && c->opts.precision != MHAR_FP64;
+}
+
 int kernels_per_iteration(const mhar_ctx* c) {
   if (tail_draws(c)) return 1;
-  return 1 + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) +
+  return (projection_draws(c) ? 0 : 1) + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) +
          ((mixed(c) || mhar::simt_warp_path(c)) ? 1 : 2);
 }
 
@@ -228,12 +239,15 @@ int emit_count(const mhar_ctx* c) {
 // launch first applies the previous iteration's moves and re-splits X.
 cudaError_t enqueue_directions(mhar_ctx* c, int j) {
   if (tail_draws(c)) return cudaSuccess;  // drawn by the previous chord kernel
-  cudaError_t e = recompute(c) ? mhar::launch_prep_walkers(c, j, 4) : mhar::launch_directions(c, j);
+  const bool fused = projection_draws(c);
+  cudaError_t e = cudaSuccess;
+  if (!fused)
+    e = recompute(c) ? mhar::launch_prep_walkers(c, j, 4) : mhar::launch_directions(c, j);
   // Preconditioned draw d = delta .* h + U g; the tensor-core modes split it
   // into the FP16 pair here unless the projection still has to run.
   if (e == cudaSuccess && c->pc_rank >= 0)
     e = mhar::launch_precondition(c, j, (mixed(c) && c->mE == 0) ? 1 : 0);
-  if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c, j);
+  if (e == cudaSuccess && c->mE > 0) e = mhar::launch_projection(c, j, fused ? 1 : 0);
   return e;
 }
 
@@ -401,6 +415,15 @@ int alloc_preconditioner(mhar_ctx* c) {
 }
 
 int set_sigma(mhar_ctx* c, const std::vector<float>& sig) {
+  for (float v : sig) {
+    // The FP32 / tensor-core projection takes 1 / sigma as the negated
+    // exponent (kernels_simt.cu, pow2_recip).
+    int e = 0;
+    if (!(std::frexp(v, &e) == 0.5f && e >= -125 && e <= 127)) {
+      set_err(c, "a coordinate scale outside the powers of two 2^-126 .. 2^126");
+      return MHAR_E_UNSUPPORTED;
+    }
+  }
   c->sigma_host = sig;
   if (!c->d.sigma) return MHAR_OK;
   c->unit_sigma = true;
@@ -815,7 +838,8 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       std::memcpy(&AEp[static_cast<size_t>(e) * c->n_ld], AE + static_cast<size_t>(e) * n,
                   sizeof(double) * n);
     if ((rc = dmalloc(c, &d.AE64, AEp.size())) || (rc = dmalloc(c, &d.Q64, AEp.size())) ||
-        (rc = dmalloc(c, &d.Q32, AEp.size())) || (rc = dmalloc(c, &d.bE64, mE)) ||
+        (rc = dmalloc(c, &d.Q32, AEp.size())) || (rc = dmalloc(c, &d.Q32lo, AEp.size())) ||
+        (rc = dmalloc(c, &d.bE64, mE)) ||
         (rc = dmalloc(c, &d.wE64, mE)) || (rc = dmalloc(c, &d.Lchol, static_cast<size_t>(mE) * mE)))
       return rc;
     MHAR_CUDA(cudaMemcpyAsync(d.AE64, AEp.data(), sizeof(double) * AEp.size(),
@@ -896,9 +920,10 @@ static int create_impl(mhar_ctx* c, const double* A, const double* b, const doub
       trsm_kernel<<<1, 32, 0, c->stream>>>(mE, 1, 1, d.Lchol, d.wE64);
       MHAR_CUDA(cudaGetLastError(), "projector solve kernel");
     }
-    to_f32_kernel<<<static_cast<unsigned>((qn + 255) / 256), 256, 0, c->stream>>>(qn, d.Q64, d.Q32);
+    to_f32_pair_kernel<<<static_cast<unsigned>((qn + 255) / 256), 256, 0, c->stream>>>(
+        qn, d.Q64, d.Q32, d.Q32lo);
     MHAR_CUDA(cudaGetLastError(), "projector conversion kernel");
-    MHAR_CUDA(mhar::projection_smem_attr(mE), "projection kernel attributes");
+    MHAR_CUDA(mhar::projection_smem_attr(mE, n), "projection kernel attributes");
   }
 
   // Algorithm 2: every column of X starts at x0.

@@ -26,6 +26,7 @@ struct DeviceBuffers {
   double* bE64 = nullptr;  // mE
   double* Q64 = nullptr;   // mE x n_ld, orthonormal rows: Q = L^{-1} A_E, P = I - Q^T Q
   float* Q32 = nullptr;    // mE x n_ld, Q in FP32
+  float* Q32lo = nullptr;  // mE x n_ld, fl32(Q - Q32): Q32 + Q32lo is Q to about 2^-48
   double* wE64 = nullptr;  // mE, w = L^{-1} b_E (Q x = w on the affine subspace)
   double* Lchol = nullptr; // mE x mE, set-up scratch: Cholesky factors of the Gram matrices
   // Tensor-core operands: A split into FP16 hi/lo after a per-row power-of-two
@@ -151,10 +152,12 @@ inline int mma_chain(const mhar_ctx* c) { return mma_per_step(c) * (c->kdim / kT
 // Every launcher enqueues on ctx->stream and returns cudaGetLastError().
 // `j` is the iteration offset added to the device counter *d.step.
 cudaError_t launch_directions(mhar_ctx* ctx, int j);
-cudaError_t launch_projection(mhar_ctx* ctx, int j);
+// draw: the FP32 / tensor-core projection draws h itself (no preconditioner);
+// otherwise it projects the direction kernels' D32 (D64 in FP64 mode).
+cudaError_t launch_projection(mhar_ctx* ctx, int j, int draw);
 // Opens the projection kernels' dynamic shared memory to mE coefficient
 // vectors per block (call once per context before the first launch).
-cudaError_t projection_smem_attr(int mE);
+cudaError_t projection_smem_attr(int mE, int n);
 cudaError_t launch_chord_simt(mhar_ctx* ctx);
 // Small bodies in the FP64 / FP32 modes: one warp per walker does the chord,
 // theta and the move (Sections 4.4-4.5) in a single launch.
