@@ -5,7 +5,8 @@ walkers the oracles compute one by one (walker0 offsets); and equality
 systems from 2 to 96 rows (random full-rank ones and transportation
 polytopes'), in FP64 against the pure oracle (1e-10) and in the FP32 and
 tensor-core modes against the reduced-precision oracle (1e-4); and the
-rejection of an A_E too ill-conditioned for the projector.
+rejection of an A_E too ill-conditioned for the projector; and a body past
+the length the projection keeps in shared memory (n = 1700).
 
 Section 3.2 (the projector, Lemma 3.1), Section 4.4 (line sets).
 """
@@ -43,6 +44,23 @@ def test_simplex1000_cuts4000_sampled_parity(prec):
             # coordinates are about 1/n: relative to the largest one, not to 1
             err = _rel(got[j, w0:w0 + cnt], want, np.abs(want).max())
             assert err <= 1e-4, (w0, j, err)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_rs"])
+def test_equalities_past_kept_length(prec):
+    """n = 1700, one equality: past the 1536 coordinates the projection keeps
+    in shared memory, so its second pass draws h again (Section 3.2, 4.3)."""
+    p = wl.simplex_cuts(1700, 600, seed=9)
+    z, steps = 64, 3
+    with mhar.Sampler(p.A, p.b, p.x0, z, AE=p.AE, bE=p.bE, precision=prec, seed=4) as s:
+        got = s.run(steps, thin=1)
+        st = s.check()
+    assert st.eq_residual <= 1e-8
+    ref = mixed.mixed_run(p.A, p.b, np.tile(p.x0, (z, 1)), steps, prec, seed=4, AE=p.AE)
+    for j in range(steps):
+        want = ref["samples"][j]
+        err = _rel(got[j], want, np.abs(want).max())
+        assert err <= 1e-4, (j, err)
 
 
 def test_illcond500_fitted_stream_k_sampled_parity():
