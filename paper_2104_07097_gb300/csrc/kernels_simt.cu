@@ -177,12 +177,6 @@ __device__ __forceinline__ void draw_quad(uint64_t seed, uint64_t step, uint32_t
       if (4 * q + u >= n) h[u] = 0.0f;
   }
 }
-// 1 / sigma for sigma = 2^e, -126 <= e <= 126 (every coordinate scale is a
-// power of two in that range, 1 past n; set_sigma checks it): the exponent
-// negated, exactly.
-__device__ __forceinline__ float pow2_recip(float sigma) {
-  return __int_as_float(0x7f000000 - __float_as_int(sigma));
-}
 __device__ __forceinline__ uint2 pack4h(const __half* h) {
   return make_uint2(static_cast<uint32_t>(__half_as_ushort(h[0])) |
                         (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16),

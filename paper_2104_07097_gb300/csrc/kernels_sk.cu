@@ -13,9 +13,14 @@
 // segment writes its partial chords (lambda_min, lambda_max of its rows) to
 // global memory and bumps the strip's counter, and the CTA that completes
 // the strip combines the partials (max / min, exact, so the result does not
-// depend on the cut), draws theta and does the walker-side work for the
-// whole strip.  Next iteration's directions are drawn early by the strip's
-// segments, each for its share of the walkers.
+// depend on the cut) and draws theta.  The walker-side work (the moves and
+// the FP16 pairs of the moved points, walker_tail.cuh) is a second launch,
+// walker_update_kernel, over all strips at once: done by the CTA that
+// completes a strip it held that CTA's tensor pipe for the whole of a
+// latency-bound loop over the strip's points (~0.2 ms for 128 walkers of
+// n = 1000, the memory system loaded by the other CTAs' operand streams),
+// on the critical path of the launch.  Next iteration's directions are
+// drawn early by the strip's segments, each for its share of the walkers.
 // The pipelines (TMA producer, two MMA issuers, 16 epilogue warps, double-buffered
 // accumulators) run across segment boundaries without re-initialisation.
 #include <cuda.h>
@@ -228,8 +233,6 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
     const int q = warp & 3;
     const int cg = e >> 2;
     const int wl = q * 32 + lane;
-    TailItem none;
-    none.valid = 0;
     int gt = 0;
     for (int sg = sb; sg < se; ++sg) {
       const SkSeg seg = p.segs[sg];
@@ -332,11 +335,9 @@ recompute_sk_kernel(const __grid_constant__ CUtensorMap tm_ah, const __grid_cons
             atomicAdd(&p.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
           }
         }
-        tail->theta_s[wl] = t;
       }
-      named_bar<kEpiWarps * 32>();
-      walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, 0, kWalkers, tail->theta_s, tail->red,
-                                  tid, none);
+      // The moves and the next operands of the strip's walkers follow in
+      // walker_update_kernel (one launch over all strips).
       named_bar<kEpiWarps * 32>();
     }
   }
@@ -649,6 +650,38 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
 
 }  // namespace
 
+// ---- the walker-side work of the stream-K kernel's iteration -----------------------
+// walker_tail.cuh's moves and splits, kUpdWalkers walkers per CTA (the same
+// arithmetic item for item as in the chord kernels that do it themselves, so
+// the schedules agree bit for bit); theta from the chord kernel.  Many small
+// CTAs on every SM keep many items' loads in flight.
+constexpr int kUpdWalkers = 8;
+constexpr int kUpdThreads = 256;
+static_assert(kWalkers % kUpdWalkers == 0, "update CTAs tile a walker strip");
+
+__global__ void __launch_bounds__(kUpdThreads)
+walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
+                     const uint64_t* step_ptr, int j, int z) {
+  __shared__ float theta_s[kWalkers];
+  __shared__ unsigned int red[kUpdWalkers];
+  // Programmatic dependent of the chord kernel: theta is read after it.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int kPerStrip = kWalkers / kUpdWalkers;
+  const int strip = blockIdx.x / kPerStrip;
+  const int w_begin = (blockIdx.x % kPerStrip) * kUpdWalkers;
+  const int cur = static_cast<int>((*step_ptr + static_cast<uint64_t>(j)) & 1ull);
+  if (threadIdx.x < kUpdWalkers) {
+    const int k = strip * kWalkers + w_begin + static_cast<int>(threadIdx.x);
+    theta_s[w_begin + threadIdx.x] = k < z ? static_cast<float>(theta[k]) : 0.0f;
+  }
+  __syncthreads();
+  TailItem none;
+  none.valid = 0;
+  walker_tail<kUpdThreads>(wt, cur, strip, z, w_begin, kUpdWalkers, theta_s, red,
+                           static_cast<int>(threadIdx.x), none);
+}
+
 // ---- host side -------------------------------------------------------------------
 struct SkPlan {
   SkSeg* segs = nullptr;
@@ -771,8 +804,19 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
     case 3: kernel = recompute_sk_kernel<3>; break;
     default: break;
   }
-  return cudaLaunchKernelEx(&cfg, kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2, tp->dl2, tp->xh,
-                            tp->xl, p, j);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, tp->ah, tp->al, tp->dh, tp->dl, tp->dh2,
+                                     tp->dl2, tp->xh, tp->xl, p, j);
+  if (e != cudaSuccess) return e;
+  // The walker-side work, a programmatic dependent of the chord kernel.
+  cudaLaunchConfig_t ucfg = {};
+  ucfg.gridDim = dim3(static_cast<unsigned>((c->z + kUpdWalkers - 1) / kUpdWalkers), 1, 1);
+  ucfg.blockDim = dim3(kUpdThreads, 1, 1);
+  ucfg.dynamicSmemBytes = 0;
+  ucfg.stream = c->stream;
+  ucfg.attrs = attr;
+  ucfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&ucfg, walker_update_kernel, p.wt, static_cast<const double*>(p.theta),
+                            static_cast<const uint64_t*>(p.step_ptr), j, p.z);
 }
 
 // ---- batched persistent launch: host side ---------------------------------------

@@ -225,10 +225,18 @@ bool projection_draws(const mhar_ctx* c) {
   return c->mE > 0 && c->pc_rank < 0 && c->opts.precision != MHAR_FP64;
 }
 
+// Launches of one iteration's chord step (enqueue_chord): the stream-K chord
+// kernel is followed by its walker update kernel, the FP32 / FP64 chord by
+// the update kernel unless one warp per walker does both.
+int chord_launches(const mhar_ctx* c) {
+  if (recompute(c)) return (!c->use_ts && c->use_sk) ? 2 : 1;
+  return (mixed(c) || mhar::simt_warp_path(c)) ? 1 : 2;
+}
+
 int kernels_per_iteration(const mhar_ctx* c) {
-  if (tail_draws(c)) return 1;
-  return (projection_draws(c) ? 0 : 1) + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) +
-         ((mixed(c) || mhar::simt_warp_path(c)) ? 1 : 2);
+  const int chord = chord_launches(c);
+  if (tail_draws(c)) return chord;
+  return (projection_draws(c) ? 0 : 1) + (c->mE > 0 ? 1 : 0) + (c->pc_rank >= 0 ? 1 : 0) + chord;
 }
 
 int emit_count(const mhar_ctx* c) {
@@ -417,7 +425,7 @@ int alloc_preconditioner(mhar_ctx* c) {
 int set_sigma(mhar_ctx* c, const std::vector<float>& sig) {
   for (float v : sig) {
     // The FP32 / tensor-core projection takes 1 / sigma as the negated
-    // exponent (kernels_simt.cu, pow2_recip).
+    // exponent (mhar_device.cuh, pow2_recip).
     int e = 0;
     if (!(std::frexp(v, &e) == 0.5f && e >= -125 && e <= 127)) {
       set_err(c, "a coordinate scale outside the powers of two 2^-126 .. 2^126");
@@ -1341,7 +1349,7 @@ int mhar_time_kernels(mhar_ctx* c, int iters, double* ms) {
   if (!tail_draws(c)) {  // otherwise the draw is part of the chord kernel
     e = time_graph(c, dirs, &t_dir);
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel timing");
-    c->launches += static_cast<int64_t>(iters) * (kernels_per_iteration(c) - 1);
+    c->launches += static_cast<int64_t>(iters) * (kernels_per_iteration(c) - chord_launches(c));
   }
   if (stored(c)) {
     auto ref = [&]() -> cudaError_t {

@@ -104,6 +104,14 @@ __device__ __forceinline__ double f64_unkey(unsigned long long k) {
   return __longlong_as_double(static_cast<long long>(u));
 }
 
+// 1 / sigma for a coordinate scale sigma = 2^e, -126 <= e <= 126 (every
+// scale is a power of two in that range, 1 past n; set_sigma checks it): the
+// exponent negated, exactly, so x * pow2_recip(sigma) has the bits of
+// x / sigma.
+__device__ __forceinline__ float pow2_recip(float sigma) {
+  return __int_as_float(0x7f000000 - __float_as_int(sigma));
+}
+
 // ---- double-float (pairs of FP32) arithmetic --------------------------------
 // Knuth's TwoSum and Dekker's FastTwoSum; TwoProd via FMA.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
