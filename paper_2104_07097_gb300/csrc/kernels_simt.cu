@@ -68,7 +68,7 @@ __global__ void directions_kernel(int mode, int split, uint64_t seed, const uint
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (i0 + e < n) {
-          const float vs = v[e] * (1.0f / sigma[i0 + e]);   // d_i / sigma_i, exact
+          const float vs = v[e] * pow2_recip(sigma[i0 + e]);   // d_i / sigma_i, exact
           const __half h = __float2half_rn(vs);
           const __half l = __float2half_rn(vs - __half2float(h));
           Dh[static_cast<size_t>(k) * k_pad + i0 + e] = h;
@@ -745,7 +745,7 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
         ld8(Xhi + xr + 8 * c, hi);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          if (8 * c + e < n) mx = fmaxf(mx, fabsf(hi[e]) / sigma[8 * c + e]);
+          if (8 * c + e < n) mx = fmaxf(mx, fabsf(hi[e]) * pow2_recip(sigma[8 * c + e]));
       }
     red[warp][lane] = mx;
     __syncthreads();
@@ -765,7 +765,7 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int i = i0 + e;
-          const float v = i < n ? (hi[e] + lo[e]) * inv / sigma[i] : 0.0f;
+          const float v = i < n ? (hi[e] + lo[e]) * inv * pow2_recip(sigma[i]) : 0.0f;
           h8[e] = __float2half_rn(v);
           l8[e] = __float2half_rn(v - __half2float(h8[e]));
           bad |= !(fabsf(v) <= kHalfMax);
@@ -800,7 +800,7 @@ prep_walkers_kernel(int flags, uint64_t seed, const uint64_t* step_ptr, int j, u
         __half h8[8], l8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float vs = v[e] * (1.0f / sigma[i0 + e]);   // d_i / sigma_i, exact
+          const float vs = v[e] * pow2_recip(sigma[i0 + e]);   // d_i / sigma_i, exact
           h8[e] = __float2half_rn(vs);
           l8[e] = __float2half_rn(vs - __half2float(h8[e]));
         }

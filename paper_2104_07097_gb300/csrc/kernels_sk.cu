@@ -651,20 +651,161 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
 }  // namespace
 
 // ---- the walker-side work of the stream-K kernel's iteration -----------------------
-// walker_tail.cuh's moves and splits, kUpdWalkers walkers per CTA (the same
-// arithmetic item for item as in the chord kernels that do it themselves, so
-// the schedules agree bit for bit); theta from the chord kernel.  Many small
-// CTAs on every SM keep many items' loads in flight.
-constexpr int kUpdWalkers = 8;
+// Every item -- a walker's 8-coordinate chunk -- takes the arithmetic of
+// walker_tail.cuh, so that the stream-K schedule agrees bit for bit with the
+// kernels that do the walker-side work themselves: (1) the move
+// x += theta (d - Q^T c') in double-float and the walker's largest scaled
+// coordinate, (2) the FP16 pair of the scaled point.
+// walker_update_kernel: a CTA takes W consecutive walkers; one thread brings
+// their rows (x hi, x lo: n_ld floats each; the direction pair: k_pad halves
+// each) into shared memory with bulk copies behind one mbarrier, so that all
+// of a CTA's loads are in flight at once; the moved rows and the pair are
+// stored from shared memory with coalesced stores (a warp on consecutive
+// chunks of one walker).
+// walker_update_direct_kernel: rows too long to stage; walker_tail itself,
+// kUpdWalkers walkers a CTA.
 constexpr int kUpdThreads = 256;
+constexpr int kUpdMaxW = 8;
+constexpr int kUpdWalkers = 8;
 static_assert(kWalkers % kUpdWalkers == 0, "update CTAs tile a walker strip");
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 __global__ void __launch_bounds__(kUpdThreads)
 walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
-                     const uint64_t* step_ptr, int j, int z) {
+                     const uint64_t* step_ptr, int j, int z, int W, int* err) {
+  using namespace tail_detail;
+  extern __shared__ __align__(128) uint8_t upd_smem[];
+  __shared__ uint64_t bar;
+  __shared__ float theta_s[kUpdMaxW];
+  __shared__ unsigned int red[kUpdMaxW];
+  __shared__ int timed_out;
+  const int n = wt.n, n_ld = wt.n_ld, k_pad = wt.k_pad;
+  float* xs = reinterpret_cast<float*>(upd_smem);                       // [W][hi, lo][n_ld]
+  __half* ds = reinterpret_cast<__half*>(xs + static_cast<size_t>(2 * W) * n_ld);  // [W][hi, lo][k_pad]
+  const int k0 = blockIdx.x * W;
+  const int wn = min(W, z - k0);
+  const int tid = static_cast<int>(threadIdx.x);
+  // Programmatic dependent of the chord kernel: theta and the points are
+  // read after it.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int cur = static_cast<int>((*step_ptr + static_cast<uint64_t>(j)) & 1ull);
+  if (tid == 0) {
+    timed_out = 0;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < wn) {
+    theta_s[tid] = static_cast<float>(theta[k0 + tid]);
+    red[tid] = 0u;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t xb = static_cast<uint32_t>(n_ld) * 4u, db = static_cast<uint32_t>(k_pad) * 2u;
+    mbar_expect_tx(&bar, static_cast<uint32_t>(wn) * 2u * (xb + db));
+    for (int w = 0; w < wn; ++w) {
+      const size_t k = static_cast<size_t>(k0 + w);
+      bulk_g2s(xs + static_cast<size_t>(2 * w) * n_ld, wt.Xhi + k * n_ld, xb, &bar);
+      bulk_g2s(xs + static_cast<size_t>(2 * w + 1) * n_ld, wt.Xlo + k * n_ld, xb, &bar);
+      bulk_g2s(ds + static_cast<size_t>(2 * w) * k_pad, wt.Dh[cur] + k * k_pad, db, &bar);
+      bulk_g2s(ds + static_cast<size_t>(2 * w + 1) * k_pad, wt.Dl[cur] + k * k_pad, db, &bar);
+    }
+  }
+  if (!mbar_wait(&bar, 0, &timed_out, err, true)) {
+    // The copies are still landing in this CTA's shared memory: wait for
+    // them once more (bounded) before leaving.
+    timed_out = 0;
+    mbar_wait(&bar, 0, &timed_out, err, true);
+    return;
+  }
+  const int chunks = (n + 7) >> 3;
+  const int items = wn * chunks;
+  // (1) the moves, in shared memory, and each walker's largest scaled coordinate.
+  for (int it = tid; it < items; it += kUpdThreads) {
+    const int wo = it / chunks, c = it - wo * chunks;
+    const int k = k0 + wo, i0 = 8 * c;
+    float* xh = xs + static_cast<size_t>(2 * wo) * n_ld + i0;
+    float* xl = xh + n_ld;
+    const float th = theta_s[wo];
+    float hi[8], lo[8];
+    ld8(xh, hi);
+    ld8(xl, lo);
+    if (th != 0.0f) {
+      float dh[8], dl[8], d[8];
+      ld8h(ds + static_cast<size_t>(2 * wo) * k_pad + i0, dh);
+      ld8h(ds + static_cast<size_t>(2 * wo + 1) * k_pad + i0, dl);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        d[e] = i0 + e < n ? (wt.unit_sigma ? dh[e] + dl[e] : (dh[e] + dl[e]) * wt.sigma[i0 + e]) : 0.0f;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) df_axpy(hi[e], lo[e], th, d[e]);
+      if (wt.corr != nullptr) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int i = i0 + e;
+          if (i >= n) continue;
+          float dlt = 0.0f;
+          for (int q = 0; q < wt.mE; ++q)
+            dlt = fmaf(wt.Q32[static_cast<size_t>(q) * n_ld + i],
+                       wt.corr[static_cast<size_t>(k) * wt.mE + q], dlt);
+          lo[e] = fmaf(-th, dlt, lo[e]);
+        }
+      }
+      st8(xh, hi);
+      st8(xl, lo);
+    }
+    float mx = 0.0f;
+    if (wt.unit_sigma) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(hi[e]));   // x = 0 past n
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (i0 + e < n) mx = fmaxf(mx, fabsf(hi[e]) * pow2_recip(wt.sigma[i0 + e]));
+    }
+    atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
+  }
+  __syncthreads();
+  // (2) the moved rows back, and the FP16 pair of the scaled point.
+  for (int it = tid; it < items; it += kUpdThreads) {
+    const int wo = it / chunks, c = it - wo * chunks;
+    const int k = k0 + wo, i0 = 8 * c;
+    const float* xh = xs + static_cast<size_t>(2 * wo) * n_ld + i0;
+    float hi[8], lo[8], v[8];
+    ld8(xh, hi);
+    ld8(xh + n_ld, lo);
+    const size_t xr = static_cast<size_t>(k) * n_ld + i0;
+    st8(wt.Xhi + xr, hi);
+    st8(wt.Xlo + xr, lo);
+    const float mx = __uint_as_float(red[wo]);
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
+    const float inv = ldexpf(1.0f, -ex);
+    if (c == 0) wt.wscale[k] = ldexpf(1.0f, ex);
+    if (wt.unit_sigma) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv * pow2_recip(wt.sigma[i0 + e]);
+    }
+    const size_t o = static_cast<size_t>(k) * k_pad + i0;   // row-major operands
+    if (split_store8(v, wt.Xh + o, wt.Xl + o)) atomicOr(wt.status, MHAR_ST_NONFINITE);
+  }
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+walker_update_direct_kernel(const WalkerTail wt, const double* __restrict__ theta,
+                            const uint64_t* step_ptr, int j, int z) {
   __shared__ float theta_s[kWalkers];
   __shared__ unsigned int red[kUpdWalkers];
-  // Programmatic dependent of the chord kernel: theta is read after it.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   constexpr int kPerStrip = kWalkers / kUpdWalkers;
@@ -682,6 +823,18 @@ walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
                            static_cast<int>(threadIdx.x), none);
 }
 
+// Walkers a walker_update_kernel CTA stages (0: the rows do not fit; the
+// direct kernel runs), and its dynamic shared memory.
+int update_walkers(int n_ld, int k_pad, size_t* smem) {
+  const size_t per = 8ull * n_ld + 4ull * k_pad;
+  const size_t budget = 48u << 10;
+  int w = static_cast<int>(budget / per);
+  if (w < 1) w = per <= (200u << 10) ? 1 : 0;
+  if (w > kUpdMaxW) w = kUpdMaxW;
+  *smem = static_cast<size_t>(w) * per;
+  return w;
+}
+
 // ---- host side -------------------------------------------------------------------
 struct SkPlan {
   SkSeg* segs = nullptr;
@@ -690,6 +843,8 @@ struct SkPlan {
   int* arrivals = nullptr;
   int grid = 0;
   int max_nseg = 1;
+  int upd_w = 0;          // walkers per walker_update_kernel CTA (0: direct kernel)
+  size_t upd_smem = 0;
 };
 
 int sk_prepare(mhar_ctx* c) {
@@ -742,6 +897,10 @@ int sk_prepare(mhar_ctx* c) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kSmemSk));
+  plan->upd_w = update_walkers(c->n_ld, c->k_pad, &plan->upd_smem);
+  if (e == cudaSuccess && plan->upd_w > 0)
+    e = cudaFuncSetAttribute(walker_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(plan->upd_smem));
   c->sk = plan;
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "stream-K schedule: %s", cudaGetErrorString(e));
@@ -809,13 +968,21 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   if (e != cudaSuccess) return e;
   // The walker-side work, a programmatic dependent of the chord kernel.
   cudaLaunchConfig_t ucfg = {};
-  ucfg.gridDim = dim3(static_cast<unsigned>((c->z + kUpdWalkers - 1) / kUpdWalkers), 1, 1);
   ucfg.blockDim = dim3(kUpdThreads, 1, 1);
-  ucfg.dynamicSmemBytes = 0;
   ucfg.stream = c->stream;
   ucfg.attrs = attr;
   ucfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&ucfg, walker_update_kernel, p.wt, static_cast<const double*>(p.theta),
+  if (plan->upd_w > 0) {
+    ucfg.gridDim = dim3(static_cast<unsigned>((c->z + plan->upd_w - 1) / plan->upd_w), 1, 1);
+    ucfg.dynamicSmemBytes = plan->upd_smem;
+    return cudaLaunchKernelEx(&ucfg, walker_update_kernel, p.wt,
+                              static_cast<const double*>(p.theta),
+                              static_cast<const uint64_t*>(p.step_ptr), j, p.z, plan->upd_w, p.err);
+  }
+  ucfg.gridDim = dim3(static_cast<unsigned>((c->z + kUpdWalkers - 1) / kUpdWalkers), 1, 1);
+  ucfg.dynamicSmemBytes = 0;
+  return cudaLaunchKernelEx(&ucfg, walker_update_direct_kernel, p.wt,
+                            static_cast<const double*>(p.theta),
                             static_cast<const uint64_t*>(p.step_ptr), j, p.z);
 }
 

@@ -324,7 +324,7 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
     if (!pre && !t.unit_sigma) {
       // The FP16 pair holds d_i / sigma_i (sigma a power of two: exact).
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] *= 1.0f / t.sigma[i0 + e];
+      for (int e = 0; e < 8; ++e) v[e] *= pow2_recip(t.sigma[i0 + e]);
     }
     if (pre) {
       const float* g = gs + wo * kMaxPcRank;
@@ -336,7 +336,7 @@ __device__ void walker_draw_next(const WalkerTail& t, int cur, uint64_t seed, ui
         float acc = t.pc_delta[i] * v[e];
 #pragma unroll 8
         for (int c2 = 0; c2 < kMaxPcRank; ++c2) acc = fmaf(u[c2], g[c2], acc);
-        v[e] = acc * (1.0f / t.sigma[i]);
+        v[e] = acc * pow2_recip(t.sigma[i]);
       }
     }
     if (split_store8(v, Dh + o, Dl + o)) atomicOr(t.status, MHAR_ST_NONFINITE);
@@ -432,7 +432,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
     } else {
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]) / t.sigma[i0 + e]);
+        if (i0 + e < t.n) mx = fmaxf(mx, fabsf(hi[e]) * pow2_recip(t.sigma[i0 + e]));
     }
     atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
   }
@@ -479,7 +479,7 @@ __device__ void walker_tail(const WalkerTail& t, int cur, int strip, int z, int 
       for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv;
     } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv / t.sigma[i0 + e];
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv * pow2_recip(t.sigma[i0 + e]);
     }
     if (split_store8(v, t.Xh + o, t.Xl + o)) atomicOr(t.status, MHAR_ST_NONFINITE);
   }
