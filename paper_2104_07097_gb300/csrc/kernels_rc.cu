@@ -81,6 +81,7 @@ struct RcParams {
   int j;
   uint32_t walker0;
   int z, kdim, k_chunks, k_pad, tiles_per_cta, m_tiles;
+  int ext_tail;             // 1: the walker-side work is a separate launch (batches)
   WalkerTail wt;            // walker-side work (walker_tail.cuh)
 };
 
@@ -337,7 +338,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
   // (the loads do not depend on theta), so their latency overlaps the barrier.
   tc_fence_before();
   cluster_arrive();
-  if (warp >= 2 && warp < kPWarp)
+  if (warp >= 2 && warp < kPWarp && !p.ext_tail)
     walker_tail_prefetch<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count,
                                          static_cast<int>(threadIdx.x) - 64, tail_item);
   cluster_wait();
@@ -383,7 +384,7 @@ __device__ __forceinline__ void rc_body(const RcMaps& mp, const RcParams& p, int
       }
     }
   }
-  if (warp >= 2 && warp < kPWarp) {
+  if (warp >= 2 && warp < kPWarp && !p.ext_tail) {
     named_bar<kEpiWarps * 32>();
     walker_tail<kEpiWarps * 32>(p.wt, cur, strip, p.z, w_begin, w_count, tail->theta_s,
                                 tail->red, static_cast<int>(threadIdx.x) - 64, tail_item);
@@ -485,6 +486,7 @@ RcParams rc_params(const mhar_ctx* c, int j, int tiles_per_cta) {
   p.rows = c->d.rows;
   p.Xh = c->d.Xh;
   p.k_pad = c->k_pad;
+  p.ext_tail = 0;
   p.wscale = c->d.wscale;
   p.lmin = c->d.lmin;
   p.lmax = c->d.lmax;
@@ -576,6 +578,7 @@ int batch_table_build(mhar_ctx* const* ctx, int count, int C, void** table, int*
       std::memset(&u, 0, sizeof(u));
       u.maps = rc_maps(plan);
       u.p = rc_params(c, 0, tpc);
+      u.p.ext_tail = 1;   // walker_update_batch_kernel follows
       u.strip = st;
       host.push_back(u);
     }

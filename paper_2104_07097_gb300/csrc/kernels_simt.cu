@@ -1299,9 +1299,13 @@ int projection_keep(int n) {
   return q <= 384 ? 4 * q : 0;
 }
 
+// The limit is a per-function attribute shared by every context, so it is
+// set to the most any context uses (198 KB: 150 KB of coefficients and 48 KB
+// of kept h), not to this context's need.
 cudaError_t projection_smem_attr(int mE, int n) {
-  const int bytes = static_cast<int>(sizeof(float)) * projection_warps(mE) *
-                    (3 * mE + projection_keep(n));
+  (void)mE;
+  (void)n;
+  const int bytes = 200 << 10;
   cudaError_t e = cudaFuncSetAttribute(projection_f64_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)

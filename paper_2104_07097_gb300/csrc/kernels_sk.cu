@@ -556,8 +556,6 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
     const int q = warp & 3;
     const int cg = e >> 2;
     const int wl = q * 32 + lane;
-    TailItem none;
-    none.valid = 0;
     int gt = 0;
     for (int r = 0;; ++r) {
       const int rs = r % kRing;
@@ -630,11 +628,8 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
             atomicAdd(&P.counters[flag == MHAR_ST_STALL ? 0 : 1], 1ull);
           }
         }
-        tail->theta_s[wl] = t;
       }
-      named_bar<kEpiWarps * 32>();
-      walker_tail<kEpiWarps * 32>(P.wt, cur, strip, P.z, 0, kWalkers, tail->theta_s, tail->red,
-                                  tid, none);
+      // The moves follow in walker_update_batch_kernel.
       named_bar<kEpiWarps * 32>();
     }
   }
@@ -677,9 +672,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-__global__ void __launch_bounds__(kUpdThreads)
-walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
-                     const uint64_t* step_ptr, int j, int z, int W, int* err) {
+// Walkers k0 .. k0 + W - 1 staged in shared memory (W >= 1).
+__device__ __forceinline__ void update_staged(const WalkerTail& wt, const double* __restrict__ theta,
+                                              const uint64_t* step_ptr, int j, int z, int k0,
+                                              int W, int* err) {
   using namespace tail_detail;
   extern __shared__ __align__(128) uint8_t upd_smem[];
   __shared__ uint64_t bar;
@@ -689,13 +685,8 @@ walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
   const int n = wt.n, n_ld = wt.n_ld, k_pad = wt.k_pad;
   float* xs = reinterpret_cast<float*>(upd_smem);                       // [W][hi, lo][n_ld]
   __half* ds = reinterpret_cast<__half*>(xs + static_cast<size_t>(2 * W) * n_ld);  // [W][hi, lo][k_pad]
-  const int k0 = blockIdx.x * W;
   const int wn = min(W, z - k0);
   const int tid = static_cast<int>(threadIdx.x);
-  // Programmatic dependent of the chord kernel: theta and the points are
-  // read after it.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int cur = static_cast<int>((*step_ptr + static_cast<uint64_t>(j)) & 1ull);
   if (tid == 0) {
     timed_out = 0;
@@ -801,35 +792,75 @@ walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
   }
 }
 
-__global__ void __launch_bounds__(kUpdThreads)
-walker_update_direct_kernel(const WalkerTail wt, const double* __restrict__ theta,
-                            const uint64_t* step_ptr, int j, int z) {
-  __shared__ float theta_s[kWalkers];
-  __shared__ unsigned int red[kUpdWalkers];
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  constexpr int kPerStrip = kWalkers / kUpdWalkers;
-  const int strip = blockIdx.x / kPerStrip;
-  const int w_begin = (blockIdx.x % kPerStrip) * kUpdWalkers;
+// Walkers k0 .. k0 + kUpdWalkers - 1 (k0 a multiple of kUpdWalkers) by
+// walker_tail itself, for rows too long to stage.
+__device__ __forceinline__ void update_direct(const WalkerTail& wt, const double* __restrict__ theta,
+                                              const uint64_t* step_ptr, int j, int z, int k0) {
+  __shared__ float theta_d[kWalkers];
+  __shared__ unsigned int red_d[kUpdWalkers];
+  const int strip = k0 / kWalkers, w_begin = k0 % kWalkers;
   const int cur = static_cast<int>((*step_ptr + static_cast<uint64_t>(j)) & 1ull);
   if (threadIdx.x < kUpdWalkers) {
-    const int k = strip * kWalkers + w_begin + static_cast<int>(threadIdx.x);
-    theta_s[w_begin + threadIdx.x] = k < z ? static_cast<float>(theta[k]) : 0.0f;
+    const int k = k0 + static_cast<int>(threadIdx.x);
+    theta_d[w_begin + threadIdx.x] = k < z ? static_cast<float>(theta[k]) : 0.0f;
   }
   __syncthreads();
   TailItem none;
   none.valid = 0;
-  walker_tail<kUpdThreads>(wt, cur, strip, z, w_begin, kUpdWalkers, theta_s, red,
+  walker_tail<kUpdThreads>(wt, cur, strip, z, w_begin, kUpdWalkers, theta_d, red_d,
                            static_cast<int>(threadIdx.x), none);
+}
+
+// One context: W walkers a CTA (W = 0: the direct form, kUpdWalkers a CTA).
+__global__ void __launch_bounds__(kUpdThreads)
+walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
+                     const uint64_t* step_ptr, int j, int z, int W, int* err) {
+  // Programmatic dependent of the chord kernel: theta and the points are
+  // read after it.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (W > 0)
+    update_staged(wt, theta, step_ptr, j, z, static_cast<int>(blockIdx.x) * W, W, err);
+  else
+    update_direct(wt, theta, step_ptr, j, z, static_cast<int>(blockIdx.x) * kUpdWalkers);
+}
+
+// Many contexts (a batch): a table of (problem, first walker, W) units.
+struct UpdProblem {
+  WalkerTail wt;
+  const double* theta;
+  const uint64_t* step_ptr;
+  int* err;
+  int z;
+};
+struct UpdUnit {
+  int prob, k0, w;
+};
+
+__global__ void __launch_bounds__(kUpdThreads)
+walker_update_batch_kernel(const UpdProblem* __restrict__ probs, const UpdUnit* __restrict__ units,
+                           int j) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const UpdUnit u = units[blockIdx.x];
+  const UpdProblem& P = probs[u.prob];
+  if (u.w > 0)
+    update_staged(P.wt, P.theta, P.step_ptr, j, P.z, u.k0, u.w, P.err);
+  else
+    update_direct(P.wt, P.theta, P.step_ptr, j, P.z, u.k0);
 }
 
 // Walkers a walker_update_kernel CTA stages (0: the rows do not fit; the
 // direct kernel runs), and its dynamic shared memory.
+// The kernels' dynamic shared memory limit is set once to the largest any
+// context asks for (kUpdSmemMax): it is a per-function attribute, and
+// contexts of different sizes launch the same function.
+constexpr int kUpdSmemMax = 200 << 10;
 int update_walkers(int n_ld, int k_pad, size_t* smem) {
   const size_t per = 8ull * n_ld + 4ull * k_pad;
   const size_t budget = 48u << 10;
   int w = static_cast<int>(budget / per);
-  if (w < 1) w = per <= (200u << 10) ? 1 : 0;
+  if (w < 1) w = per <= static_cast<size_t>(kUpdSmemMax) ? 1 : 0;
   if (w > kUpdMaxW) w = kUpdMaxW;
   *smem = static_cast<size_t>(w) * per;
   return w;
@@ -898,9 +929,9 @@ int sk_prepare(mhar_ctx* c) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kSmemSk));
   plan->upd_w = update_walkers(c->n_ld, c->k_pad, &plan->upd_smem);
-  if (e == cudaSuccess && plan->upd_w > 0)
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(walker_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(plan->upd_smem));
+                             kUpdSmemMax);
   c->sk = plan;
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "stream-K schedule: %s", cudaGetErrorString(e));
@@ -972,18 +1003,86 @@ cudaError_t launch_recompute_sk(mhar_ctx* c, int j) {
   ucfg.stream = c->stream;
   ucfg.attrs = attr;
   ucfg.numAttrs = 1;
-  if (plan->upd_w > 0) {
-    ucfg.gridDim = dim3(static_cast<unsigned>((c->z + plan->upd_w - 1) / plan->upd_w), 1, 1);
-    ucfg.dynamicSmemBytes = plan->upd_smem;
-    return cudaLaunchKernelEx(&ucfg, walker_update_kernel, p.wt,
-                              static_cast<const double*>(p.theta),
-                              static_cast<const uint64_t*>(p.step_ptr), j, p.z, plan->upd_w, p.err);
+  const int per = plan->upd_w > 0 ? plan->upd_w : kUpdWalkers;
+  ucfg.gridDim = dim3(static_cast<unsigned>((c->z + per - 1) / per), 1, 1);
+  ucfg.dynamicSmemBytes = plan->upd_smem;
+  return cudaLaunchKernelEx(&ucfg, walker_update_kernel, p.wt, static_cast<const double*>(p.theta),
+                            static_cast<const uint64_t*>(p.step_ptr), j, p.z, plan->upd_w, p.err);
+}
+
+// ---- the batched walker update: host side -----------------------------------------
+struct UpdPlan {
+  UpdProblem* probs = nullptr;
+  UpdUnit* units = nullptr;
+  int n_units = 0;
+  size_t smem = 0;
+};
+
+int update_plan_build(mhar_ctx* const* ctx, int count, void** plan_out, char* err, size_t err_len) {
+  *plan_out = nullptr;
+  std::vector<UpdProblem> probs(count);
+  std::vector<UpdUnit> units;
+  size_t smem = 0;
+  for (int q = 0; q < count; ++q) {
+    mhar_ctx* c = ctx[q];
+    UpdProblem& P = probs[q];
+    std::memset(&P, 0, sizeof(P));
+    P.wt = make_walker_tail(c, 0);
+    P.theta = c->d.theta;
+    P.step_ptr = c->d.step;
+    P.err = c->d.status + 1;
+    P.z = c->z;
+    size_t sm = 0;
+    const int w = update_walkers(c->n_ld, c->k_pad, &sm);
+    smem = std::max(smem, sm);
+    const int per = w > 0 ? w : kUpdWalkers;
+    for (int k0 = 0; k0 < c->z; k0 += per) units.push_back({q, k0, w});
   }
-  ucfg.gridDim = dim3(static_cast<unsigned>((c->z + kUpdWalkers - 1) / kUpdWalkers), 1, 1);
-  ucfg.dynamicSmemBytes = 0;
-  return cudaLaunchKernelEx(&ucfg, walker_update_direct_kernel, p.wt,
-                            static_cast<const double*>(p.theta),
-                            static_cast<const uint64_t*>(p.step_ptr), j, p.z);
+  UpdPlan* plan = new UpdPlan();
+  plan->n_units = static_cast<int>(units.size());
+  plan->smem = smem;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&plan->probs), sizeof(UpdProblem) * probs.size());
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&plan->units), sizeof(UpdUnit) * units.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->probs, probs.data(), sizeof(UpdProblem) * probs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->units, units.data(), sizeof(UpdUnit) * units.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(walker_update_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kUpdSmemMax);
+  if (e != cudaSuccess) {
+    snprintf(err, err_len, "walker update table: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    update_plan_destroy(plan);
+    return MHAR_E_CUDA;
+  }
+  *plan_out = plan;
+  return MHAR_OK;
+}
+
+void update_plan_destroy(void* plan_v) {
+  UpdPlan* plan = static_cast<UpdPlan*>(plan_v);
+  if (!plan) return;
+  if (plan->probs) cudaFree(plan->probs);
+  if (plan->units) cudaFree(plan->units);
+  delete plan;
+}
+
+cudaError_t launch_update_plan(const void* plan_v, int j, cudaStream_t stream) {
+  const UpdPlan* plan = static_cast<const UpdPlan*>(plan_v);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(plan->n_units), 1, 1);
+  cfg.blockDim = dim3(kUpdThreads, 1, 1);
+  cfg.dynamicSmemBytes = plan->smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, walker_update_batch_kernel,
+                            static_cast<const UpdProblem*>(plan->probs),
+                            static_cast<const UpdUnit*>(plan->units), j);
 }
 
 // ---- batched persistent launch: host side ---------------------------------------

@@ -1425,6 +1425,7 @@ struct BatchBucket {
   void* table = nullptr;
   int units = 0;
   void* sk = nullptr;
+  void* upd = nullptr;              // the walker update of its problems
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
 };
@@ -1438,6 +1439,7 @@ struct mhar_batch {
   void* table = nullptr;
   int units = 0;
   void* sk = nullptr;           // stream-K plan (C == 0)
+  void* upd = nullptr;          // the walker update of every problem
   uint64_t** steps = nullptr;   // device array of every problem's step counter
   cudaGraphExec_t g_chunk = nullptr;
   cudaGraphExec_t g_one = nullptr;
@@ -1520,7 +1522,14 @@ int batch_buckets_init(mhar_batch* b) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&k.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming);
   }
-  return e == cudaSuccess ? MHAR_OK : batch_cuda(b, e, "bucket streams");
+  if (e != cudaSuccess) return batch_cuda(b, e, "bucket streams");
+  int rc = mhar::update_plan_build(b->ctx.data(), static_cast<int>(b->ctx.size()), &b->upd, b->err,
+                                   sizeof(b->err));
+  for (BatchBucket& k : b->buckets)
+    if (rc == MHAR_OK)
+      rc = mhar::update_plan_build(k.ctx.data(), static_cast<int>(k.ctx.size()), &k.upd, b->err,
+                                   sizeof(b->err));
+  return rc;
 }
 
 // The largest shape allowed for a bucket at or below C (cluster sizes may
@@ -1554,9 +1563,11 @@ cudaError_t batch_enqueue(mhar_batch* b, int count) {
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
     for (BatchBucket& k : b->buckets) {
       if (e == cudaSuccess) e = cudaStreamWaitEvent(k.stream, b->fork, 0);
-      for (int j = 0; j < count && e == cudaSuccess; ++j)
+      for (int j = 0; j < count && e == cudaSuccess; ++j) {
         e = k.C == 0 ? mhar::launch_recompute_batch_sk(k.sk, j, k.stream)
                      : mhar::launch_recompute_batch(k.table, k.units, k.C, j, k.stream);
+        if (e == cudaSuccess) e = mhar::launch_update_plan(k.upd, j, k.stream);
+      }
       if (e == cudaSuccess) e = cudaEventRecord(k.done, k.stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, k.done, 0);
     }
@@ -1566,6 +1577,7 @@ cudaError_t batch_enqueue(mhar_batch* b, int count) {
   for (int j = 0; j < count; ++j) {
     cudaError_t e = b->C == 0 ? mhar::launch_recompute_batch_sk(b->sk, j, b->stream)
                               : mhar::launch_recompute_batch(b->table, b->units, b->C, j, b->stream);
+    if (e == cudaSuccess) e = mhar::launch_update_plan(b->upd, j, b->stream);
     if (e != cudaSuccess) return e;
   }
   return mhar::launch_advance_many(b->steps, static_cast<int>(b->ctx.size()), count, b->stream);
@@ -1597,7 +1609,8 @@ int batch_advance(mhar_batch* b, int64_t count) {
     if (rc) return rc;
   }
   const int64_t n = count;
-  const int64_t per_iter = b->per_bucket ? static_cast<int64_t>(b->buckets.size()) : 1;
+  // Each bucket's (or the batch's) chord kernel and walker update.
+  const int64_t per_iter = 2 * (b->per_bucket ? static_cast<int64_t>(b->buckets.size()) : 1);
   while (count >= b->graph_len) {
     cudaError_t e = cudaGraphLaunch(b->g_chunk, b->stream);
     if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
@@ -1933,9 +1946,11 @@ void mhar_batch_destroy(mhar_batch* b) {
   mhar::batch_sk_destroy(b->sk);
   for (BatchBucket& k : b->buckets) {
     bucket_release(k);
+    mhar::update_plan_destroy(k.upd);
     if (k.done) cudaEventDestroy(k.done);
     if (k.stream) cudaStreamDestroy(k.stream);
   }
+  mhar::update_plan_destroy(b->upd);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->steps) cudaFree(b->steps);
   for (mhar_ctx* c : b->ctx) mhar_destroy(c);

@@ -230,6 +230,13 @@ cudaError_t launch_recompute_batch(const void* table, int units, int C, int j,
 int batch_sk_build(mhar_ctx* const* ctx, int count, void** plan, char* err, size_t err_len);
 void batch_sk_destroy(void* plan);
 cudaError_t launch_recompute_batch_sk(const void* plan, int j, cudaStream_t stream);
+// The batch kernels leave the walker-side work (the moves and the FP16 pairs
+// of the moved points, walker_tail.cuh) to one update launch per iteration
+// over all the batch's problems (kernels_sk.cu): a device table of
+// (problem, walkers) units built from the contexts.
+int update_plan_build(mhar_ctx* const* ctx, int count, void** plan, char* err, size_t err_len);
+void update_plan_destroy(void* plan);
+cudaError_t launch_update_plan(const void* plan, int j, cudaStream_t stream);
 cudaError_t launch_advance_many(uint64_t* const* steps, int count, int by, cudaStream_t stream);
 
 // Whether the stream-K schedule beats clusters along the rows for this shape.

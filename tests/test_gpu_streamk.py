@@ -96,3 +96,23 @@ def test_tall_body_goes_to_stream_k():
     with pytest.raises(mhar.MharError) as e:
         mhar.Sampler(p.A, p.b, p.x0, z, precision="mixed_rs", smem_operands=True, schedule=1)
     assert e.value.code == mhar.E_UNSUPPORTED
+
+
+def test_contexts_of_different_sizes_side_by_side():
+    """Dynamic shared memory limits are set per kernel function, not per
+    context: a small context created after a large one must leave the large
+    one launchable (the stream-K walker update stages 4 walkers of n = 1000
+    but 8 of n = 200; the projection keeps h of either length)."""
+    big = wl.simplex_cuts(1000, 600, seed=2)
+    small = wl.simplex_cuts(200, 300, seed=3)
+    opts = dict(precision="mixed_rs", smem_operands=True, schedule=2)
+    with mhar.Sampler(big.A, big.b, big.x0, 256, AE=big.AE, bE=big.bE, seed=1, **opts) as a:
+        with mhar.Sampler(small.A, small.b, small.x0, 256, AE=small.AE, bE=small.bE, seed=2,
+                          **opts) as b:
+            assert a.kernel_name() == b.kernel_name() == "recompute_sk_kernel"
+            a.run(2)
+            b.run(2)
+            a.run(2)
+            for s in (a, b):
+                st = s.check()
+                assert st.max_violation <= 1e-10 and st.eq_residual <= 1e-8
