@@ -61,7 +61,7 @@ METRIC = "walker-steps/s"
 # entry must be dropped when its kernel changes.
 PROFILED_TRAFFIC = {
     ("rand100x2000", "recompute_ts_kernel"): 9.575e6 + 0.0,
-    ("illcond500x10000", "recompute_sk_kernel"): 271.018e6 + 91.291e6,
+    ("illcond500x10000", "recompute_sk_kernel"): 127.926e6 + 30.817e6,
 }
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = dict(walkers=256, iterations=200)
