@@ -260,7 +260,8 @@ def batch_leg(stream, torch, mhar, peaks) -> dict:
             "value": B["count"] * z * iters / secs, "unit": METRIC,
             "seconds": secs,
             "shape": ({"per_bucket": [c for c in bucket_shapes]} if per_bucket else C),
-            "launches_per_iteration": (sum(1 for c in bucket_shapes if c >= 0) if per_bucket else 1),
+            # a chord kernel and a walker update per bucket (per batch)
+            "launches_per_iteration": 2 * (sum(1 for c in bucket_shapes if c >= 0) if per_bucket else 1),
             "create_seconds": create_s,
             "roofline": {"bound": "tensor", "achieved": flops / secs / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": flops / secs / 1e12 / peak,

@@ -651,15 +651,18 @@ recompute_batch_sk_kernel(const __grid_constant__ BskParams bp, int j) {
 // kernels that do the walker-side work themselves: (1) the move
 // x += theta (d - Q^T c') in double-float and the walker's largest scaled
 // coordinate, (2) the FP16 pair of the scaled point.
-// walker_update_kernel: a CTA takes W consecutive walkers; one thread brings
-// their rows (x hi, x lo: n_ld floats each; the direction pair: k_pad halves
-// each) into shared memory with bulk copies behind one mbarrier, so that all
-// of a CTA's loads are in flight at once; the moved rows and the pair are
-// stored from shared memory with coalesced stores (a warp on consecutive
-// chunks of one walker).
-// walker_update_direct_kernel: rows too long to stage; walker_tail itself,
+// walker_update_kernel (one context) and walker_update_batch_kernel (a table
+// of (problem, first walker, W) units): a CTA of kUpdThreads threads takes W
+// consecutive walkers, as many as 12 KB of shared memory holds (at most
+// kUpdMaxW): small CTAs, sixteen to an SM, so that one CTA's copies overlap the
+// others' arithmetic.  One thread brings the walkers' rows (x hi, x lo: n_ld
+// floats each; the direction pair: k_pad halves each) into shared memory with
+// bulk copies behind one mbarrier, so that all of a CTA's loads are in flight
+// at once; the moved rows and the pair are stored from shared memory with
+// coalesced stores (a warp on consecutive chunks of one walker).  Rows too
+// long to stage (over kUpdSmemMax a walker) take walker_tail itself,
 // kUpdWalkers walkers a CTA.
-constexpr int kUpdThreads = 256;
+constexpr int kUpdThreads = 64;
 constexpr int kUpdMaxW = 8;
 constexpr int kUpdWalkers = 8;
 static_assert(kWalkers % kUpdWalkers == 0, "update CTAs tile a walker strip");
@@ -858,7 +861,7 @@ walker_update_batch_kernel(const UpdProblem* __restrict__ probs, const UpdUnit* 
 constexpr int kUpdSmemMax = 200 << 10;
 int update_walkers(int n_ld, int k_pad, size_t* smem) {
   const size_t per = 8ull * n_ld + 4ull * k_pad;
-  const size_t budget = 48u << 10;
+  const size_t budget = 12u << 10;
   int w = static_cast<int>(budget / per);
   if (w < 1) w = per <= static_cast<size_t>(kUpdSmemMax) ? 1 : 0;
   if (w > kUpdMaxW) w = kUpdMaxW;
