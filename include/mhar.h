@@ -344,8 +344,9 @@ int mhar_fit_from_moments(mhar_ctx* ctx, const double* s1, const double* s2, int
                           int32_t rank, int32_t power_iters);
 
 /* ---- batches of polytopes ------------------------------------------------- */
-/* Many independent problems advanced together, one kernel launch per
- * iteration for all of them (the paper runs one polytope at a time; its
+/* Many independent problems advanced together, two kernel launches per
+ * iteration for all of them -- the chord kernel and the walker update (the
+ * moves and the next operands) -- (the paper runs one polytope at a time; its
  * padding study, Section 6.2, is about filling the GPU with walkers, which a
  * batch does with problems).  Every problem is a full MHAR_MIXED_RECOMPUTE
  * sampler of its own (Algorithm 2, Lemma 4.2 on the tensor cores) with z
@@ -354,9 +355,10 @@ int mhar_fit_from_moments(mhar_ctx* ctx, const double* s1, const double* s2, int
  * Two launch shapes, over the (problem, strip of 128 walkers) units,
  * largest first: each unit on a cluster of C CTAs along its rows (C = 1, 2,
  * 4, 8); or a persistent launch of one CTA per SM in which every CTA pulls
- * whole units from a device queue, so that one unit's walker-side work
- * overlaps the next unit's loads and MMAs (shape 0).  mhar_batch_tune picks
- * the shape, for the whole batch or per bucket (below). */
+ * whole units from a device queue, with its pipelines carried from unit to
+ * unit (shape 0).  mhar_batch_tune picks the shape, for the whole batch or
+ * per bucket (below; in per-bucket mode each bucket has its own two
+ * launches). */
 typedef struct {
   const double* A;   /* m x n, row-major (copied)                 */
   const double* b;   /* m                                         */

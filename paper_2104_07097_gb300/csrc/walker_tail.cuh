@@ -1,5 +1,7 @@
 // walker_tail.cuh -- the walker-side work of a recompute-mode iteration, run
-// inside the chord kernel of iteration s.
+// inside the chord kernel of iteration s (the TMEM-operand and cluster
+// kernels), or after it, item for item the same, by the walker update kernels
+// of the stream-K and batched launches (kernels_sk.cu).
 //
 // Every CTA of a walker strip's cluster takes a contiguous share of the
 // strip's 128 walkers.

@@ -473,8 +473,8 @@ class Sampler:
 
 
 class Batch:
-    """Many polytopes advanced together, one launch per iteration
-    (``mhar_batch_*``).  ``problems``: list of (A, b, x0); problem p uses
+    """Many polytopes advanced together, a chord launch and a walker-update
+    launch per iteration (``mhar_batch_*``).  ``problems``: list of (A, b, x0); problem p uses
     Philox key seed + p; every problem has z walkers; recompute tensor-core mode."""
 
     def __init__(self, problems, z: int, seed: int = 0, stream=None, out_on_device: bool = False,
