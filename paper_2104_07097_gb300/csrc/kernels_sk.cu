@@ -721,23 +721,33 @@ __device__ __forceinline__ void update_staged(const WalkerTail& wt, const double
   }
   const int chunks = (n + 7) >> 3;
   const int items = wn * chunks;
+  // Items it = wo chunks + c, tid + kUpdThreads apart: (wo, c) advanced by a
+  // fixed (step_w, step_c) instead of a division per item.
+  const int step_w = kUpdThreads / chunks, step_c = kUpdThreads - step_w * chunks;
+  const int wo0 = tid / chunks, c0 = tid - wo0 * chunks;
+  const bool unit = wt.unit_sigma != 0;
   // (1) the moves, in shared memory, and each walker's largest scaled coordinate.
-  for (int it = tid; it < items; it += kUpdThreads) {
-    const int wo = it / chunks, c = it - wo * chunks;
+  for (int it = tid, wo = wo0, c = c0; it < items; it += kUpdThreads) {
     const int k = k0 + wo, i0 = 8 * c;
+    const bool last = i0 + 8 > n;   // the one chunk that reaches past n
     float* xh = xs + static_cast<size_t>(2 * wo) * n_ld + i0;
     float* xl = xh + n_ld;
     const float th = theta_s[wo];
-    float hi[8], lo[8];
+    float hi[8], lo[8], sg[8];
     ld8(xh, hi);
     ld8(xl, lo);
+    if (!unit) ld8(wt.sigma + i0, sg);
     if (th != 0.0f) {
       float dh[8], dl[8], d[8];
       ld8h(ds + static_cast<size_t>(2 * wo) * k_pad + i0, dh);
       ld8h(ds + static_cast<size_t>(2 * wo + 1) * k_pad + i0, dl);
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        d[e] = i0 + e < n ? (wt.unit_sigma ? dh[e] + dl[e] : (dh[e] + dl[e]) * wt.sigma[i0 + e]) : 0.0f;
+      for (int e = 0; e < 8; ++e) d[e] = unit ? dh[e] + dl[e] : (dh[e] + dl[e]) * sg[e];
+      if (last) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (i0 + e >= n) d[e] = 0.0f;
+      }
 #pragma unroll
       for (int e = 0; e < 8; ++e) df_axpy(hi[e], lo[e], th, d[e]);
       if (wt.corr != nullptr) {
@@ -756,20 +766,35 @@ __device__ __forceinline__ void update_staged(const WalkerTail& wt, const double
       st8(xl, lo);
     }
     float mx = 0.0f;
-    if (wt.unit_sigma) {
+    if (unit) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(hi[e]));   // x = 0 past n
     } else {
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        if (i0 + e < n) mx = fmaxf(mx, fabsf(hi[e]) * pow2_recip(wt.sigma[i0 + e]));
+        if (!last || i0 + e < n) mx = fmaxf(mx, fabsf(hi[e]) * pow2_recip(sg[e]));
     }
     atomicMax(red + wo, __float_as_uint(mx));  // non-negative floats order as their bits
+    c += step_c;
+    wo += step_w;
+    if (c >= chunks) {
+      c -= chunks;
+      ++wo;
+    }
+  }
+  __syncthreads();
+  // Each walker's power-of-two scale, once.
+  __shared__ float inv_s[kUpdMaxW];
+  if (tid < wn) {
+    const float mx = __uint_as_float(red[tid]);
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
+    inv_s[tid] = ldexpf(1.0f, -ex);
+    wt.wscale[k0 + tid] = ldexpf(1.0f, ex);
   }
   __syncthreads();
   // (2) the moved rows back, and the FP16 pair of the scaled point.
-  for (int it = tid; it < items; it += kUpdThreads) {
-    const int wo = it / chunks, c = it - wo * chunks;
+  for (int it = tid, wo = wo0, c = c0; it < items; it += kUpdThreads) {
     const int k = k0 + wo, i0 = 8 * c;
     const float* xh = xs + static_cast<size_t>(2 * wo) * n_ld + i0;
     float hi[8], lo[8], v[8];
@@ -778,20 +803,25 @@ __device__ __forceinline__ void update_staged(const WalkerTail& wt, const double
     const size_t xr = static_cast<size_t>(k) * n_ld + i0;
     st8(wt.Xhi + xr, hi);
     st8(wt.Xlo + xr, lo);
-    const float mx = __uint_as_float(red[wo]);
-    int ex = 0;
-    if (mx > 0.0f) frexpf(mx, &ex);
-    const float inv = ldexpf(1.0f, -ex);
-    if (c == 0) wt.wscale[k] = ldexpf(1.0f, ex);
-    if (wt.unit_sigma) {
+    const float inv = inv_s[wo];
+    // x = 0 and sigma = 1 past n: no per-coordinate branch.
+    if (unit) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv;
     } else {
+      float sg[8];
+      ld8(wt.sigma + i0, sg);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv * pow2_recip(wt.sigma[i0 + e]);
+      for (int e = 0; e < 8; ++e) v[e] = (hi[e] + lo[e]) * inv * pow2_recip(sg[e]);
     }
     const size_t o = static_cast<size_t>(k) * k_pad + i0;   // row-major operands
     if (split_store8(v, wt.Xh + o, wt.Xl + o)) atomicOr(wt.status, MHAR_ST_NONFINITE);
+    c += step_c;
+    wo += step_w;
+    if (c >= chunks) {
+      c -= chunks;
+      ++wo;
+    }
   }
 }
 
@@ -815,7 +845,7 @@ __device__ __forceinline__ void update_direct(const WalkerTail& wt, const double
 }
 
 // One context: W walkers a CTA (W = 0: the direct form, kUpdWalkers a CTA).
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(kUpdThreads, 16)
 walker_update_kernel(const WalkerTail wt, const double* __restrict__ theta,
                      const uint64_t* step_ptr, int j, int z, int W, int* err) {
   // Programmatic dependent of the chord kernel: theta and the points are
@@ -840,7 +870,7 @@ struct UpdUnit {
   int prob, k0, w;
 };
 
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(kUpdThreads, 16)
 walker_update_batch_kernel(const UpdProblem* __restrict__ probs, const UpdUnit* __restrict__ units,
                            int j) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
