@@ -11,9 +11,9 @@ every iteration (opts.audit_every = 1, every walker) on
   * random bodies with m close to 2n: nearly unbounded, with long axes, so
     the points and chords are long and sum |a_ij x_j| is large;
   * the simplex with cuts (one equality, checked to 1e-8);
-in every arithmetic mode and launch schedule.  The bound is the benchmark spec's
-max(A x - b) <= 1e-6 |b|_inf; the construction aims at <= 0 up to the FP64
-rounding of the audit itself, which is asserted too.
+in every arithmetic mode and launch schedule.  The required bound is
+max(A x - b) <= 1e-6 |b|_inf at every step; the construction aims at <= 0 up
+to the FP64 rounding of the audit itself, which is asserted too.
 """
 import numpy as np
 import pytest
